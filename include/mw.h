@@ -1,0 +1,183 @@
+/* mw.h -- C interface of the GB300 m-double matrix product library (libmw.so).
+ *
+ * An m-double is an unevaluated sum of m nonoverlapping doubles (Section 1 of
+ * J. Verschelde, "Multiword Arithmetic and Parallel Computing"); m is 2
+ * (double double), 4 (quad double) or 8 (octo double).  A matrix of
+ * m-doubles is stored as m planes of doubles ("structure of arrays", the
+ * register-friendly layout the abstract argues for): entry (r, c) of word
+ * plane j is at  base[j * plane_stride + r * ld + c]  (row major, ld >= cols,
+ * plane_stride >= rows * ld, planes must not overlap).
+ *
+ * The library computes C = op(A) op(B) with the paper's error-free
+ * summation (Section 2, Figure 1; matrix form in Section 4):
+ *   1. every row of op(A) and every column of op(B) gets one shared exponent E;
+ *   2. every entry is cut, on a fixed-point grid below 2^E, into S pieces of w
+ *      bits whose high bits are zero (balanced digits, |d| <= 2^(w-1));
+ *   3. the products of pieces are summed exactly, grouped by diagonal
+ *      t = p + q, s_t = sum_{p+q=t} sum_k dA_{p,ik} dB_{q,kj}  (the paper's s_i);
+ *   4. the diagonal sums are fused into m nonoverlapping doubles.
+ * Two forms compute step 3:
+ *   MW_PLAIN  pieces are doubles (w about 20), products and sums on the FP64
+ *             pipe, exact while the number of terms stays below the threshold
+ *             of Section 2; step 4 adds the scaled s_t in m-double arithmetic.
+ *   MW_OZAKI  pieces are integers of w = 7 or 8 bits held in bfloat16, every
+ *             pair of piece matrices is a tensor-core product (tcgen05,
+ *             fp32 accumulation, exact below 2^24 and drained to 64-bit integers
+ *             before that), the "stepping stone to the Ozaki scheme" of
+ *             Section 1; step 4 is exact integer fusion and rounding to nearest
+ *             of each word in turn.
+ *
+ * Conventions for every entry point:
+ *  - Device pointers unless the name says otherwise; the caller owns all memory.
+ *  - Work is ordered on `stream` (a cudaStream_t; NULL = legacy default stream)
+ *    and is asynchronous unless the comment says the call synchronizes.
+ *  - The return value is MW_OK or an MW_E* code for errors found on the host
+ *    (bad arguments, launch failures).  Errors found on the GPU (non-finite or
+ *    badly normalised input, a wait that timed out) are OR-ed into a per-device
+ *    status word that mw_get_status() reads.
+ *  - mw_last_error() gives a message for the last host-side error of the
+ *    calling thread.  Nothing throws across this interface.
+ */
+#ifndef MW_H
+#define MW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mw_stream_t; /* same type as cudaStream_t */
+
+/* return codes (host) and status bits (device, see mw_get_status) */
+enum {
+  MW_OK = 0,
+  MW_EINVAL = 1,      /* bad argument: m not in {2,4,8}, dims <= 0, ld too small, NULL */
+  MW_ERANGE = 2,      /* status bit: fixed-point value outside [-2^(wS-1), 2^(wS-1)) (input not normalised) */
+  MW_ENONFINITE = 4,  /* status bit: an input word is inf or nan */
+  MW_ECUDA = 8,       /* a CUDA call failed */
+  MW_ETIMEOUT = 16,   /* status bit: a bounded wait inside a kernel gave up */
+  MW_ENOSPC = 32,     /* workspace smaller than mw_gemm_workspace_size() */
+  MW_WRANGE = 64,     /* status bit (warning): an operand's exponent spread exceeds the
+                         spread the plan was made for; the error bound is not guaranteed */
+  MW_EUNSUPPORTED = 128
+};
+
+/* forms of the product */
+enum { MW_PLAIN = 0, MW_OZAKI = 1 };
+
+/* digit formats written by mw_split */
+enum { MW_DIGITS_BF16 = 0, MW_DIGITS_F64 = 1 };
+
+/* A plan fixes the slicing of a product.  mw_plan_gemm fills it from the error
+ * analysis (see there); a caller may also set the fields directly.
+ *   w      piece width in bits (MW_OZAKI: 7 or 8; MW_PLAIN: 1..26)
+ *   S_A    pieces per entry of op(A); S_B pieces per entry of op(B)
+ *   D      diagonals kept: pairs (p, q) with p < S_A, q < S_B, p + q < D
+ *   group  diagonals fused into one 64-bit partial sum (MW_OZAKI)
+ *   chunk  products of pieces accumulated in fp32 before a drain (MW_OZAKI;
+ *          multiple of 64)
+ *   range_A, range_B  exponent spread (bits) the plan assumes for the rows of
+ *          op(A) / columns of op(B); larger spreads raise MW_WRANGE. */
+typedef struct mw_plan {
+  int m, mode, w, S_A, S_B, D, group, chunk, range_A, range_B;
+} mw_plan;
+
+/* Plan a product so that |C - C_exact| <= 2K 2^(-52m) (|op(A)||op(B)|)
+ * componentwise for any operands whose rows of op(A) (columns of op(B)) span at
+ * most range_A (range_B) binary orders of magnitude, measured as max minus min
+ * of ilogb+1 over the nonzero entries.  Host only, no GPU work.
+ * Returns MW_EINVAL for bad arguments, MW_EUNSUPPORTED if no plan fits the
+ * exactness thresholds (e.g. K too long for MW_PLAIN). */
+int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, int range_B,
+                 mw_plan *plan);
+
+/* Steps 1-2 for one operand (Section 2; the quarters of the double double
+ * inner product generalised to S pieces of w bits).
+ * The logical operand has R rows (the output dimension) and K columns (the
+ * reduction dimension).  trans = 0: X is stored R x K (X[r*ld + k]);
+ * trans = 1: X is stored K x R (X[k*ld + r]).
+ * Outputs (device memory owned by the caller):
+ *   exps[r]   = E_r = max over the row of (ilogb(x_j) + 1) over nonzero words x_j,
+ *               0 for an all-zero row;
+ *   spread[r] = E_r - min over nonzero entries of (max_j ilogb(x_j) + 1);
+ *   digits    S planes of R x digit_ld pieces, piece p of entry (r, k) at
+ *             digits[(p * R + r) * digit_ld + k], as bfloat16 (format
+ *             MW_DIGITS_BF16, w <= 9) or double (MW_DIGITS_F64); columns
+ *             K..digit_ld-1 are written with zeros.  Piece p weighs
+ *             2^(E_r + 2 - w (p + 1)); the pieces are the balanced base-2^w
+ *             digits of T = sum_j trunc(x_j 2^(wS - 2 - E_r)).
+ *   max_spread (may be NULL): one int updated with atomicMax of spread[r].
+ * GPU-side errors: MW_ENONFINITE, MW_ERANGE (T outside [-2^(wS-1), 2^(wS-1))) in the status word;
+ * MW_WRANGE when spread[r] > range (pass range < 0 to skip the check). */
+int mw_split(int m, int trans, int64_t R, int64_t K, const double *X, int64_t ld,
+             int64_t plane_stride, int w, int S, int format, void *digits, int64_t digit_ld,
+             int32_t *exps, int32_t *spread, int32_t *max_spread, int range, mw_stream_t stream);
+
+/* Bytes of device workspace mw_gemm needs for this plan and shape. */
+int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K, size_t *bytes);
+
+/* Where mw_gemm keeps its intermediates inside ws, for inspection and tests:
+ * offsets[0] int32 exponents and spreads: E_A[M], spread_A[M], E_B[N], spread_B[N];
+ * offsets[1] pieces of op(A): S_A planes of M x Kp (Kp = K rounded up to 64),
+ *            bfloat16 (MW_OZAKI) or double (MW_PLAIN), layout as in mw_split;
+ * offsets[2] pieces of op(B)^T: S_B planes of N x Kp;
+ * offsets[3] (MW_OZAKI) 64-bit partial sums: for group g of diagonals
+ *            [g*group, min(D, (g+1)*group) - 1] and output tile (tm, tn) of
+ *            128 x 128, entry (r, c) of the tile at
+ *            ((g * tiles + tn * tiles_m + tm) * 128 + r) * 128 + c,
+ *            V = sum_t s_t 2^(w (t1 - t)) over the group's diagonals.
+ * bytes = total workspace size (same as mw_gemm_workspace_size). */
+int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
+                             size_t offsets[4], size_t *bytes);
+
+/* C = op(A) op(B), overwriting the m planes of C (M x N).  op(A) is M x K,
+ * op(B) is K x N; transA/transB = 1 take the stored matrix transposed
+ * (A stored K x M, B stored N x K).  plan->m words per entry in A, B and C.
+ * ws: device workspace of at least mw_gemm_workspace_size() bytes; it holds the
+ * pieces, the exponents and the diagonal partial sums; no memory is allocated.
+ * Asynchronous on `stream`. */
+int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, int64_t K,
+            const double *A, int64_t lda, int64_t plane_stride_a,
+            const double *B, int64_t ldb, int64_t plane_stride_b,
+            double *C, int64_t ldc, int64_t plane_stride_c,
+            void *ws, size_t ws_bytes, mw_stream_t stream);
+
+/* Exponent spreads (max over rows of op(A), columns of op(B)) measured on the
+ * GPU; synchronizes the stream.  ws as for mw_gemm with any plan of this m
+ * (only 2 * (M + N + 1) int32 are used).  Feed the results to mw_plan_gemm. */
+int mw_measure_spread(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,
+                      const double *A, int64_t lda, int64_t plane_stride_a,
+                      const double *B, int64_t ldb, int64_t plane_stride_b,
+                      void *ws, size_t ws_bytes, int *range_A, int *range_B, mw_stream_t stream);
+
+/* Adjoint of C = A B for a loss L with dL/dC = G (M x N), all m-doubles:
+ * dA = G B^T (M x K) and dB = A^T G (K x N), each computed like mw_gemm with
+ * the transposes folded into the slicing.  plan_dA and plan_dB are plans of the
+ * two products (shapes M x K x N and K x N x M).  ws: at least the larger of
+ * their workspace sizes.  Either output may be NULL to skip it. */
+int mw_gemm_backward(const mw_plan *plan_dA, const mw_plan *plan_dB,
+                     int64_t M, int64_t N, int64_t K,
+                     const double *A, int64_t lda, int64_t plane_stride_a,
+                     const double *B, int64_t ldb, int64_t plane_stride_b,
+                     const double *G, int64_t ldg, int64_t plane_stride_g,
+                     double *dA, int64_t ldda, int64_t plane_stride_da,
+                     double *dB, int64_t lddb, int64_t plane_stride_db,
+                     void *ws, size_t ws_bytes, mw_stream_t stream);
+
+/* Read the device status word of the current device (synchronizes the device);
+ * clear != 0 resets it to zero afterwards. */
+int mw_get_status(int *bits, int clear);
+
+/* Message for the last host-side error of the calling thread ("" if none). */
+const char *mw_last_error(void);
+
+/* Library version string. */
+const char *mw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MW_H */

@@ -19,7 +19,9 @@ the readings the GPU library follows:
   E_r = max over the row of e (0 for an all-zero row);
 * fixed point: with S pieces of w bits, F_r = w S - 2 - E_r and
   T = sum_j trunc(x_j 2^F_r) (every word truncated toward zero on its own, as
-  the paper cuts hi and lo words separately), |T| <= 2^(wS-1) required;
+  the paper cuts hi and lo words separately), -2^(wS-1) <= T < 2^(wS-1)
+  required (the two's complement range of wS bits; the digit bounds below
+  hold on it);
 * pieces: the balanced base-2^w digits of T, d_0 most significant,
   T = sum_p d_p 2^(w(S-1-p)), -2^(w-1) <= d_p <= 2^(w-1); digit p of row r
   weighs 2^(E_r + 2 - w(p+1));
@@ -131,7 +133,7 @@ class Split:
             for k in range(K):
                 T = fixed_point(L[:, r, k], F)
                 self.T[a][k] = T
-                if abs(T) > lim:
+                if not (-lim <= T < lim):
                     self.in_range = False
                 d = balanced_digits(T, w, S)
                 for p in range(S):

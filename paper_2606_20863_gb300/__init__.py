@@ -1,0 +1,281 @@
+"""Python binding of libmw, the GB300 m-double matrix product library.
+
+Argument marshalling only: every step of the product runs in the CUDA kernels
+of ``libmw.so`` (C interface ``include/mw.h``); PyTorch supplies device memory
+and the current stream.  An m-double matrix is a float64 tensor of shape
+(m, rows, cols) whose last dimension is contiguous; plane j holds word j of
+every entry (m = 2, 4 or 8).
+
+The functions keep the names of the C entry points: ``mw_plan_gemm``,
+``mw_split``, ``mw_gemm``, ``mw_gemm_backward``; ``MWGemm`` is the
+``torch.autograd.Function`` over ``mw_gemm`` / ``mw_gemm_backward``.
+If the compiled library is missing this module raises on import: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmw.so")
+
+MW_OK, MW_EINVAL, MW_ERANGE, MW_ENONFINITE, MW_ECUDA, MW_ETIMEOUT, MW_ENOSPC, MW_WRANGE = (
+    0, 1, 2, 4, 8, 16, 32, 64)
+MW_PLAIN, MW_OZAKI = 0, 1
+MW_DIGITS_BF16, MW_DIGITS_F64 = 0, 1
+_MODES = {"plain": MW_PLAIN, "ozaki": MW_OZAKI}
+STATUS_NAMES = {MW_ERANGE: "ERANGE", MW_ENONFINITE: "ENONFINITE", MW_ETIMEOUT: "ETIMEOUT",
+                MW_WRANGE: "WRANGE"}
+
+
+class MWError(RuntimeError):
+    pass
+
+
+class mw_plan(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in
+                ("m", "mode", "w", "S_A", "S_B", "D", "group", "chunk", "range_A", "range_B")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+    def __repr__(self):
+        return "mw_plan(" + ", ".join(f"{k}={v}" for k, v in self.as_dict().items()) + ")"
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(_LIB_PATH)
+    i64, i32, vp, ip = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)
+    pp = ctypes.POINTER(mw_plan)
+    sig = {
+        "mw_plan_gemm": [i32, i32, i64, i64, i64, i32, i32, pp],
+        "mw_split": [i32, i32, i64, i64, vp, i64, i64, i32, i32, i32, vp, i64, vp, vp, vp, i32, vp],
+        "mw_gemm_workspace_size": [pp, i64, i64, i64, ctypes.POINTER(ctypes.c_size_t)],
+        "mw_gemm_workspace_layout": [pp, i64, i64, i64, ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)],
+        "mw_gemm": [pp, i32, i32, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
+                    vp, ctypes.c_size_t, vp],
+        "mw_measure_spread": [i32, i32, i32, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp,
+                              ctypes.c_size_t, ip, ip, vp],
+        "mw_gemm_backward": [pp, pp, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
+                             vp, i64, i64, vp, i64, i64, vp, ctypes.c_size_t, vp],
+        "mw_get_status": [ip, i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.mw_last_error.restype = ctypes.c_char_p
+    lib.mw_version.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _LIB_PATH
+EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_workspace_layout",
+            "mw_gemm",
+            "mw_measure_spread", "mw_gemm_backward", "mw_get_status", "mw_last_error",
+            "mw_version")
+
+
+def _check(rc: int, what: str):
+    if rc != MW_OK:
+        raise MWError(f"{what} failed ({rc}): {_lib.mw_last_error().decode()}")
+
+
+def version() -> str:
+    return _lib.mw_version().decode()
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _mat(X: torch.Tensor, name: str):
+    """(pointer, ld, plane_stride) of an (m, rows, cols) float64 CUDA tensor."""
+    if X.dtype != torch.float64 or X.dim() != 3 or not X.is_cuda:
+        raise MWError(f"{name} must be a CUDA float64 tensor of shape (m, rows, cols)")
+    if X.stride(2) != 1:
+        raise MWError(f"{name}: last dimension must be contiguous")
+    return ctypes.c_void_p(X.data_ptr()), X.stride(1), X.stride(0)
+
+
+def get_status(clear: bool = True) -> int:
+    """Status bits raised by kernels on the current device (synchronizes)."""
+    bits = ctypes.c_int(0)
+    _check(_lib.mw_get_status(ctypes.byref(bits), int(clear)), "mw_get_status")
+    return bits.value
+
+
+def check_status(allow: int = MW_WRANGE):
+    """Raise if a kernel reported an error bit other than those in ``allow``."""
+    bits = get_status(clear=True)
+    if bits & ~allow:
+        names = [n for b, n in STATUS_NAMES.items() if bits & b]
+        raise MWError(f"kernel status {bits}: {', '.join(names)}")
+    return bits
+
+
+def mw_plan_gemm(m: int, mode: str | int, M: int, N: int, K: int, range_A: int,
+                 range_B: int) -> mw_plan:
+    p = mw_plan()
+    mode = _MODES.get(mode, mode)
+    _check(_lib.mw_plan_gemm(m, mode, M, N, K, range_A, range_B, ctypes.byref(p)),
+           "mw_plan_gemm")
+    return p
+
+
+def workspace_size(plan: mw_plan, M: int, N: int, K: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_lib.mw_gemm_workspace_size(ctypes.byref(plan), M, N, K, ctypes.byref(n)),
+           "mw_gemm_workspace_size")
+    return n.value
+
+
+def workspace_layout(plan: mw_plan, M: int, N: int, K: int):
+    """(offsets of exponents, pieces of A, pieces of B, partial sums; total bytes)."""
+    off = (ctypes.c_size_t * 4)()
+    n = ctypes.c_size_t(0)
+    _check(_lib.mw_gemm_workspace_layout(ctypes.byref(plan), M, N, K, off, ctypes.byref(n)),
+           "mw_gemm_workspace_layout")
+    return list(off), n.value
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def _dims(A, B, transA, transB):
+    m = A.shape[0]
+    M, K = (A.shape[2], A.shape[1]) if transA else (A.shape[1], A.shape[2])
+    Kb, N = (B.shape[2], B.shape[1]) if transB else (B.shape[1], B.shape[2])
+    if K != Kb or B.shape[0] != m:
+        raise MWError(f"shape mismatch: op(A) {M}x{K}, op(B) {Kb}x{N}, m {m}/{B.shape[0]}")
+    return m, M, N, K
+
+
+def mw_measure_spread(A: torch.Tensor, B: torch.Tensor, transA=False, transB=False):
+    """Exponent spreads of the rows of op(A) and the columns of op(B) (synchronizes)."""
+    m, M, N, K = _dims(A, B, transA, transB)
+    ws = _workspace(4 * (2 * M + 2 * N + 2), A.device)
+    ra, rb = ctypes.c_int(0), ctypes.c_int(0)
+    pa, lda, psa = _mat(A, "A")
+    pb, ldb, psb = _mat(B, "B")
+    _check(_lib.mw_measure_spread(m, int(transA), int(transB), M, N, K, pa, lda, psa, pb, ldb,
+                                  psb, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                  ctypes.byref(ra), ctypes.byref(rb), _stream()),
+           "mw_measure_spread")
+    return ra.value, rb.value
+
+
+def mw_split(X: torch.Tensor, w: int, S: int, trans: bool = False, fmt: str = "bf16",
+             range_: int = -1):
+    """Cut the logical operand (rows x K; X stored rows x K, or K x rows when
+    ``trans``) into S pieces of w bits.  Returns (digits, exps, spread):
+    digits (S, rows, Kp) bfloat16 or float64 with Kp = K rounded up to 64."""
+    m = X.shape[0]
+    R, K = (X.shape[2], X.shape[1]) if trans else (X.shape[1], X.shape[2])
+    Kp = (K + 63) // 64 * 64
+    dtype = torch.bfloat16 if fmt == "bf16" else torch.float64
+    digits = torch.empty((S, R, Kp), dtype=dtype, device=X.device)
+    exps = torch.empty(R, dtype=torch.int32, device=X.device)
+    spread = torch.empty(R, dtype=torch.int32, device=X.device)
+    px, ld, ps = _mat(X, "X")
+    _check(_lib.mw_split(m, int(trans), R, K, px, ld, ps, w, S,
+                         MW_DIGITS_BF16 if fmt == "bf16" else MW_DIGITS_F64,
+                         ctypes.c_void_p(digits.data_ptr()), Kp,
+                         ctypes.c_void_p(exps.data_ptr()), ctypes.c_void_p(spread.data_ptr()),
+                         None, range_, _stream()), "mw_split")
+    return digits, exps, spread
+
+
+def plan_for(A: torch.Tensor, B: torch.Tensor, mode="ozaki", transA=False, transB=False,
+             **overrides) -> mw_plan:
+    """Plan with the exponent spreads measured on the operands (synchronizes)."""
+    m, M, N, K = _dims(A, B, transA, transB)
+    ra, rb = mw_measure_spread(A, B, transA, transB)
+    p = mw_plan_gemm(m, mode, M, N, K, ra, rb)
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def mw_gemm(A: torch.Tensor, B: torch.Tensor, plan: mw_plan | None = None, mode="ozaki",
+            transA=False, transB=False, C: torch.Tensor | None = None,
+            ws: torch.Tensor | None = None, check: bool = True) -> torch.Tensor:
+    """C = op(A) op(B) in m-double precision."""
+    m, M, N, K = _dims(A, B, transA, transB)
+    if plan is None:
+        plan = plan_for(A, B, mode, transA, transB)
+    if C is None:
+        C = torch.empty((m, M, N), dtype=torch.float64, device=A.device)
+    need = workspace_size(plan, M, N, K)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, A.device)
+    pa, lda, psa = _mat(A, "A")
+    pb, ldb, psb = _mat(B, "B")
+    pc, ldc, psc = _mat(C, "C")
+    _check(_lib.mw_gemm(ctypes.byref(plan), int(transA), int(transB), M, N, K, pa, lda, psa,
+                        pb, ldb, psb, pc, ldc, psc, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                        _stream()), "mw_gemm")
+    if check:
+        check_status()
+    return C
+
+
+def mw_gemm_backward(A: torch.Tensor, B: torch.Tensor, G: torch.Tensor,
+                     plan_dA: mw_plan | None = None, plan_dB: mw_plan | None = None,
+                     mode="ozaki", need_dA=True, need_dB=True, check: bool = True):
+    """dA = G B^T and dB = A^T G for C = A B (A M x K, B K x N, G M x N)."""
+    m, M, K = A.shape
+    N = B.shape[2]
+    if plan_dA is None and need_dA:
+        plan_dA = plan_for(G, B, mode, False, True)
+    if plan_dB is None and need_dB:
+        plan_dB = plan_for(A, G, mode, True, False)
+    need = max(workspace_size(plan_dA, M, K, N) if need_dA else 0,
+               workspace_size(plan_dB, K, N, M) if need_dB else 0)
+    ws = _workspace(need, A.device)
+    dA = torch.empty((m, M, K), dtype=torch.float64, device=A.device) if need_dA else None
+    dB = torch.empty((m, K, N), dtype=torch.float64, device=A.device) if need_dB else None
+    pa, lda, psa = _mat(A, "A")
+    pb, ldb, psb = _mat(B, "B")
+    pg, ldg, psg = _mat(G, "G")
+    pda, ldda, psda = _mat(dA, "dA") if need_dA else (None, 0, 0)
+    pdb, lddb, psdb = _mat(dB, "dB") if need_dB else (None, 0, 0)
+    _check(_lib.mw_gemm_backward(ctypes.byref(plan_dA) if need_dA else None,
+                                 ctypes.byref(plan_dB) if need_dB else None, M, N, K,
+                                 pa, lda, psa, pb, ldb, psb, pg, ldg, psg,
+                                 pda, ldda, psda, pdb, lddb, psdb,
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()),
+           "mw_gemm_backward")
+    if check:
+        check_status()
+    return dA, dB
+
+
+class MWGemm(torch.autograd.Function):
+    """C = A B for m-double tensors (m, rows, cols).  The gradient with respect
+    to an m-double input is the m-double value of dL/dA in the same plane
+    format (not a derivative per plane): dA = G B^T, dB = A^T G."""
+
+    @staticmethod
+    def forward(ctx, A, B, mode="ozaki"):
+        ctx.save_for_backward(A, B)
+        ctx.mode = mode
+        return mw_gemm(A, B, mode=mode)
+
+    @staticmethod
+    def backward(ctx, G):
+        A, B = ctx.saved_tensors
+        G = G.contiguous()
+        dA, dB = mw_gemm_backward(A, B, G, mode=ctx.mode, need_dA=ctx.needs_input_grad[0],
+                                  need_dB=ctx.needs_input_grad[1])
+        return dA, dB, None

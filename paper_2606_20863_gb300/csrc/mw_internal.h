@@ -1,0 +1,57 @@
+// Internal declarations of libmw shared by its translation units (not installed).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mw.h"
+
+namespace mw {
+
+// Host-side error message of the calling thread (mw_last_error).
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+// Device address of the status word of the current device.
+unsigned int *status_ptr();
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// ---- split (mw_split.cu) ----------------------------------------------------
+struct SplitArgs {
+  int m, trans, w, S, format, range;
+  int64_t R, K, ld, plane_stride, digit_ld;
+  const double *X;
+  void *digits;
+  int32_t *exps, *spread, *max_spread;
+};
+int launch_split(const SplitArgs &a, bool exponents_only, cudaStream_t s);
+
+// ---- plain FP64 form (mw_plain.cu) -------------------------------------------
+struct PlainArgs {
+  int m, w, S_A, S_B, D;
+  int64_t M, N, Kp;            // Kp: padded reduction length (digit row stride)
+  const double *dA, *dB;        // S_A x M x Kp, S_B x N x Kp pieces
+  const int32_t *eA, *eB;       // row / column exponents
+  double *C;
+  int64_t ldc, psc;
+};
+int launch_plain(const PlainArgs &a, cudaStream_t s);
+
+// ---- Ozaki form (mw_ozaki.cu) ------------------------------------------------
+struct OzakiArgs {
+  int m, w, S_A, S_B, D, group, chunk;
+  int64_t M, N, Kp;
+  const void *dA, *dB;          // bf16 pieces, S x rows x Kp
+  const int32_t *eA, *eB;
+  int64_t *partials;            // G x tiles x 128 x 128
+  double *C;
+  int64_t ldc, psc;
+};
+int launch_ozaki(const OzakiArgs &a, cudaStream_t s);
+size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group);
+
+// Number of diagonal groups.
+inline int n_groups(int D, int group) { return (D + group - 1) / group; }
+
+}  // namespace mw

@@ -1,0 +1,341 @@
+// Steps 1-2 of the error-free summation (Section 2): a shared exponent per row
+// of the logical operand, then every entry cut into S balanced pieces of w bits.
+//
+// Logical operand: R rows (output dimension) x K columns (reduction).  trans = 0
+// reads X[r*ld + k] (k contiguous), trans = 1 reads X[k*ld + r] (r contiguous)
+// and transposes through shared memory so that the pieces are written with k
+// contiguous either way.
+//
+// Pass 1 (exponents): E'_r = max over nonzero words of ilogb+1, e'_r = min over
+//   nonzero entries of the entry exponent, kept biased in int32 so that zero
+//   means "nothing seen" and a memset initialises them.
+// Finalize: E_r (0 for an all-zero row), spread_r = E_r - e_r, warning check.
+// Pass 2 (pieces): T = sum_j trunc(x_j 2^(wS-2-E_r)) in NL 64-bit limbs (two's
+//   complement), then the balanced base-2^w digits from the least significant
+//   end with a carry, written as bfloat16 or double.
+#include <cuda_bf16.h>
+#include <cstdio>
+
+#include "mw_device.cuh"
+
+namespace mw {
+namespace {
+
+constexpr int kBias = 1 << 20;  // E and -e stored as value + kBias (> 0 for any double)
+
+__device__ __forceinline__ void entry_exps(const double *x, int64_t plane_stride, int m,
+                                           int &e_entry, bool &nonfinite) {
+  e_entry = kExpZero;
+  for (int j = 0; j < m; ++j) {
+    const int e = exp_plus1(x[j * plane_stride]);
+    if (e == kExpNonFinite) nonfinite = true;
+    else if (e > e_entry) e_entry = e;
+  }
+}
+
+// ---- pass 1 ------------------------------------------------------------------
+// trans = 0: block = 256 threads along k of one row; grid (R, ceil(K/1024)).
+__global__ void exps_rows_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
+                                 int64_t ld, int64_t ps, int *Eb, int *eminb,
+                                 unsigned int *status) {
+  const int64_t r = blockIdx.x;
+  int emax = kExpZero, emin = -kExpZero;
+  bool bad = false;
+  for (int64_t k = blockIdx.y * (int64_t)blockDim.x * 4 + threadIdx.x;
+       k < K && k < (blockIdx.y + 1) * (int64_t)blockDim.x * 4; k += blockDim.x) {
+    int e;
+    entry_exps(X + r * ld + k, ps, m, e, bad);
+    if (e != kExpZero) {
+      emax = max(emax, e);
+      emin = min(emin, e);
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+  }
+  if (bad) raise_status(status, MW_ENONFINITE);
+  if ((threadIdx.x & 31) == 0 && emax != kExpZero) {
+    atomicMax(Eb + r, emax + kBias);
+    atomicMax(eminb + r, kBias - emin);
+  }
+}
+
+// trans = 1: block = 32 (r) x 8 (k) threads; each block covers 32 columns and
+// kRowsPerBlock rows of the stored K x R matrix.
+constexpr int kRowsPerBlock = 256;
+__global__ void exps_cols_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
+                                 int64_t ld, int64_t ps, int *Eb, int *eminb,
+                                 unsigned int *status) {
+  __shared__ int smax[8][32], smin[8][32];
+  const int64_t r = blockIdx.x * 32 + threadIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.y * kRowsPerBlock;
+  int emax = kExpZero, emin = -kExpZero;
+  bool bad = false;
+  if (r < R) {
+    for (int64_t k = k0 + threadIdx.y; k < K && k < k0 + kRowsPerBlock; k += 8) {
+      int e;
+      entry_exps(X + k * ld + r, ps, m, e, bad);
+      if (e != kExpZero) {
+        emax = max(emax, e);
+        emin = min(emin, e);
+      }
+    }
+  }
+  if (bad) raise_status(status, MW_ENONFINITE);
+  smax[threadIdx.y][threadIdx.x] = emax;
+  smin[threadIdx.y][threadIdx.x] = emin;
+  __syncthreads();
+  if (threadIdx.y == 0 && r < R) {
+    for (int i = 1; i < 8; ++i) {
+      emax = max(emax, smax[i][threadIdx.x]);
+      emin = min(emin, smin[i][threadIdx.x]);
+    }
+    if (emax != kExpZero) {
+      atomicMax(Eb + r, emax + kBias);
+      atomicMax(eminb + r, kBias - emin);
+    }
+  }
+}
+
+__global__ void exps_finalize_kernel(int64_t R, int *E, int *spread, int *max_spread, int range,
+                                     unsigned int *status) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int eb = E[r], mb = spread[r];
+  const int Er = eb > 0 ? eb - kBias : 0;
+  const int sp = eb > 0 ? Er - (kBias - mb) : 0;
+  E[r] = Er;
+  spread[r] = sp;
+  if (max_spread) atomicMax(max_spread, sp);
+  if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
+}
+
+// ---- pass 2 ------------------------------------------------------------------
+// Fixed-point value of one entry in NL limbs (two's complement, little endian).
+template <int NL>
+__device__ __forceinline__ void fixed_point(const double *w, int m, int F, uint64_t (&T)[NL]) {
+#pragma unroll
+  for (int i = 0; i < NL; ++i) T[i] = 0;
+  for (int j = 0; j < m; ++j) {
+    int e2;
+    bool neg;
+    uint64_t M = mantissa_of(w[j], e2, neg);
+    if (M == 0) continue;
+    const int sh = e2 + F;
+    uint64_t lo = 0, hi = 0;
+    int li = 0;
+    if (sh < 0) {
+      lo = (-sh) >= 64 ? 0 : (M >> (-sh));
+      li = 0;
+    } else {
+      li = sh >> 6;
+      const int off = sh & 63;
+      lo = M << off;
+      hi = off ? (M >> (64 - off)) : 0;
+    }
+    // T += (neg ? -1 : 1) * (hi:lo << 64*li), as T + (~V) + 1 when negative
+    uint64_t carry = neg ? 1 : 0;
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+      uint64_t a = (i == li) ? lo : ((i == li + 1) ? hi : 0);
+      if (neg) a = ~a;
+      const uint64_t s1 = T[i] + a;
+      const uint64_t c1 = s1 < a;
+      const uint64_t s2 = s1 + carry;
+      const uint64_t c2 = s2 < carry;
+      T[i] = s2;
+      carry = c1 | c2;
+    }
+  }
+}
+
+// Arithmetic right shift of the limbs by w (0 < w < 64).
+template <int NL>
+__device__ __forceinline__ void shr(uint64_t (&T)[NL], int w) {
+#pragma unroll
+  for (int i = 0; i < NL - 1; ++i) T[i] = (T[i] >> w) | (T[i + 1] << (64 - w));
+  T[NL - 1] = (uint64_t)((int64_t)T[NL - 1] >> w);
+}
+
+template <typename Out>
+__device__ __forceinline__ Out to_out(int d);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(int d) {
+  return __float2bfloat16_rn((float)d);  // |d| <= 2^(w-1) <= 256: exact
+}
+template <>
+__device__ __forceinline__ double to_out<double>(int d) { return (double)d; }
+
+template <typename Out>
+__device__ __forceinline__ void store2(Out *p, int d0, int d1);
+template <>
+__device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16 *p, int d0, int d1) {
+  __nv_bfloat162 v;
+  v.x = to_out<__nv_bfloat16>(d0);
+  v.y = to_out<__nv_bfloat16>(d1);
+  *reinterpret_cast<__nv_bfloat162 *>(p) = v;
+}
+template <>
+__device__ __forceinline__ void store2<double>(double *p, int d0, int d1) {
+  *reinterpret_cast<double2 *>(p) = make_double2((double)d0, (double)d1);
+}
+
+// Cut two entries (k, k+1 of one row) into S pieces and store them.
+template <int NL, typename Out>
+__device__ __forceinline__ void cut_pair(const double *w0, const double *w1, bool v0, bool v1,
+                                         int m, int F, int w, int S, Out *dst, int64_t plane,
+                                         unsigned int *status) {
+  uint64_t T0[NL], T1[NL];
+  double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  fixed_point<NL>(v0 ? w0 : z, m, F, T0);
+  fixed_point<NL>(v1 ? w1 : z, m, F, T1);
+  const uint64_t mask = (1ull << w) - 1;
+  const int half = 1 << (w - 1);
+  int c0 = 0, c1 = 0;
+  for (int p = S - 1; p >= 1; --p) {
+    int r0 = (int)(T0[0] & mask) + c0, r1 = (int)(T1[0] & mask) + c1;
+    c0 = r0 >= half;
+    c1 = r1 >= half;
+    r0 -= c0 << w;
+    r1 -= c1 << w;
+    store2<Out>(dst + p * plane, r0, r1);
+    shr<NL>(T0, w);
+    shr<NL>(T1, w);
+  }
+  // what is left is T >> w(S-1); T in [-2^(wS-1), 2^(wS-1)) <=> it lies in
+  // [-2^(w-1), 2^(w-1)) with all higher limbs the sign extension of limb 0
+  bool ok = true;
+  const int64_t t0 = (int64_t)T0[0], t1 = (int64_t)T1[0];
+#pragma unroll
+  for (int i = 1; i < NL; ++i) {
+    ok &= T0[i] == (uint64_t)(t0 >> 63);
+    ok &= T1[i] == (uint64_t)(t1 >> 63);
+  }
+  ok &= t0 >= -half && t0 < half && t1 >= -half && t1 < half;
+  if (!ok) raise_status(status, MW_ERANGE);
+  store2<Out>(dst, (int)t0 + c0, (int)t1 + c1);
+}
+
+// trans = 0: one thread per (row, pair of columns), pairs cover the padded width.
+template <int NL, typename Out>
+__global__ void pieces_rows_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
+                                   int64_t ld, int64_t ps, int w, int S, Out *digits,
+                                   int64_t dld, const int *E, unsigned int *status) {
+  const int64_t npair = dld / 2;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= R * npair) return;
+  const int64_t r = idx / npair, k = 2 * (idx % npair);
+  double a[8], b[8];
+  const bool v0 = k < K, v1 = k + 1 < K;
+  const double *row = X + r * ld;
+  const bool vec = v1 && ((((uintptr_t)(row + k)) & 15) == 0) && ((ps & 1) == 0);
+  for (int j = 0; j < m; ++j) {
+    if (vec) {
+      const double2 v = *reinterpret_cast<const double2 *>(row + j * ps + k);  // 128-bit load
+      a[j] = v.x;
+      b[j] = v.y;
+    } else {
+      a[j] = v0 ? row[j * ps + k] : 0.0;
+      b[j] = v1 ? row[j * ps + k + 1] : 0.0;
+    }
+  }
+  const int F = w * S - 2 - E[r];
+  cut_pair<NL, Out>(a, b, v0, v1, m, F, w, S, digits + r * dld + k, R * dld, status);
+}
+
+// trans = 1: 32 x 32 tiles (32 rows r, 32 columns k of the logical operand)
+// staged through shared memory as doubles (m planes), then cut like trans = 0.
+template <int NL, typename Out>
+__global__ void pieces_cols_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
+                                   int64_t ld, int64_t ps, int w, int S, Out *digits,
+                                   int64_t dld, const int *E, unsigned int *status) {
+  extern __shared__ double tile[];  // [m][32 k][33]
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int64_t r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < 4; ++i) {
+      const int kl = ty + 8 * i;
+      const int64_t k = k0 + kl, r = r0 + tx;
+      tile[(j * 32 + kl) * 33 + tx] = (k < K && r < R) ? X[j * ps + k * ld + r] : 0.0;
+    }
+  __syncthreads();
+  const int tid = ty * 32 + tx;
+  for (int it = 0; it < 2; ++it) {
+    const int e = tid + 256 * it;      // 512 pairs per tile
+    const int rl = e >> 4, kl = 2 * (e & 15);
+    const int64_t r = r0 + rl, k = k0 + kl;
+    if (r >= R || k >= dld) continue;
+    double a[8], b[8];
+    for (int j = 0; j < m; ++j) {
+      a[j] = tile[(j * 32 + kl) * 33 + rl];
+      b[j] = tile[(j * 32 + kl + 1) * 33 + rl];
+    }
+    const int F = w * S - 2 - E[r];
+    cut_pair<NL, Out>(a, b, k < K, k + 1 < K, m, F, w, S, digits + r * dld + k, R * dld, status);
+  }
+}
+
+template <typename Out, int NL>
+int launch_pieces(const SplitArgs &a, cudaStream_t s) {
+  Out *dig = static_cast<Out *>(a.digits);
+  if (!a.trans) {
+    const int64_t n = a.R * (a.digit_ld / 2);
+    const int threads = 256;
+    pieces_rows_kernel<NL, Out><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        a.X, a.m, a.R, a.K, a.ld, a.plane_stride, a.w, a.S, dig, a.digit_ld, a.exps,
+        status_ptr());
+  } else {
+    dim3 grid((unsigned)((a.R + 31) / 32), (unsigned)((a.digit_ld + 31) / 32));
+    const size_t sm = (size_t)a.m * 32 * 33 * sizeof(double);
+    static bool attr_set = false;  // once per instantiation
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(pieces_cols_kernel<NL, Out>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           8 * 32 * 33 * (int)sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e, "split smem attribute");
+      attr_set = true;
+    }
+    pieces_cols_kernel<NL, Out><<<grid, dim3(32, 8), sm, s>>>(
+        a.X, a.m, a.R, a.K, a.ld, a.plane_stride, a.w, a.S, dig, a.digit_ld, a.exps,
+        status_ptr());
+  }
+  return cuda_fail(cudaGetLastError(), "split pieces launch");
+}
+
+template <typename Out>
+int launch_pieces_nl(const SplitArgs &a, cudaStream_t s) {
+  const int bits = a.w * a.S + 3;  // |T| < m 2^(wS-2) < 2^(wS+1), one sign bit
+  if (bits <= 128) return launch_pieces<Out, 2>(a, s);
+  if (bits <= 256) return launch_pieces<Out, 4>(a, s);
+  if (bits <= 384) return launch_pieces<Out, 6>(a, s);
+  if (bits <= 512) return launch_pieces<Out, 8>(a, s);
+  if (bits <= 640) return launch_pieces<Out, 10>(a, s);
+  return fail(MW_EUNSUPPORTED, "w*S = %d too large (at most 637 bits)", a.w * a.S);
+}
+
+}  // namespace
+
+int launch_split(const SplitArgs &a, bool exponents_only, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.exps, 0, sizeof(int32_t) * a.R, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.spread, 0, sizeof(int32_t) * a.R, s);
+  if (e != cudaSuccess) return cuda_fail(e, "split memset");
+  if (!a.trans) {
+    dim3 grid((unsigned)a.R, (unsigned)((a.K + 1023) / 1024));
+    exps_rows_kernel<<<grid, 256, 0, s>>>(a.X, a.m, a.R, a.K, a.ld, a.plane_stride, a.exps,
+                                          a.spread, status_ptr());
+  } else {
+    dim3 grid((unsigned)((a.R + 31) / 32), (unsigned)((a.K + kRowsPerBlock - 1) / kRowsPerBlock));
+    exps_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(a.X, a.m, a.R, a.K, a.ld, a.plane_stride,
+                                                  a.exps, a.spread, status_ptr());
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split exponent launch");
+  exps_finalize_kernel<<<(unsigned)((a.R + 255) / 256), 256, 0, s>>>(
+      a.R, a.exps, a.spread, a.max_spread, a.range, status_ptr());
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split finalize launch");
+  if (exponents_only) return MW_OK;
+  if (a.format == MW_DIGITS_BF16) return launch_pieces_nl<__nv_bfloat16>(a, s);
+  return launch_pieces_nl<double>(a, s);
+}
+
+}  // namespace mw

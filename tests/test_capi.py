@@ -1,0 +1,123 @@
+"""The C interface on the CPU: the library loads, exports every entry point of
+include/mw.h, rejects bad arguments on the host, and its planner's slice counts
+meet the error bound when the oracle runs the method with them."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_2606_20863_gb300", "libmw.so")
+
+
+@pytest.fixture(scope="module")
+def mw():
+    if not os.path.exists(LIB):
+        import __graft_entry__
+        __graft_entry__.build()
+    import paper_2606_20863_gb300 as mw
+    return mw
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "mw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mw_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(mw):
+    lib = ctypes.CDLL(LIB)
+    names = declared_entry_points()
+    assert "mw_gemm" in names and "mw_split" in names and "mw_gemm_backward" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(mw.EXPORTED) <= set(names)
+
+
+def test_version(mw):
+    assert "sm_103a" in mw.version()
+
+
+@pytest.mark.parametrize("m", [2, 4, 8])
+@pytest.mark.parametrize("mode", ["ozaki", "plain"])
+def test_plan_constraints(mw, m, mode):
+    for K in (1, 7, 64, 1024, 4096, 65536):
+        for ra, rb in ((0, 0), (16, 16), (40, 40), (3, 60)):
+            p = mw.mw_plan_gemm(m, mode, 100, 100, K, ra, rb)
+            lgK = math.log2(K)
+            # truncation of each operand within a quarter of the budget
+            assert p.w * p.S_A >= 52 * m + ra + math.log2(m) + 5 - lgK - 1e-9
+            assert p.w * p.S_B >= 52 * m + rb + math.log2(m) + 5 - lgK - 1e-9
+            S_min = min(p.S_A, p.S_B)
+            if p.D < p.S_A + p.S_B - 1:
+                assert p.w * p.D >= 52 * m + ra + rb + math.log2(S_min) + 6 - lgK - 1e-9
+            if mode == "ozaki":
+                assert p.w == 8 and p.chunk * 2 ** (2 * p.w - 2) <= 2 ** 22
+                max_s = S_min * K * 2 ** (2 * p.w - 2)
+                assert max_s * 2 ** (p.w * (p.group - 1)) * (1 + 2 ** (1 - p.w)) < 2 ** 63
+            else:
+                assert S_min * K * 2 ** (2 * p.w - 2) <= 2 ** 53
+
+
+def test_host_side_errors(mw):
+    with pytest.raises(mw.MWError):
+        mw.mw_plan_gemm(3, "ozaki", 10, 10, 10, 0, 0)
+    with pytest.raises(mw.MWError):
+        mw.mw_plan_gemm(2, "ozaki", 0, 10, 10, 0, 0)
+    with pytest.raises(mw.MWError):
+        mw.mw_plan_gemm(2, "ozaki", 10, 10, 10, -1, 0)
+    p = mw.mw_plan_gemm(2, "ozaki", 64, 64, 64, 0, 0)
+    p.group = 99
+    with pytest.raises(mw.MWError):
+        mw.workspace_size(p, 64, 64, 64)
+    p = mw.mw_plan_gemm(2, "plain", 64, 64, 64, 0, 0)
+    p.w = 26
+    with pytest.raises(mw.MWError):           # FP64 sums no longer exact
+        mw.workspace_size(p, 64, 64, 64)
+    # a NULL operand is refused before any GPU work
+    p = mw.mw_plan_gemm(2, "ozaki", 8, 8, 8, 0, 0)
+    rc = mw._lib.mw_gemm(ctypes.byref(p), 0, 0, 8, 8, 8, None, 8, 64, None, 8, 64, None, 8, 64,
+                         None, 0, None)
+    assert rc == mw.MW_EINVAL
+    assert "NULL" in mw._lib.mw_last_error().decode()
+
+
+def test_workspace_layout_is_consistent(mw):
+    p = mw.mw_plan_gemm(4, "ozaki", 300, 200, 1000, 10, 10)
+    off, total = mw.workspace_layout(p, 300, 200, 1000)
+    Kp = 1024
+    assert off[0] == 0 and off[1] >= 4 * (2 * 300 + 2 * 200 + 2)
+    assert off[2] - off[1] >= p.S_A * 300 * Kp * 2
+    assert off[3] - off[2] >= p.S_B * 200 * Kp * 2
+    G = -(-p.D // p.group)
+    assert total - off[3] >= G * 3 * 2 * 128 * 128 * 8
+    assert total == mw.workspace_size(p, 300, 200, 1000)
+    assert all(o % 256 == 0 for o in off)
+
+
+@pytest.mark.parametrize("m,mode,lo,hi", [(2, "ozaki", -20, 20), (2, "plain", -8, 8),
+                                          (4, "ozaki", -8, 8)])
+def test_planner_meets_bound_on_the_oracle(mw, m, mode, lo, hi):
+    """The plan computed from the measured spreads gives errors within the bound
+    when the CPU oracle carries out the method with it, including operands
+    built so that small entries of A meet large entries of B."""
+    from oracle import exact, slicing
+    from synthetic import SplitMix64, loguniform_mdouble
+    rng = SplitMix64(90 + m)
+    n = 20
+    A = loguniform_mdouble(rng, m, n, n, lo, hi)
+    B = loguniform_mdouble(rng, m, n, n, lo, hi)
+    # adversarial: row 0 of A tiny except one huge entry; column 0 of B the mirror
+    A[:, 0, 1:] *= 2.0 ** (lo - hi)
+    A[:, 0, 0] = loguniform_mdouble(rng, m, 1, 1, hi - 1, hi)[:, 0, 0]
+    B[:, 0, 0] *= 2.0 ** (lo - hi)
+    ra = int(slicing.row_exponents(A)[1].max())
+    rb = int(slicing.row_exponents(slicing.logical(B, True))[1].max())
+    p = mw.mw_plan_gemm(m, mode, n, n, n, ra, rb)
+    sp = slicing.SlicedProduct(A, B, p.w, p.S_A, p.S_B, p.D)
+    assert sp.A.in_range and sp.B.in_range
+    ratio = exact.exact_product_full(A, B).error_ratio(sp.result())
+    assert ratio.max() <= 1.0
