@@ -1,0 +1,292 @@
+#!/usr/bin/env python
+"""Benchmark of the m-double matrix product on GB300.
+
+Workload: quad-double C = A B, M = N = K = 1024, every leading word of
+magnitude 2^U[-8, 8) with a random sign and lower words scaled by 2^-53 U[-1,1)
+(seed 1).  One step is the whole product through the C interface: exponents
+and pieces of both operands, the tensor-core slice products with their exact
+int64 drains, and the exact fusion into four words (MW_OZAKI).  The plain FP64
+form of the paper (MW_PLAIN) is timed on the same operands and the same error
+bound for the comparison the metric asks for.
+
+Printed: one JSON line (rank 0).  value = m-double GFLOP/s = 2 M N K / time,
+summed over ranks (each rank a replica).  L2 is flushed (a 256 MiB write)
+before every timed step; steps are timed with CUDA events on the stream the
+library launches on.  `--impl reference` times the CPU oracle (textbook
+m-double product, all host cores) on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "m-double GEMM GFLOP/s (dd,qd) Ozaki-INT8 vs FP64 plain, same error bound"
+WORKLOAD = ("quad-double GEMM C=A*B, M=N=K=1024, leading words 2^U[-8,8) random sign, "
+            "lower words x2^-53 U[-1,1), seed 1")
+M_WORDS, N_DIM = 4, 1024
+KERNELS_PER_STEP = 8   # per operand: exponent, finalize, pieces (x2); product; combine
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mw", choices=["mw", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--cpu-rows", type=int, default=0, help="rows in the CPU sample (0 = auto)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    import torch
+    import torch.distributed as dist
+    if n > 1 or "WORLD_SIZE" in os.environ and int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        dist.init_process_group("nccl")
+        rank = dist.get_rank()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        return dist, rank, dist.get_world_size()
+    return None, 0, 1
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), d.get("hbm_gbs"), "measured"
+    return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs():
+    from synthetic import qd_1024
+    return qd_1024(seed=1, n=N_DIM)
+
+
+def cpu_baseline(A, B, rows, label):
+    """The oracle's textbook m-double product on a bounded row sample."""
+    from oracle import textbook
+    tc = textbook.TextbookC()
+    threads = tc.max_threads()
+    sel = np.linspace(0, A.shape[1] - 1, rows).astype(np.int64)
+    t0 = time.perf_counter()
+    tc.gemm(A, B, rows=sel, threads=threads)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * rows * B.shape[2] * A.shape[2]
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"{rows} of {A.shape[1]} rows of C ({label}), {dt:.2f} s"}
+
+
+def auto_rows(A, B, target_s=12.0):
+    from oracle import textbook
+    tc = textbook.TextbookC()
+    t0 = time.perf_counter()
+    tc.gemm(A, B, rows=[0], threads=1)
+    one = time.perf_counter() - t0
+    return int(max(tc.max_threads(), min(A.shape[1], target_s * tc.max_threads() / max(one, 1e-6))))
+
+
+def run_reference(args):
+    dist, rank, world = None, 0, 1
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return
+    A, B = make_inputs()
+    rows = args.cpu_rows or auto_rows(A, B, target_s=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        cpu_baseline(A, B, max(1, rows // 8), "warm-up")
+    vals = [cpu_baseline(A, B, rows, "quad double") for _ in range(args.steps)]
+    dt = statistics.mean(2.0 * rows * N_DIM * N_DIM / (v["value"] * 1e9) for v in vals)
+    value = statistics.mean(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M_WORDS, "M": N_DIM, "N": N_DIM, "K": N_DIM,
+                       "form": "textbook m-double (two-sum, Dekker two-product), CPU oracle"},
+            "cpu_baseline": vals[-1],
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2606_20863_gb300 as mw
+
+    dist, rank, world = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A, B = make_inputs()
+    tA = torch.from_numpy(A).to(dev)
+    tB = torch.from_numpy(B).to(dev)
+    M = N = K = N_DIM
+    flops = 2.0 * M * N * K
+
+    plan = mw.plan_for(tA, tB, "ozaki")
+    ws = torch.empty(mw.workspace_size(plan, M, N, K), dtype=torch.uint8, device=dev)
+    C = torch.empty((M_WORDS, M, N), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    pairs = sum(1 for t in range(plan.D) for p in range(plan.S_A) if 0 <= t - p < plan.S_B)
+
+    def step():
+        mw.mw_gemm(tA, tB, plan, C=C, ws=ws, check=False)
+
+    for _ in range(args.warmup):
+        step()
+    mw.check_status()
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = Clocks(dev.index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for s in range(args.steps):
+        flush.fill_(float(s))                                  # untimed L2 flush
+        mw.set_phase_events(ev[s])
+        step()
+    mw.set_phase_events(None)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    mw.check_status()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    kern_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    t_step = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = world * flops * args.steps / t_step / 1e9
+
+    # plain FP64 form on the same operands and bound (the comparison of the metric)
+    pplan = mw.plan_for(tA, tB, "plain")
+    pws = torch.empty(mw.workspace_size(pplan, M, N, K), dtype=torch.uint8, device=dev)
+    Cp = torch.empty_like(C)
+    mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws)
+    pe = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.plain_steps)]
+    for s in range(args.plain_steps):
+        flush.fill_(float(s))
+        pe[2 * s].record()
+        mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws, check=False)
+        pe[2 * s + 1].record()
+    torch.cuda.synchronize()
+    mw.check_status()
+    plain_s = sum(pe[2 * s].elapsed_time(pe[2 * s + 1]) for s in range(args.plain_steps)) / 1e3
+    plain_gflops = flops * args.plain_steps / plain_s / 1e9
+    del pws, Cp
+
+    # end to end through the public call: pinned host operands in, host result out
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.empty((M_WORDS, M, N), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dA = hA.to(dev, non_blocking=True)
+        dB = hB.to(dev, non_blocking=True)
+        out = mw.mw_gemm(dA, dB, mode="ozaki", check=False)   # plans from the data (synchronizes)
+        hC.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
+           "d2h_bytes_per_step": int(hC.numel() * 8)}
+
+    bf16_burst, bf16_sust, hbm, peak_src = load_peaks()
+    kern_s = statistics.mean(kern_ms) / 1e3
+    achieved = pairs * flops / kern_s / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
+                "frac": achieved / bf16_burst, "traffic": None,
+                "kernel": "ozaki_kernel (tcgen05 kind::f16, bf16 integer slices)",
+                "peak_source": f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json)",
+                "algorithmic": f"{pairs} slice pairs x 2MNK = {pairs * flops:.3e} flop per launch"}
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M_WORDS, "M": M, "N": N, "K": K,
+                       "form": "Ozaki: bf16 integer slices on tcgen05, fp32 drained to int64",
+                       "plan": plan.as_dict(), "slice_pairs": pairs,
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "plain_fp64_gflops": plain_gflops, "plain_plan": pplan.as_dict(),
+                       "speedup_vs_plain": value / world / plain_gflops,
+                       "product_kernel_ms": kern_s * 1e3,
+                       "step_ms_min": min(step_ms)},
+            "roofline": roofline, "clocks": clk, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * args.steps}
+    if rank == 0 and not args.no_cpu:
+        rows = args.cpu_rows or auto_rows(A, B)
+        line["cpu_baseline"] = cpu_baseline(A, B, rows, "quad double")
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -166,6 +166,13 @@ int mw_gemm_backward(const mw_plan *plan_dA, const mw_plan *plan_dB,
                      double *dB, int64_t lddb, int64_t plane_stride_db,
                      void *ws, size_t ws_bytes, mw_stream_t stream);
 
+/* Profiling hook: while set, every mw_gemm records events[0] on its stream
+ * before the first launch, events[1] after the pieces are cut (before the
+ * product kernel), events[2] after the product kernel and events[3] after the
+ * last launch.  events are cudaEvent_t created by the caller; pass NULL (or
+ * n = 0) to stop.  Process-wide setting, not thread safe. */
+int mw_set_phase_events(void *const *events, int n);
+
 /* Read the device status word of the current device (synchronizes the device);
  * clear != 0 resets it to zero afterwards. */
 int mw_get_status(int *bits, int clear);

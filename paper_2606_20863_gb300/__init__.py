@@ -67,6 +67,7 @@ def _load():
         "mw_gemm_backward": [pp, pp, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
                              vp, i64, i64, vp, i64, i64, vp, ctypes.c_size_t, vp],
         "mw_get_status": [ip, i32],
+        "mw_set_phase_events": [ctypes.POINTER(ctypes.c_void_p), i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -82,7 +83,7 @@ LIB_PATH = _LIB_PATH
 EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_workspace_layout",
             "mw_gemm",
             "mw_measure_spread", "mw_gemm_backward", "mw_get_status", "mw_last_error",
-            "mw_version")
+            "mw_version", "mw_set_phase_events")
 
 
 def _check(rc: int, what: str):
@@ -105,6 +106,16 @@ def _mat(X: torch.Tensor, name: str):
     if X.stride(2) != 1:
         raise MWError(f"{name}: last dimension must be contiguous")
     return ctypes.c_void_p(X.data_ptr()), X.stride(1), X.stride(0)
+
+
+def set_phase_events(events=None):
+    """Record torch.cuda.Event objects (4 of them) between the phases of every
+    mw_gemm: before the pieces, before the product kernel, after it, at the end."""
+    if events is None:
+        _check(_lib.mw_set_phase_events(None, 0), "mw_set_phase_events")
+        return
+    arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _check(_lib.mw_set_phase_events(arr, 4), "mw_set_phase_events")
 
 
 def get_status(clear: bool = True) -> int:

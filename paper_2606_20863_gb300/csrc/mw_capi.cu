@@ -17,6 +17,12 @@ __device__ unsigned int g_status_word;  // MW_* bits raised by kernels of this d
 constexpr int kMaxDevices = 64;
 unsigned int *g_status_addr[kMaxDevices] = {nullptr};
 std::mutex g_status_mu;
+cudaEvent_t g_phase[4] = {nullptr, nullptr, nullptr, nullptr};
+bool g_phase_on = false;
+
+void phase(int i, cudaStream_t s) {
+  if (g_phase_on && g_phase[i]) cudaEventRecord(g_phase[i], s);
+}
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -131,6 +137,17 @@ extern "C" {
 const char *mw_last_error(void) { return g_msg.c_str(); }
 
 const char *mw_version(void) { return "mw 0.1 (sm_103a, tcgen05 bf16 slices, fp64 pieces)"; }
+
+int mw_set_phase_events(void *const *events, int n) {
+  if (!events || n <= 0) {
+    g_phase_on = false;
+    return MW_OK;
+  }
+  if (n < 4) return fail(MW_EINVAL, "need 4 events");
+  for (int i = 0; i < 4; ++i) g_phase[i] = static_cast<cudaEvent_t>(events[i]);
+  g_phase_on = true;
+  return MW_OK;
+}
 
 int mw_get_status(int *bits, int clear) {
   if (!bits) return fail(MW_EINVAL, "bits is NULL");
@@ -300,10 +317,12 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
   if (!ws || ws_bytes < L.total)
     return fail(MW_ENOSPC, "workspace %zu bytes, need %zu", ws_bytes, L.total);
   cudaStream_t s = (cudaStream_t)stream;
+  phase(0, s);
   cudaError_t e = cudaMemsetAsync(ops_in(ws, M, N).maxsp, 0, 2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "mw_gemm memset");
   if ((rc = split_both(p, transA, transB, M, N, K, A, lda, psa, B, ldb, psb, ws, L, false, s)))
     return rc;
+  phase(1, s);
   Operands o = ops_in(ws, M, N);
   uint8_t *w8 = static_cast<uint8_t *>(ws);
   if (p.mode == MW_PLAIN) {
@@ -313,7 +332,10 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
     a.dA = reinterpret_cast<const double *>(w8 + L.digA);
     a.dB = reinterpret_cast<const double *>(w8 + L.digB);
     a.eA = o.eA; a.eB = o.eB; a.C = C; a.ldc = ldc; a.psc = psc;
-    return launch_plain(a, s);
+    rc = launch_plain(a, s);
+    phase(2, s);
+    phase(3, s);
+    return rc;
   }
   OzakiArgs a{};
   a.m = p.m; a.w = p.w; a.S_A = p.S_A; a.S_B = p.S_B; a.D = p.D; a.group = p.group;
@@ -321,7 +343,9 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
   a.dA = w8 + L.digA; a.dB = w8 + L.digB; a.eA = o.eA; a.eB = o.eB;
   a.partials = reinterpret_cast<int64_t *>(w8 + L.partials);
   a.C = C; a.ldc = ldc; a.psc = psc;
-  return launch_ozaki(a, s);
+  rc = launch_ozaki(a, s, [&] { phase(2, s); });
+  phase(3, s);
+  return rc;
 }
 
 int mw_measure_spread(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,

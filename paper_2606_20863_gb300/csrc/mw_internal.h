@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <functional>
+
 #include "../../include/mw.h"
 
 namespace mw {
@@ -48,7 +50,8 @@ struct OzakiArgs {
   double *C;
   int64_t ldc, psc;
 };
-int launch_ozaki(const OzakiArgs &a, cudaStream_t s);
+// between_kernels runs after the product kernel is launched, before the combine.
+int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels);
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group);
 
 // Number of diagonal groups.

@@ -503,7 +503,7 @@ size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group) {
   return (size_t)n_groups(D, group) * tm * tn * BM * BN * sizeof(int64_t);
 }
 
-int launch_ozaki(const OzakiArgs &a, cudaStream_t s) {
+int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels) {
   if (a.Kp % BK) return fail(MW_EINVAL, "padded K must be a multiple of %d", BK);
   if (a.chunk < BK || a.chunk % BK) return fail(MW_EINVAL, "chunk must be a positive multiple of 64");
   if (a.w < 2 || a.w > 8 || (int64_t)a.chunk << (2 * a.w - 2) > (1 << 22))
@@ -554,6 +554,7 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s) {
   const int grid = std::min(P.units, nsm);
   ozaki_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, P);
   if ((rc = cuda_fail(cudaGetLastError(), "ozaki kernel launch"))) return rc;
+  if (between_kernels) between_kernels();
   switch (a.m) {
     case 2: return launch_combine_nl<2>(a, P.tiles_m, P.tiles_n, G, s);
     case 4: return launch_combine_nl<4>(a, P.tiles_m, P.tiles_n, G, s);
