@@ -114,6 +114,9 @@ def set_phase_events(events=None):
     if events is None:
         _check(_lib.mw_set_phase_events(None, 0), "mw_set_phase_events")
         return
+    for e in events:            # torch creates the CUDA event on its first record
+        if not e.cuda_event:
+            e.record()
     arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
     _check(_lib.mw_set_phase_events(arr, 4), "mw_set_phase_events")
 
