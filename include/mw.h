@@ -144,6 +144,26 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
             double *C, int64_t ldc, int64_t plane_stride_c,
             void *ws, size_t ws_bytes, mw_stream_t stream);
 
+/* mw_gemm for callers that cannot allocate device memory.  The paper has no
+ * counterpart; it exists for callers such as a plug-in inside a host program
+ * that owns all device memory through its own pool (a framework's caching
+ * allocator, a server with a fixed memory budget) and may not call cudaMalloc,
+ * which synchronizes the device and takes memory the host does not account for.
+ * Same arguments and result as mw_gemm without ws/ws_bytes: the workspace is a
+ * fixed 32 MiB array that the library reserves on every device it is loaded on
+ * and holds until the process exits; no memory is allocated or freed by the
+ * call.  Products whose mw_gemm_workspace_size exceeds 32 MiB are rejected with
+ * MW_ENOSPC (and a message) before any GPU work.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the array and leaves its contents behind (mw_gemm itself
+ * clears what must start at zero); calls whose work overlaps on the GPU race
+ * on it, so order them on one stream or otherwise serialise them. */
+int mw_gemm_noalloc(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, int64_t K,
+                    const double *A, int64_t lda, int64_t plane_stride_a,
+                    const double *B, int64_t ldb, int64_t plane_stride_b,
+                    double *C, int64_t ldc, int64_t plane_stride_c, mw_stream_t stream);
+
 /* Exponent spreads (max over rows of op(A), columns of op(B)) measured on the
  * GPU; synchronizes the stream.  ws as for mw_gemm with any plan of this m
  * (only 2 * (M + N + 1) int32 are used).  Feed the results to mw_plan_gemm. */

@@ -62,6 +62,8 @@ def _load():
                                      ctypes.POINTER(ctypes.c_size_t)],
         "mw_gemm": [pp, i32, i32, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
                     vp, ctypes.c_size_t, vp],
+        "mw_gemm_noalloc": [pp, i32, i32, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64,
+                            i64, vp],
         "mw_measure_spread": [i32, i32, i32, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp,
                               ctypes.c_size_t, ip, ip, vp],
         "mw_gemm_backward": [pp, pp, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
@@ -83,7 +85,7 @@ LIB_PATH = _LIB_PATH
 EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_workspace_layout",
             "mw_gemm",
             "mw_measure_spread", "mw_gemm_backward", "mw_get_status", "mw_last_error",
-            "mw_version", "mw_set_phase_events")
+            "mw_version", "mw_set_phase_events", "mw_gemm_noalloc")
 
 
 def _check(rc: int, what: str):
@@ -241,6 +243,22 @@ def mw_gemm(A: torch.Tensor, B: torch.Tensor, plan: mw_plan | None = None, mode=
                         _stream()), "mw_gemm")
     if check:
         check_status()
+    return C
+
+
+def mw_gemm_noalloc(A: torch.Tensor, B: torch.Tensor, plan: mw_plan, transA=False,
+                    transB=False, C: torch.Tensor | None = None) -> torch.Tensor:
+    """mw_gemm without a workspace argument, for callers that cannot allocate
+    device memory: the library's fixed per-device scratch (32 MiB) is used;
+    larger products raise.  C, if given, must be preallocated by the caller."""
+    m, M, N, K = _dims(A, B, transA, transB)
+    if C is None:
+        C = torch.empty((m, M, N), dtype=torch.float64, device=A.device)
+    pa, lda, psa = _mat(A, "A")
+    pb, ldb, psb = _mat(B, "B")
+    pc, ldc, psc = _mat(C, "C")
+    _check(_lib.mw_gemm_noalloc(ctypes.byref(plan), int(transA), int(transB), M, N, K, pa, lda,
+                                psa, pb, ldb, psb, pc, ldc, psc, _stream()), "mw_gemm_noalloc")
     return C
 
 

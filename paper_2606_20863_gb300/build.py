@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmw.so")
-SOURCES = ["mw_capi.cu", "mw_split.cu", "mw_plain.cu", "mw_ozaki.cu"]
+SOURCES = ["mw_capi.cu", "mw_split.cu", "mw_plain.cu", "mw_ozaki.cu", "mw_noalloc.cu"]
 HEADERS = ["mw_device.cuh", "mw_internal.h", os.path.join("..", "..", "include", "mw.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
