@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mw", choices=["mw", "reference"])
-    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--plain-steps", type=int, default=2,
+                    help="timed runs of the plain FP64 form (0 = leave it out)")
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="end-to-end runs from host memory (-1 = steps/4, at least 3; 0 = leave out)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows in the CPU sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     return ap.parse_args()
@@ -222,38 +225,42 @@ def main():
 
     # plain FP64 form on the same operands and bound (the comparison of the metric)
     pplan = mw.plan_for(tA, tB, "plain")
-    pws = torch.empty(mw.workspace_size(pplan, M, N, K), dtype=torch.uint8, device=dev)
-    Cp = torch.empty_like(C)
-    mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws)
-    pe = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.plain_steps)]
-    for s in range(args.plain_steps):
-        flush.fill_(float(s))
-        pe[2 * s].record()
-        mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws, check=False)
-        pe[2 * s + 1].record()
-    torch.cuda.synchronize()
-    mw.check_status()
-    plain_s = sum(pe[2 * s].elapsed_time(pe[2 * s + 1]) for s in range(args.plain_steps)) / 1e3
-    plain_gflops = flops * args.plain_steps / plain_s / 1e9
-    del pws, Cp
+    plain_gflops = None
+    if args.plain_steps > 0:
+        pws = torch.empty(mw.workspace_size(pplan, M, N, K), dtype=torch.uint8, device=dev)
+        Cp = torch.empty_like(C)
+        mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws)
+        pe = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.plain_steps)]
+        for s in range(args.plain_steps):
+            flush.fill_(float(s))
+            pe[2 * s].record()
+            mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws, check=False)
+            pe[2 * s + 1].record()
+        torch.cuda.synchronize()
+        mw.check_status()
+        plain_s = sum(pe[2 * s].elapsed_time(pe[2 * s + 1]) for s in range(args.plain_steps)) / 1e3
+        plain_gflops = flops * args.plain_steps / plain_s / 1e9
+        del pws, Cp
 
     # end to end through the public call: pinned host operands in, host result out
-    hA = torch.from_numpy(A).pin_memory()
-    hB = torch.from_numpy(B).pin_memory()
-    hC = torch.empty((M_WORDS, M, N), dtype=torch.float64).pin_memory()
-    e2e_steps = max(3, args.steps // 4)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        dA = hA.to(dev, non_blocking=True)
-        dB = hB.to(dev, non_blocking=True)
-        out = mw.mw_gemm(dA, dB, mode="ozaki", check=False)   # plans from the data (synchronizes)
-        hC.copy_(out, non_blocking=True)
+    e2e_steps = args.e2e_steps if args.e2e_steps >= 0 else max(3, args.steps // 4)
+    e2e = None
+    if e2e_steps > 0:
+        hA = torch.from_numpy(A).pin_memory()
+        hB = torch.from_numpy(B).pin_memory()
+        hC = torch.empty((M_WORDS, M, N), dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
-           "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
-           "d2h_bytes_per_step": int(hC.numel() * 8)}
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            dA = hA.to(dev, non_blocking=True)
+            dB = hB.to(dev, non_blocking=True)
+            out = mw.mw_gemm(dA, dB, mode="ozaki", check=False)  # plans from the data (synchronizes)
+            hC.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
+               "d2h_bytes_per_step": int(hC.numel() * 8)}
 
     bf16_burst, bf16_sust, hbm, peak_src = load_peaks()
     kern_s = statistics.mean(kern_ms) / 1e3
@@ -274,7 +281,7 @@ def main():
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "plain_fp64_gflops": plain_gflops, "plain_plan": pplan.as_dict(),
-                       "speedup_vs_plain": value / world / plain_gflops,
+                       "speedup_vs_plain": (value / world / plain_gflops) if plain_gflops else None,
                        "product_kernel_ms": kern_s * 1e3,
                        "step_ms_min": min(step_ms)},
             "roofline": roofline, "clocks": clk, "e2e": e2e,
