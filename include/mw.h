@@ -123,11 +123,9 @@ int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
  * offsets[1] pieces of op(A): S_A planes of M x Kp (Kp = K rounded up to 64),
  *            bfloat16 (MW_OZAKI) or double (MW_PLAIN), layout as in mw_split;
  * offsets[2] pieces of op(B)^T: S_B planes of N x Kp;
- * offsets[3] (MW_OZAKI) 64-bit partial sums: for group g of diagonals
- *            [g*group, min(D, (g+1)*group) - 1] and output tile (tm, tn) of
- *            128 x 128, entry (r, c) of the tile at
- *            ((g * tiles + tn * tiles_m + tm) * 128 + r) * 128 + c,
- *            V = sum_t s_t 2^(w (t1 - t)) over the group's diagonals.
+ * offsets[3] (MW_OZAKI) 64-bit partial sums [g][M][N]: entry (g, i, j) is
+ *            V = sum_t s_t 2^(w (t1 - t)) over the diagonals t of group g,
+ *            [g*group, t1 = min(D, (g+1)*group) - 1];
  * bytes = total workspace size (same as mw_gemm_workspace_size). */
 int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
                              size_t offsets[4], size_t *bytes);
@@ -163,6 +161,51 @@ int mw_gemm_noalloc(const mw_plan *plan, int transA, int transB, int64_t M, int6
                     const double *A, int64_t lda, int64_t plane_stride_a,
                     const double *B, int64_t ldb, int64_t plane_stride_b,
                     double *C, int64_t ldc, int64_t plane_stride_c, mw_stream_t stream);
+
+/* ---- batches of independent products (power-series coefficient convolutions,
+ * Section 1, come as many small products of uneven sizes) -------------------- */
+
+/* One product of a batch: C = A B, A M x K, B K x N, C M x N, every matrix m
+ * planes of row-major doubles in device memory (no transposes). */
+typedef struct mw_problem {
+  int64_t M, N, K;
+  const double *A;
+  int64_t lda, plane_stride_a;
+  const double *B;
+  int64_t ldb, plane_stride_b;
+  double *C;
+  int64_t ldc, plane_stride_c;
+} mw_problem;
+
+/* Host-side summary of a batch (sizes only); mw_batch_describe fills it. */
+typedef struct mw_batch {
+  int count;
+  int64_t sum_M, sum_N, sum_MN, max_M, max_N, min_K, max_K;
+} mw_batch;
+
+/* shapes: host array of count x {M, N, K}. Host only. */
+int mw_batch_describe(int count, const int64_t *shapes, mw_batch *batch);
+
+/* Bytes of device workspace for mw_gemm_batched with this plan (MW_OZAKI). */
+int mw_gemm_batched_workspace_size(const mw_plan *plan, const mw_batch *batch, size_t *bytes);
+
+/* Exponent spreads over all rows of the A_i and all columns of the B_i
+ * (synchronizes); input to mw_plan_gemm for the batch. */
+int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *problems,
+                              void *ws, size_t ws_bytes, int *range_A, int *range_B,
+                              mw_stream_t stream);
+
+/* C_i = A_i B_i for every problem of the batch in the Ozaki form, one plan for
+ * all (plan it with the smallest K of the batch for the error bound; its group
+ * must also fit the largest K).  problems: device array of batch->count
+ * descriptors.  Launches a short prologue (offsets of every problem's pieces
+ * and partial sums, computed on the GPU from the descriptors), one split of all
+ * operands, one persistent product kernel over (problem, tile, diagonal group)
+ * work items, one fusion; no host synchronisation, so the call can be captured
+ * in a CUDA graph and replayed while the descriptors and ws keep their
+ * addresses.  For load balance order the problems by decreasing size. */
+int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem *problems,
+                    void *ws, size_t ws_bytes, mw_stream_t stream);
 
 /* Exponent spreads (max over rows of op(A), columns of op(B)) measured on the
  * GPU; synchronizes the stream.  ws as for mw_gemm with any plan of this m

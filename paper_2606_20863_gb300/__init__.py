@@ -47,6 +47,18 @@ class mw_plan(ctypes.Structure):
         return "mw_plan(" + ", ".join(f"{k}={v}" for k, v in self.as_dict().items()) + ")"
 
 
+class mw_problem(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("plane_stride_a", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("plane_stride_b", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64), ("plane_stride_c", ctypes.c_int64)]
+
+
+class mw_batch(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int)] + [(n, ctypes.c_int64) for n in
+                ("sum_M", "sum_N", "sum_MN", "max_M", "max_N", "min_K", "max_K")]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"{_LIB_PATH} is missing: build it with "
@@ -69,6 +81,12 @@ def _load():
         "mw_gemm_backward": [pp, pp, i64, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
                              vp, i64, i64, vp, i64, i64, vp, ctypes.c_size_t, vp],
         "mw_get_status": [ip, i32],
+        "mw_batch_describe": [i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(mw_batch)],
+        "mw_gemm_batched_workspace_size": [pp, ctypes.POINTER(mw_batch),
+                                           ctypes.POINTER(ctypes.c_size_t)],
+        "mw_measure_spread_batched": [i32, ctypes.POINTER(mw_batch), vp, vp, ctypes.c_size_t,
+                                      ip, ip, vp],
+        "mw_gemm_batched": [pp, ctypes.POINTER(mw_batch), vp, vp, ctypes.c_size_t, vp],
         "mw_set_phase_events": [ctypes.POINTER(ctypes.c_void_p), i32],
     }
     for name, args in sig.items():
@@ -85,7 +103,8 @@ LIB_PATH = _LIB_PATH
 EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_workspace_layout",
             "mw_gemm",
             "mw_measure_spread", "mw_gemm_backward", "mw_get_status", "mw_last_error",
-            "mw_version", "mw_set_phase_events", "mw_gemm_noalloc")
+            "mw_version", "mw_set_phase_events", "mw_gemm_noalloc", "mw_batch_describe",
+            "mw_gemm_batched_workspace_size", "mw_measure_spread_batched", "mw_gemm_batched")
 
 
 def _check(rc: int, what: str):
@@ -102,12 +121,17 @@ def _stream():
 
 
 def _mat(X: torch.Tensor, name: str):
-    """(pointer, ld, plane_stride) of an (m, rows, cols) float64 CUDA tensor."""
+    """(pointer, ld, plane_stride) of an (m, rows, cols) float64 CUDA tensor whose
+    rows are contiguous (strides of dimensions of size 1 do not matter)."""
     if X.dtype != torch.float64 or X.dim() != 3 or not X.is_cuda:
         raise MWError(f"{name} must be a CUDA float64 tensor of shape (m, rows, cols)")
-    if X.stride(2) != 1:
+    rows, cols = X.shape[1], X.shape[2]
+    if cols > 1 and X.stride(2) != 1:
         raise MWError(f"{name}: last dimension must be contiguous")
-    return ctypes.c_void_p(X.data_ptr()), X.stride(1), X.stride(0)
+    ld = X.stride(1) if rows > 1 else cols
+    if ld < cols:
+        raise MWError(f"{name}: rows overlap (stride {ld} < {cols} columns)")
+    return ctypes.c_void_p(X.data_ptr()), ld, X.stride(0)
 
 
 def set_phase_events(events=None):
@@ -291,6 +315,87 @@ def mw_gemm_backward(A: torch.Tensor, B: torch.Tensor, G: torch.Tensor,
     if check:
         check_status()
     return dA, dB
+
+
+class Batch:
+    """A batch of independent products C_i = A_i B_i, every matrix an m-double
+    CUDA tensor (m, rows, cols).  Holds the device array of descriptors, the
+    plan and the workspace, so that ``run()`` can be captured in a CUDA graph
+    and replayed while the tensors keep their addresses."""
+
+    def __init__(self, As, Bs, Cs=None, plan: mw_plan | None = None):
+        if len(As) != len(Bs) or not As:
+            raise MWError("need equally many A and B, at least one")
+        self.m = As[0].shape[0]
+        dev = As[0].device
+        self.As, self.Bs = As, Bs
+        self.Cs = Cs if Cs is not None else [
+            torch.empty((self.m, a.shape[1], b.shape[2]), dtype=torch.float64, device=dev)
+            for a, b in zip(As, Bs)]
+        count = len(As)
+        host = (mw_problem * count)()
+        shapes = (ctypes.c_int64 * (3 * count))()
+        for i, (a, b, c) in enumerate(zip(As, Bs, self.Cs)):
+            if a.shape[2] != b.shape[1] or a.shape[0] != self.m or b.shape[0] != self.m:
+                raise MWError(f"problem {i}: shape mismatch")
+            pa, lda, psa = _mat(a, "A")
+            pb, ldb, psb = _mat(b, "B")
+            pc, ldc, psc = _mat(c, "C")
+            host[i] = mw_problem(a.shape[1], b.shape[2], a.shape[2], pa.value, lda, psa,
+                                 pb.value, ldb, psb, pc.value, ldc, psc)
+            shapes[3 * i:3 * i + 3] = [a.shape[1], b.shape[2], a.shape[2]]
+        self.batch = mw_batch()
+        _check(_lib.mw_batch_describe(count, shapes, ctypes.byref(self.batch)), "mw_batch_describe")
+        raw = torch.frombuffer(bytearray(ctypes.string_at(host, ctypes.sizeof(host))),
+                               dtype=torch.uint8)
+        self.d_problems = raw.to(dev)
+        if plan is None:
+            plan = self.plan()
+        self.plan_ = plan
+        n = ctypes.c_size_t(0)
+        _check(_lib.mw_gemm_batched_workspace_size(ctypes.byref(plan), ctypes.byref(self.batch),
+                                                   ctypes.byref(n)),
+               "mw_gemm_batched_workspace_size")
+        self.ws = _workspace(n.value, dev)
+
+    def measure_spread(self):
+        """Largest exponent spreads over the batch (synchronizes)."""
+        b = self.batch
+        need = 4096 + 200 * b.count + 16 * (b.sum_M + b.sum_N) + 4096
+        ws = _workspace(need, self.d_problems.device)
+        ra, rb = ctypes.c_int(0), ctypes.c_int(0)
+        _check(_lib.mw_measure_spread_batched(self.m, ctypes.byref(b),
+                                              ctypes.c_void_p(self.d_problems.data_ptr()),
+                                              ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                              ctypes.byref(ra), ctypes.byref(rb), _stream()),
+               "mw_measure_spread_batched")
+        return ra.value, rb.value
+
+    def plan(self) -> mw_plan:
+        """Plan for every problem: slice counts from the smallest K (tightest bound),
+        diagonal groups that fit the largest K."""
+        ra, rb = self.measure_spread()
+        b = self.batch
+        p = mw_plan_gemm(self.m, "ozaki", b.max_M, b.max_N, b.min_K, ra, rb)
+        p.group = min(p.group, mw_plan_gemm(self.m, "ozaki", b.max_M, b.max_N, b.max_K, ra,
+                                            rb).group)
+        return p
+
+    def run(self):
+        _check(_lib.mw_gemm_batched(ctypes.byref(self.plan_), ctypes.byref(self.batch),
+                                    ctypes.c_void_p(self.d_problems.data_ptr()),
+                                    ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                    _stream()), "mw_gemm_batched")
+        return self.Cs
+
+
+def mw_gemm_batched(As, Bs, Cs=None, plan: mw_plan | None = None, check: bool = True):
+    """C_i = A_i B_i for every i in one batched call (Ozaki form)."""
+    b = Batch(As, Bs, Cs, plan)
+    out = b.run()
+    if check:
+        check_status()
+    return out
 
 
 class MWGemm(torch.autograd.Function):

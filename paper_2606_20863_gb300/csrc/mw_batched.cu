@@ -1,0 +1,400 @@
+// mw_gemm_batched: many independent m-double products in the Ozaki form.
+//
+// The paper's application (Section 1) is power series, whose coefficient
+// convolutions are many small products of uneven sizes.  One call runs every
+// product of a batch with four launches, none of which needs the host to know
+// more than the batch's sums (mw_batch):
+//   1. prologue  (1 CTA): reads the device array of problem descriptors and
+//      computes, for every problem, where its pieces, exponents and partial
+//      sums live and which work items are its own (exclusive scans);
+//   2. split: one warp per row of an A_i or column of a B_i -- the shared
+//      exponent by a warp reduction, then the balanced pieces of the row;
+//   3. product: persistent CTAs walk the work items (problem, output tile,
+//      diagonal group) -- the kernel of the single product with the tile's
+//      coordinates looked up per item;
+//   4. fusion: one warp per output row, exact integer fusion and greedy
+//      rounding as for the single product.
+// The pieces of all problems share two row-major arrays of pitch Kpitch (the
+// largest K rounded up to 64), so one tensor map per operand covers the batch;
+// a tile that runs past a problem's last row reads the next rows, which only
+// feed output rows/columns that are never stored.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "mw_device.cuh"
+#include "mw_fuse.cuh"
+#include "mw_pieces.cuh"
+#include "mw_work.cuh"
+
+namespace mw {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+
+struct Layout {
+  size_t header, info, eA, spA, eB, spB, pieceA, pieceB, partials, total;
+  int64_t Kpitch;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout_of(const mw_plan &p, const mw_batch &b) {
+  Layout L{};
+  L.Kpitch = round_up(b.max_K, 64);
+  size_t off = 0;
+  L.header = off; off = a256(off + sizeof(BHeader));
+  L.info = off;   off = a256(off + sizeof(BInfo) * (size_t)b.count);
+  L.eA = off;     off = a256(off + 4 * (size_t)b.sum_M);
+  L.spA = off;    off = a256(off + 4 * (size_t)b.sum_M);
+  L.eB = off;     off = a256(off + 4 * (size_t)b.sum_N);
+  L.spB = off;    off = a256(off + 4 * (size_t)b.sum_N);
+  L.pieceA = off; off = a256(off + 2 * (size_t)p.S_A * b.sum_M * L.Kpitch);
+  L.pieceB = off; off = a256(off + 2 * (size_t)p.S_B * b.sum_N * L.Kpitch);
+  L.partials = off;
+  off = a256(off + 8 * (size_t)n_groups(p.D, p.group) * b.sum_MN);
+  L.total = off;
+  return L;
+}
+
+// ---- 1. prologue --------------------------------------------------------------
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t *sh) {
+  // 1024 threads: inclusive warp scans, then a scan of the 32 warp totals
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t t = sh[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sh[lane] = t;  // inclusive totals of warps 0..lane
+  }
+  __syncthreads();
+  const int64_t before = warp ? sh[warp - 1] : 0;
+  const int64_t total = sh[31];
+  __syncthreads();
+  sh[32] = total;
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs, int count,
+                                                        int G, int S_A, int S_B, int64_t Kpitch,
+                                                        mw_batch want, BInfo *info, BHeader *hdr,
+                                                        unsigned int *status) {
+  __shared__ int64_t sh[33];
+  int64_t cM = 0, cN = 0, cMN = 0, cW = 0;
+  int bad = 0;
+  for (int base = 0; base < count; base += 1024) {
+    const int i = base + threadIdx.x;
+    int64_t M = 0, N = 0, K = 0, w = 0;
+    int tm = 0, tn = 0;
+    mw_problem p{};
+    if (i < count) {
+      p = probs[i];
+      M = p.M; N = p.N; K = p.K;
+      const bool ok = M > 0 && N > 0 && K > 0 && K <= Kpitch && p.A && p.B && p.C &&
+                      p.lda >= K && p.ldb >= N && p.ldc >= N;
+      if (!ok) { bad = 1; M = N = K = 0; }
+      tm = (int)((M + BM - 1) / BM);
+      tn = (int)((N + BN - 1) / BN);
+      w = (int64_t)tm * tn * G;
+    }
+    const int64_t pM = block_exclusive_scan(M, sh) + cM; const int64_t tM = sh[32];
+    const int64_t pN = block_exclusive_scan(N, sh) + cN; const int64_t tN = sh[32];
+    const int64_t pMN = block_exclusive_scan(M * N, sh) + cMN; const int64_t tMN = sh[32];
+    const int64_t pW = block_exclusive_scan(w, sh) + cW; const int64_t tW = sh[32];
+    if (i < count) {
+      BInfo b{};
+      b.M = M; b.N = N; b.K = K;
+      b.A = p.A; b.lda = p.lda; b.psa = p.plane_stride_a;
+      b.B = p.B; b.ldb = p.ldb; b.psb = p.plane_stride_b;
+      b.C = p.C; b.ldc = p.ldc; b.psc = p.plane_stride_c;
+      b.rowA = (int64_t)S_A * pM; b.rowB = (int64_t)S_B * pN;
+      b.eA = pM; b.eB = pN; b.part = (int64_t)G * pMN; b.work = pW;
+      b.tiles_m = tm; b.tiles_n = tn; b.KB = (int)((K + BK - 1) / BK);
+      info[i] = b;
+    }
+    cM += tM; cN += tN; cMN += tMN; cW += tW;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    if (cM != want.sum_M || cN != want.sum_N || cMN != want.sum_MN) bad = 1;
+    hdr->sum_M = cM; hdr->sum_N = cN; hdr->sum_MN = cMN; hdr->total_work = bad ? 0 : cW;
+    hdr->bad = bad;
+    if (bad) raise_status(status, MW_EINVAL);
+  }
+}
+
+// ---- 2. split ---------------------------------------------------------------------
+// One warp per row of some A_i (tasks [0, sum_M)) or column of some B_i
+// (tasks [sum_M, sum_M + sum_N)).
+template <int NL>
+__global__ void __launch_bounds__(256) batch_split_kernel(
+    const BInfo *info, const BHeader *hdr, int count, int m, int w, int S_A, int S_B,
+    int64_t Kpitch, __nv_bfloat16 *pieceA, __nv_bfloat16 *pieceB, int32_t *eA, int32_t *spA,
+    int32_t *eB, int32_t *spB, int32_t *max_spread, int range_A, int range_B, int exps_only,
+    unsigned int *status) {
+  if (hdr->bad) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t sum_M = hdr->sum_M, total = hdr->sum_M + hdr->sum_N;
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < total;
+       task += nwarps) {
+    const bool isA = task < sum_M;
+    const int i = isA ? find_problem(info, count, task, [](const BInfo &b) { return b.eA; })
+                      : find_problem(info, count, task - sum_M,
+                                     [](const BInfo &b) { return b.eB; });
+    const BInfo &b = info[i];
+    const int64_t r = isA ? task - b.eA : task - sum_M - b.eB;  // row of A_i / column of B_i
+    const int64_t K = b.K;
+    // entry k of the row: A_i[r][k] or B_i[k][r]
+    const double *base = isA ? b.A + r * b.lda : b.B + r;
+    const int64_t kstride = isA ? 1 : b.ldb, ps = isA ? b.psa : b.psb;
+    int emax = kExpZero, emin = -kExpZero;
+    bool nonfinite = false;
+    for (int64_t k = lane; k < K; k += 32) {
+      int e = kExpZero;
+      for (int j = 0; j < m; ++j) {
+        const int x = exp_plus1(base[j * ps + k * kstride]);
+        if (x == kExpNonFinite) nonfinite = true;
+        else e = max(e, x);
+      }
+      if (e != kExpZero) { emax = max(emax, e); emin = min(emin, e); }
+    }
+    for (int o = 16; o; o >>= 1) {
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    }
+    if (nonfinite) raise_status(status, MW_ENONFINITE);
+    const int E = emax == kExpZero ? 0 : emax;
+    const int sp = emax == kExpZero ? 0 : emax - emin;
+    if (lane == 0) {
+      (isA ? eA : eB)[task - (isA ? 0 : sum_M)] = E;
+      (isA ? spA : spB)[task - (isA ? 0 : sum_M)] = sp;
+      atomicMax(max_spread + (isA ? 0 : 1), sp);
+      const int rg = isA ? range_A : range_B;
+      if (rg >= 0 && sp > rg) raise_status(status, MW_WRANGE);
+    }
+    if (exps_only) continue;
+    const int S = isA ? S_A : S_B;
+    const int64_t rows = isA ? b.M : b.N;
+    __nv_bfloat16 *dst = (isA ? pieceA + (b.rowA + r) * Kpitch : pieceB + (b.rowB + r) * Kpitch);
+    const int F = w * S - 2 - E;
+    for (int64_t k = 2 * lane; k < Kpitch; k += 64) {
+      double x0[8], x1[8];
+      const bool v0 = k < K, v1 = k + 1 < K;
+      for (int j = 0; j < m; ++j) {
+        x0[j] = v0 ? base[j * ps + k * kstride] : 0.0;
+        x1[j] = v1 ? base[j * ps + (k + 1) * kstride] : 0.0;
+      }
+      cut_pair<NL, __nv_bfloat16>(x0, x1, v0, v1, m, F, w, S, dst + k, rows * Kpitch, status);
+    }
+  }
+}
+
+// ---- 4. fusion ------------------------------------------------------------------------
+template <int MW, int NL>
+__global__ void __launch_bounds__(256) batch_combine_kernel(const BInfo *info, const BHeader *hdr,
+                                                            int count, const int64_t *partials,
+                                                            const int32_t *eA, const int32_t *eB,
+                                                            int G, int group, int D, int w) {
+  if (hdr->bad) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       task < hdr->sum_M; task += nwarps) {
+    const int i = find_problem(info, count, task, [](const BInfo &b) { return b.eA; });
+    const BInfo &b = info[i];
+    const int64_t r = task - b.eA;
+    const int ea = eA[task];
+    for (int64_t j = lane; j < b.N; j += 32) {
+      uint64_t X[NL];
+#pragma unroll
+      for (int k = 0; k < NL; ++k) X[k] = 0;
+      for (int g = 0; g < G; ++g) {
+        const int t1 = min(D, (g + 1) * group) - 1;
+        add_shifted<NL>(X, partials[b.part + ((int64_t)g * b.M + r) * b.N + j], w * (D - 1 - t1));
+      }
+      double words[MW];
+      round_words<MW, NL>(X, ea + eB[b.eB + j] + 4 - w * (D + 1), words);
+#pragma unroll
+      for (int k = 0; k < MW; ++k) b.C[k * b.psc + r * b.ldc + j] = words[k];
+    }
+  }
+}
+
+int grid_for(int per_sm) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm * per_sm;
+}
+
+int check_batch(const mw_plan *p, const mw_batch *b) {
+  if (!p || !b) return fail(MW_EINVAL, "plan/batch is NULL");
+  if (p->mode != MW_OZAKI) return fail(MW_EUNSUPPORTED, "batches run in the Ozaki form");
+  if (p->m != 2 && p->m != 4 && p->m != 8) return fail(MW_EINVAL, "m must be 2, 4 or 8");
+  if (b->count < 1 || b->sum_M < 1 || b->sum_N < 1 || b->max_K < 1)
+    return fail(MW_EINVAL, "empty batch");
+  if (p->w < 2 || p->w > 8 || (int64_t)p->chunk << (2 * p->w - 2) > (1 << 22) || p->chunk % 64)
+    return fail(MW_EINVAL, "bad w/chunk");
+  if (p->S_A < 1 || p->S_B < 1 || p->D < 1 || p->group < 1) return fail(MW_EINVAL, "bad plan");
+  const int S_min = std::min(p->S_A, p->S_B);
+  const double bits = std::ceil(std::log2((double)S_min * (double)b->max_K)) + 2 * p->w - 2;
+  if (bits > 62 || bits + (double)p->w * (p->group - 1) > 62)
+    return fail(MW_EINVAL, "group %d too large for K = %lld", p->group, (long long)b->max_K);
+  if ((int64_t)p->S_A * b->sum_M > 0x7fffffffLL || (int64_t)p->S_B * b->sum_N > 0x7fffffffLL)
+    return fail(MW_EUNSUPPORTED, "batch too large for 32-bit piece rows");
+  return MW_OK;
+}
+
+template <int NL>
+void launch_split_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
+                     uint8_t *w8, const Layout &L, int exps_only, cudaStream_t s) {
+  batch_split_kernel<NL><<<grid_for(8), 256, 0, s>>>(
+      info, hdr, b.count, p.m, p.w, p.S_A, p.S_B, L.Kpitch,
+      reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceA),
+      reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceB), reinterpret_cast<int32_t *>(w8 + L.eA),
+      reinterpret_cast<int32_t *>(w8 + L.spA), reinterpret_cast<int32_t *>(w8 + L.eB),
+      reinterpret_cast<int32_t *>(w8 + L.spB),
+      reinterpret_cast<BHeader *>(w8 + L.header)->max_spread, p.range_A, p.range_B, exps_only,
+      status_ptr());
+}
+
+int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void *ws,
+              const Layout &L, int exps_only, cudaStream_t s) {
+  uint8_t *w8 = static_cast<uint8_t *>(ws);
+  BInfo *info = reinterpret_cast<BInfo *>(w8 + L.info);
+  BHeader *hdr = reinterpret_cast<BHeader *>(w8 + L.header);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(BHeader), s);
+  if (e != cudaSuccess) return cuda_fail(e, "batch header memset");
+  prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, n_groups(p.D, p.group), p.S_A, p.S_B,
+                                     L.Kpitch, b, info, hdr, status_ptr());
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch prologue launch");
+  const int bits = p.w * std::max(p.S_A, p.S_B) + 3;
+  if (bits <= 128) launch_split_nl<2>(info, hdr, b, p, w8, L, exps_only, s);
+  else if (bits <= 256) launch_split_nl<4>(info, hdr, b, p, w8, L, exps_only, s);
+  else if (bits <= 384) launch_split_nl<6>(info, hdr, b, p, w8, L, exps_only, s);
+  else if (bits <= 512) launch_split_nl<8>(info, hdr, b, p, w8, L, exps_only, s);
+  else if (bits <= 640) launch_split_nl<10>(info, hdr, b, p, w8, L, exps_only, s);
+  else return fail(MW_EUNSUPPORTED, "w*S too large");
+  return cuda_fail(cudaGetLastError(), "batch split launch");
+}
+
+template <int MW, int NL>
+void launch_combine_b(const BInfo *info, const BHeader *hdr, const mw_batch &b,
+                      const mw_plan &p, uint8_t *w8, const Layout &L, cudaStream_t s) {
+  batch_combine_kernel<MW, NL><<<grid_for(8), 256, 0, s>>>(
+      info, hdr, b.count, reinterpret_cast<const int64_t *>(w8 + L.partials),
+      reinterpret_cast<const int32_t *>(w8 + L.eA), reinterpret_cast<const int32_t *>(w8 + L.eB),
+      n_groups(p.D, p.group), p.group, p.D, p.w);
+}
+
+template <int MW>
+int combine_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
+               uint8_t *w8, const Layout &L, cudaStream_t s) {
+  const int bits = 64 + p.w * (p.D - 1) + 1;
+  if (bits <= 256) launch_combine_b<MW, 4>(info, hdr, b, p, w8, L, s);
+  else if (bits <= 384) launch_combine_b<MW, 6>(info, hdr, b, p, w8, L, s);
+  else if (bits <= 512) launch_combine_b<MW, 8>(info, hdr, b, p, w8, L, s);
+  else if (bits <= 640) launch_combine_b<MW, 10>(info, hdr, b, p, w8, L, s);
+  else return fail(MW_EUNSUPPORTED, "too many diagonals for the fusion");
+  return cuda_fail(cudaGetLastError(), "batch combine launch");
+}
+
+}  // namespace
+}  // namespace mw
+
+using namespace mw;
+
+extern "C" {
+
+int mw_batch_describe(int count, const int64_t *shapes, mw_batch *batch) {
+  if (!shapes || !batch || count < 1) return fail(MW_EINVAL, "bad batch description");
+  mw_batch b{};
+  b.count = count;
+  b.min_K = INT64_MAX;
+  for (int i = 0; i < count; ++i) {
+    const int64_t M = shapes[3 * i], N = shapes[3 * i + 1], K = shapes[3 * i + 2];
+    if (M < 1 || N < 1 || K < 1) return fail(MW_EINVAL, "problem %d has an empty dimension", i);
+    b.sum_M += M;
+    b.sum_N += N;
+    b.sum_MN += M * N;
+    b.max_M = std::max(b.max_M, M);
+    b.max_N = std::max(b.max_N, N);
+    b.min_K = std::min(b.min_K, K);
+    b.max_K = std::max(b.max_K, K);
+  }
+  *batch = b;
+  return MW_OK;
+}
+
+int mw_gemm_batched_workspace_size(const mw_plan *plan, const mw_batch *batch, size_t *bytes) {
+  if (!bytes) return fail(MW_EINVAL, "bytes is NULL");
+  int rc = check_batch(plan, batch);
+  if (rc) return rc;
+  *bytes = layout_of(*plan, *batch).total;
+  return MW_OK;
+}
+
+int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *problems, void *ws,
+                              size_t ws_bytes, int *range_A, int *range_B, mw_stream_t stream) {
+  if (!range_A || !range_B || !problems) return fail(MW_EINVAL, "NULL argument");
+  mw_plan p{};
+  p.m = m; p.mode = MW_OZAKI; p.w = 8; p.S_A = p.S_B = 1; p.D = 1; p.group = 1; p.chunk = 64;
+  p.range_A = p.range_B = -1;
+  int rc = check_batch(&p, batch);
+  if (rc) return rc;
+  Layout L = layout_of(p, *batch);
+  if (!ws || ws_bytes < L.pieceA) return fail(MW_ENOSPC, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = run_front(p, *batch, problems, ws, L, 1, s))) return rc;
+  int32_t host[2];
+  BHeader *hdr = reinterpret_cast<BHeader *>(static_cast<uint8_t *>(ws) + L.header);
+  cudaError_t e = cudaMemcpyAsync(host, hdr->max_spread, sizeof host, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "batched spread read");
+  *range_A = host[0];
+  *range_B = host[1];
+  return MW_OK;
+}
+
+int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem *problems,
+                    void *ws, size_t ws_bytes, mw_stream_t stream) {
+  int rc = check_batch(plan, batch);
+  if (rc) return rc;
+  if (!problems) return fail(MW_EINVAL, "problems is NULL");
+  const mw_plan &p = *plan;
+  const mw_batch &b = *batch;
+  const Layout L = layout_of(p, b);
+  if (!ws || ws_bytes < L.total)
+    return fail(MW_ENOSPC, "workspace %zu bytes, need %zu", ws_bytes, L.total);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t *w8 = static_cast<uint8_t *>(ws);
+  if ((rc = run_front(p, b, problems, ws, L, 0, s))) return rc;
+  ProductLaunch P{};
+  P.pieceA = w8 + L.pieceA; P.pieceB = w8 + L.pieceB;
+  P.rowsA = (int64_t)p.S_A * b.sum_M; P.rowsB = (int64_t)p.S_B * b.sum_N; P.Kpitch = L.Kpitch;
+  P.S_A = p.S_A; P.S_B = p.S_B; P.D = p.D; P.w = p.w; P.group = p.group; P.chunk = p.chunk;
+  P.info = w8 + L.info; P.hdr = w8 + L.header; P.count = b.count;
+  P.partials = reinterpret_cast<int64_t *>(w8 + L.partials);
+  P.next_item = &reinterpret_cast<BHeader *>(w8 + L.header)->next_item;
+  if ((rc = launch_product(P, s))) return rc;
+  const BInfo *info = reinterpret_cast<const BInfo *>(w8 + L.info);
+  const BHeader *hdr = reinterpret_cast<const BHeader *>(w8 + L.header);
+  switch (p.m) {
+    case 2: return combine_nl<2>(info, hdr, b, p, w8, L, s);
+    case 4: return combine_nl<4>(info, hdr, b, p, w8, L, s);
+    default: return combine_nl<8>(info, hdr, b, p, w8, L, s);
+  }
+}
+
+}  // extern "C"

@@ -46,10 +46,24 @@ struct OzakiArgs {
   int64_t M, N, Kp;
   const void *dA, *dB;          // bf16 pieces, S x rows x Kp
   const int32_t *eA, *eB;
-  int64_t *partials;            // G x tiles x 128 x 128
+  int64_t *partials;            // [group][M][N], then the work counter
   double *C;
   int64_t ldc, psc;
 };
+// The product kernel for one problem (info == nullptr: M, N, K) or a batch
+// (info, hdr: device arrays written by the batched prologue, mw_work.cuh).
+struct ProductLaunch {
+  const void *pieceA, *pieceB;  // bf16 pieces, rows of Kpitch elements
+  int64_t rowsA, rowsB, Kpitch;
+  int S_A, S_B, D, w, group, chunk;
+  const void *info, *hdr;
+  int count;
+  int64_t M, N, K;
+  int64_t *partials;
+  unsigned long long *next_item;  // work counter (reset by launch_product)
+};
+int launch_product(const ProductLaunch &a, cudaStream_t s);
+
 // between_kernels runs after the product kernel is launched, before the combine.
 int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels);
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group);

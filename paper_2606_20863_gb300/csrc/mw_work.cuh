@@ -1,0 +1,45 @@
+// Description of the products a product kernel works on (device side, shared
+// by the single and batched paths).  A work item is (problem, diagonal group,
+// output tile); items are numbered problem by problem.
+#pragma once
+#include <cstdint>
+
+namespace mw {
+namespace {
+
+struct BInfo {            // one problem, filled by the prologue
+  int64_t M, N, K;
+  const double *A;
+  int64_t lda, psa;
+  const double *B;
+  int64_t ldb, psb;
+  double *C;
+  int64_t ldc, psc;
+  int64_t rowA, rowB;     // first piece row of the problem in the A / B piece arrays
+  int64_t eA, eB;         // prefix sums of M and N: exponent offsets
+  int64_t part;           // offset of the partial sums (int64 units)
+  int64_t work;           // first work item
+  int32_t tiles_m, tiles_n, KB, pad;
+};
+
+struct BHeader {          // written by the prologue
+  int64_t sum_M, sum_N, sum_MN, total_work;
+  int32_t bad;            // the descriptors disagree with the host summary
+  int32_t max_spread[2];
+  int32_t pad;
+  unsigned long long next_item;  // work counter of the product kernel
+};
+
+// problem owning flat index x, given a field that holds exclusive prefix sums
+template <typename F>
+__device__ __forceinline__ int find_problem(const BInfo *info, int count, int64_t x, F key) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (key(info[mid]) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace
+}  // namespace mw

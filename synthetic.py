@@ -155,6 +155,24 @@ def batch_problems(sizes: np.ndarray, m: int = 8, seed: int = 3):
     return out
 
 
+def batch_flat(sizes: np.ndarray, m: int = 8, seed: int = 3):
+    """All square problems of a batch in two flat buffers (every A_i, then every
+    B_i, each m planes of n_i x n_i), plus each problem's element offset.
+    Leading words U[-1,1), lower words x 2^-53 U[-1,1).  The stream continues
+    after the sizes were drawn with the same seed."""
+    rng = SplitMix64(seed)
+    rng.next(len(sizes))
+    n2 = sizes.astype(np.int64) ** 2
+    offs = np.concatenate([[0], np.cumsum(n2)[:-1]])
+    total = int(n2.sum())
+    flats = []
+    for _ in range(2):
+        lead = rng.sym(total)
+        words = _lower_words(rng, lead, m)          # (m, total)
+        flats.append(words)
+    return flats[0], flats[1], offs
+
+
 def adjoint_case(seed: int = 4, M: int = 2048, K: int = 1024, N: int = 2048):
     """Double-double A (M x K), B (K x N), and loss weights W (M x N) U[-1,1)."""
     rng = SplitMix64(seed)

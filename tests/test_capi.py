@@ -93,7 +93,7 @@ def test_workspace_layout_is_consistent(mw):
     assert off[2] - off[1] >= p.S_A * 300 * Kp * 2
     assert off[3] - off[2] >= p.S_B * 200 * Kp * 2
     G = -(-p.D // p.group)
-    assert total - off[3] >= G * 3 * 2 * 128 * 128 * 8
+    assert total - off[3] >= G * 300 * 200 * 8
     assert total == mw.workspace_size(p, 300, 200, 1000)
     assert all(o % 256 == 0 for o in off)
 
