@@ -88,6 +88,9 @@ typedef struct mw_plan {
  * componentwise for any operands whose rows of op(A) (columns of op(B)) span at
  * most range_A (range_B) binary orders of magnitude, measured as max minus min
  * of ilogb+1 over the nonzero entries.  Host only, no GPU work.
+ * plan->w on input: 0 lets the planner choose (MW_OZAKI 8, MW_PLAIN the widest
+ * width whose sums stay exact); a width in range (2..8 for MW_OZAKI, 4..26 for
+ * MW_PLAIN) is used as given.  Zero the struct before the call.
  * Returns MW_EINVAL for bad arguments, MW_EUNSUPPORTED if no plan fits the
  * exactness thresholds (e.g. K too long for MW_PLAIN). */
 int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, int range_B,

@@ -164,8 +164,9 @@ def check_status(allow: int = MW_WRANGE):
 
 
 def mw_plan_gemm(m: int, mode: str | int, M: int, N: int, K: int, range_A: int,
-                 range_B: int) -> mw_plan:
+                 range_B: int, w: int = 0) -> mw_plan:
     p = mw_plan()
+    p.w = w
     mode = _MODES.get(mode, mode)
     _check(_lib.mw_plan_gemm(m, mode, M, N, K, range_A, range_B, ctypes.byref(p)),
            "mw_plan_gemm")
@@ -241,7 +242,7 @@ def plan_for(A: torch.Tensor, B: torch.Tensor, mode="ozaki", transA=False, trans
     """Plan with the exponent spreads measured on the operands (synchronizes)."""
     m, M, N, K = _dims(A, B, transA, transB)
     ra, rb = mw_measure_spread(A, B, transA, transB)
-    p = mw_plan_gemm(m, mode, M, N, K, ra, rb)
+    p = mw_plan_gemm(m, mode, M, N, K, ra, rb, overrides.pop("w", 0))
     for k, v in overrides.items():
         setattr(p, k, v)
     return p

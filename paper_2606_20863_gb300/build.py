@@ -16,6 +16,8 @@ SOURCES = ["mw_capi.cu", "mw_split.cu", "mw_plain.cu", "mw_ozaki.cu", "mw_noallo
 HEADERS = ["mw_device.cuh", "mw_internal.h", "mw_pieces.cuh", "mw_tc.cuh", "mw_fuse.cuh", "mw_work.cuh", os.path.join("..", "..", "include", "mw.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+# extra nvcc flags, e.g. -DMW_STAGES=7 to build a variant of the pipeline depth
+EXTRA = os.environ.get("MW_NVCC_EXTRA", "").split()
 
 
 def nvcc() -> str:
@@ -32,7 +34,7 @@ def _newest_input() -> float:
 
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc()] + ARCH + FLAGS + EXTRA + ["-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
 // ---- 2. split ---------------------------------------------------------------------
 // One warp per row of some A_i (tasks [0, sum_M)) or column of some B_i
 // (tasks [sum_M, sum_M + sum_N)).
-template <int NL>
+template <int MW, int NL>
 __global__ void __launch_bounds__(256) batch_split_kernel(
-    const BInfo *info, const BHeader *hdr, int count, int m, int w, int S_A, int S_B,
+    const BInfo *info, const BHeader *hdr, int count, int w, int S_A, int S_B,
     int64_t Kpitch, __nv_bfloat16 *pieceA, __nv_bfloat16 *pieceB, int32_t *eA, int32_t *spA,
     int32_t *eB, int32_t *spB, int32_t *max_spread, int range_A, int range_B, int exps_only,
     unsigned int *status) {
@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(256) batch_split_kernel(
     bool nonfinite = false;
     for (int64_t k = lane; k < K; k += 32) {
       int e = kExpZero;
-      for (int j = 0; j < m; ++j) {
+#pragma unroll
+      for (int j = 0; j < MW; ++j) {
         const int x = exp_plus1(base[j * ps + k * kstride]);
         if (x == kExpNonFinite) nonfinite = true;
         else e = max(e, x);
@@ -189,13 +190,14 @@ __global__ void __launch_bounds__(256) batch_split_kernel(
     __nv_bfloat16 *dst = (isA ? pieceA + (b.rowA + r) * Kpitch : pieceB + (b.rowB + r) * Kpitch);
     const int F = w * S - 2 - E;
     for (int64_t k = 2 * lane; k < Kpitch; k += 64) {
-      double x0[8], x1[8];
+      double x0[MW], x1[MW];
       const bool v0 = k < K, v1 = k + 1 < K;
-      for (int j = 0; j < m; ++j) {
+#pragma unroll
+      for (int j = 0; j < MW; ++j) {
         x0[j] = v0 ? base[j * ps + k * kstride] : 0.0;
         x1[j] = v1 ? base[j * ps + (k + 1) * kstride] : 0.0;
       }
-      cut_pair<NL, __nv_bfloat16>(x0, x1, v0, v1, m, F, w, S, dst + k, rows * Kpitch, status);
+      cut_pair<MW, NL, __nv_bfloat16>(x0, x1, F, w, S, dst + k, rows * Kpitch, status);
     }
   }
 }
@@ -256,11 +258,11 @@ int check_batch(const mw_plan *p, const mw_batch *b) {
   return MW_OK;
 }
 
-template <int NL>
+template <int MW, int NL>
 void launch_split_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
                      uint8_t *w8, const Layout &L, int exps_only, cudaStream_t s) {
-  batch_split_kernel<NL><<<grid_for(8), 256, 0, s>>>(
-      info, hdr, b.count, p.m, p.w, p.S_A, p.S_B, L.Kpitch,
+  batch_split_kernel<MW, NL><<<grid_for(8), 256, 0, s>>>(
+      info, hdr, b.count, p.w, p.S_A, p.S_B, L.Kpitch,
       reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceA),
       reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceB), reinterpret_cast<int32_t *>(w8 + L.eA),
       reinterpret_cast<int32_t *>(w8 + L.spA), reinterpret_cast<int32_t *>(w8 + L.eB),
@@ -280,12 +282,14 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
                                      L.Kpitch, b, info, hdr, status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch prologue launch");
   const int bits = p.w * std::max(p.S_A, p.S_B) + 3;
-  if (bits <= 128) launch_split_nl<2>(info, hdr, b, p, w8, L, exps_only, s);
-  else if (bits <= 256) launch_split_nl<4>(info, hdr, b, p, w8, L, exps_only, s);
-  else if (bits <= 384) launch_split_nl<6>(info, hdr, b, p, w8, L, exps_only, s);
-  else if (bits <= 512) launch_split_nl<8>(info, hdr, b, p, w8, L, exps_only, s);
-  else if (bits <= 640) launch_split_nl<10>(info, hdr, b, p, w8, L, exps_only, s);
-  else return fail(MW_EUNSUPPORTED, "w*S too large");
+  int nl = bits <= 128 ? 2 : bits <= 256 ? 4 : bits <= 384 ? 6 : bits <= 512 ? 8 : bits <= 640 ? 10 : 0;
+  if (!nl) return fail(MW_EUNSUPPORTED, "w*S too large");
+#define MW_SPLIT_CASE(MWV, NLV) \
+  if (p.m == MWV && nl == NLV) launch_split_nl<MWV, NLV>(info, hdr, b, p, w8, L, exps_only, s);
+  MW_SPLIT_CASE(2, 2) MW_SPLIT_CASE(2, 4) MW_SPLIT_CASE(2, 6) MW_SPLIT_CASE(2, 8) MW_SPLIT_CASE(2, 10)
+  MW_SPLIT_CASE(4, 2) MW_SPLIT_CASE(4, 4) MW_SPLIT_CASE(4, 6) MW_SPLIT_CASE(4, 8) MW_SPLIT_CASE(4, 10)
+  MW_SPLIT_CASE(8, 2) MW_SPLIT_CASE(8, 4) MW_SPLIT_CASE(8, 6) MW_SPLIT_CASE(8, 8) MW_SPLIT_CASE(8, 10)
+#undef MW_SPLIT_CASE
   return cuda_fail(cudaGetLastError(), "batch split launch");
 }
 

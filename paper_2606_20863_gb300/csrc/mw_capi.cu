@@ -170,6 +170,7 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
   if (!valid_m(m)) return fail(MW_EINVAL, "m = %d, must be 2, 4 or 8", m);
   if (M <= 0 || N <= 0 || K <= 0) return fail(MW_EINVAL, "dimensions must be positive");
   if (range_A < 0 || range_B < 0) return fail(MW_EINVAL, "ranges must be >= 0");
+  const int want_w = plan->w;
   // Error budget 2K 2^(-52m) per unit of sum |a||b|, a quarter each to the
   // truncation of A, of B, the dropped pairs and the final rounding:
   //   truncation of A: m 2^(rA + 3 - w S_A) <= K 2^(-52m-1)
@@ -192,13 +193,15 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
     if (p.D > p.S_A + p.S_B - 1) p.D = p.S_A + p.S_B - 1;
   };
   if (mode == MW_OZAKI) {
-    finish(8);
+    if (want_w != 0 && (want_w < 2 || want_w > 8)) return fail(MW_EINVAL, "Ozaki w must be 2..8");
+    finish(want_w ? want_w : 8);
     p.chunk = 1 << (24 - 2 * p.w);  // chunk 2^(2w-2) <= 2^22
     const int S_min = p.S_A < p.S_B ? p.S_A : p.S_B;
     p.group = group_size(S_min, K, p.w);
     if (p.group < 1) return fail(MW_EUNSUPPORTED, "K = %lld too long for 64-bit partial sums", (long long)K);
   } else if (mode == MW_PLAIN) {
-    int w = 26;
+    if (want_w != 0 && (want_w < 4 || want_w > 26)) return fail(MW_EINVAL, "plain w must be 4..26");
+    int w = want_w ? want_w : 26;
     for (; w >= 4; --w) {
       finish(w);
       const int S_min = p.S_A < p.S_B ? p.S_A : p.S_B;

@@ -41,11 +41,19 @@
 namespace mw {
 namespace {
 
+#ifndef MW_STAGES
+#define MW_STAGES 6      // TMA pipeline depth (32 KB per stage)
+#endif
+#ifndef MW_ACC_BUFS
+#define MW_ACC_BUFS 2    // accumulators in tensor memory (128 columns each)
+#endif
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 6;
+constexpr int STAGES = MW_STAGES;
+constexpr int NBUF = MW_ACC_BUFS;
 constexpr int NUM_DRAIN_WARPS = 8;
 constexpr int NUM_THREADS = 64 + 32 * NUM_DRAIN_WARPS;
-constexpr int TMEM_COLS = 2 * BN;
+constexpr int TMEM_COLS = NBUF * BN;
+static_assert(NBUF == 2 || NBUF == 4, "2 or 4 accumulator buffers");
 constexpr uint32_t STAGE_A = BM * BK * 2, STAGE_B = BN * BK * 2;
 constexpr uint32_t MAGIC_BITS = 0x4B400000u;  // bit pattern of 1.5 * 2^23
 constexpr size_t SMEM_BYTES = 1024 + STAGES * (STAGE_A + STAGE_B) + 512;
@@ -109,8 +117,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t *full = (uint64_t *)(smem + STAGES * (STAGE_A + STAGE_B));
   uint64_t *empty = full + STAGES;
   uint64_t *accf = empty + STAGES;
-  uint64_t *acce = accf + 2;
-  uint64_t *done = acce + 2;
+  uint64_t *acce = accf + NBUF;
+  uint64_t *done = acce + NBUF;
   uint64_t *uf = done + 1;           // work item published
   uint64_t *ue = uf + RING;          // work item read by the MMA thread and every drain warp
   volatile int64_t *ring = (volatile int64_t *)(ue + RING);
@@ -125,7 +133,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], NUM_DRAIN_WARPS);
     }
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int tot = nsteps(P, t, x.KB);
           for (int j = 0; j < tot && !*abort; ++ch) {
             const int nk = min(P.chunk_kb, tot - j);
-            const uint32_t b = ch & 1, bph = (ch >> 1) & 1;
+            const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
             if (!mbar_wait(&acce[b], bph ^ 1, P.status, abort)) break;
             tc_fence_after();
             const uint32_t d = tmem + b * BN;
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int nch = (nsteps(P, t, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
         bias += (uint64_t)nch * MAGIC_BITS;
         for (int c = 0; c < nch; ++c, ++ch) {
-          const uint32_t b = ch & 1, bph = (ch >> 1) & 1;
+          const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
           if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], bph, P.status, abort))) {
             ok = false;
             break;

@@ -13,11 +13,12 @@ namespace mw {
 namespace {
 
 // Fixed-point value of one entry in NL limbs (two's complement, little endian).
-template <int NL>
-__device__ __forceinline__ void fixed_point(const double *w, int m, int F, uint64_t (&T)[NL]) {
+template <int MW, int NL>
+__device__ __forceinline__ void fixed_point(const double (&w)[MW], int F, uint64_t (&T)[NL]) {
 #pragma unroll
   for (int i = 0; i < NL; ++i) T[i] = 0;
-  for (int j = 0; j < m; ++j) {
+#pragma unroll
+  for (int j = 0; j < MW; ++j) {
     int e2;
     bool neg;
     uint64_t M = mantissa_of(w[j], e2, neg);
@@ -82,14 +83,14 @@ __device__ __forceinline__ void store2<double>(double *p, int d0, int d1) {
 }
 
 // Cut two entries (k, k+1 of one row) into S pieces and store them.
-template <int NL, typename Out>
-__device__ __forceinline__ void cut_pair(const double *w0, const double *w1, bool v0, bool v1,
-                                         int m, int F, int w, int S, Out *dst, int64_t plane,
+// w0, w1: the words of the two entries (zeros stand for entries past the row end).
+template <int MW, int NL, typename Out>
+__device__ __forceinline__ void cut_pair(const double (&w0)[MW], const double (&w1)[MW], int F,
+                                         int w, int S, Out *dst, int64_t plane,
                                          unsigned int *status) {
   uint64_t T0[NL], T1[NL];
-  double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  fixed_point<NL>(v0 ? w0 : z, m, F, T0);
-  fixed_point<NL>(v1 ? w1 : z, m, F, T1);
+  fixed_point<MW, NL>(w0, F, T0);
+  fixed_point<MW, NL>(w1, F, T1);
   const uint64_t mask = (1ull << w) - 1;
   const int half = 1 << (w - 1);
   int c0 = 0, c1 = 0;

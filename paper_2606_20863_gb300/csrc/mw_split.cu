@@ -64,7 +64,7 @@ __global__ void exps_rows_kernel(const double *__restrict__ X, int m, int64_t R,
 
 // trans = 1: block = 32 (r) x 8 (k) threads; each block covers 32 columns and
 // kRowsPerBlock rows of the stored K x R matrix.
-constexpr int kRowsPerBlock = 256;
+constexpr int kRowsPerBlock = 32;
 __global__ void exps_cols_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
                                  int64_t ld, int64_t ps, int *Eb, int *eminb,
                                  unsigned int *status) {
@@ -114,19 +114,20 @@ __global__ void exps_finalize_kernel(int64_t R, int *E, int *spread, int *max_sp
 
 // ---- pass 2 ------------------------------------------------------------------
 // trans = 0: one thread per (row, pair of columns), pairs cover the padded width.
-template <int NL, typename Out>
-__global__ void pieces_rows_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
+template <int MW, int NL, typename Out>
+__global__ void pieces_rows_kernel(const double *__restrict__ X, int64_t R, int64_t K,
                                    int64_t ld, int64_t ps, int w, int S, Out *digits,
                                    int64_t dld, const int *E, unsigned int *status) {
   const int64_t npair = dld / 2;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= R * npair) return;
   const int64_t r = idx / npair, k = 2 * (idx % npair);
-  double a[8], b[8];
+  double a[MW], b[MW];
   const bool v0 = k < K, v1 = k + 1 < K;
   const double *row = X + r * ld;
   const bool vec = v1 && ((((uintptr_t)(row + k)) & 15) == 0) && ((ps & 1) == 0);
-  for (int j = 0; j < m; ++j) {
+#pragma unroll
+  for (int j = 0; j < MW; ++j) {
     if (vec) {
       const double2 v = *reinterpret_cast<const double2 *>(row + j * ps + k);  // 128-bit load
       a[j] = v.x;
@@ -137,19 +138,21 @@ __global__ void pieces_rows_kernel(const double *__restrict__ X, int m, int64_t 
     }
   }
   const int F = w * S - 2 - E[r];
-  cut_pair<NL, Out>(a, b, v0, v1, m, F, w, S, digits + r * dld + k, R * dld, status);
+  cut_pair<MW, NL, Out>(a, b, F, w, S, digits + r * dld + k, R * dld, status);
 }
 
 // trans = 1: 32 x 32 tiles (32 rows r, 32 columns k of the logical operand)
 // staged through shared memory as doubles (m planes), then cut like trans = 0.
-template <int NL, typename Out>
-__global__ void pieces_cols_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
+template <int MW, int NL, typename Out>
+__global__ void pieces_cols_kernel(const double *__restrict__ X, int64_t R, int64_t K,
                                    int64_t ld, int64_t ps, int w, int S, Out *digits,
                                    int64_t dld, const int *E, unsigned int *status) {
   extern __shared__ double tile[];  // [m][32 k][33]
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int64_t r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-  for (int j = 0; j < m; ++j)
+#pragma unroll
+  for (int j = 0; j < MW; ++j)
+#pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int kl = ty + 8 * i;
       const int64_t k = k0 + kl, r = r0 + tx;
@@ -162,52 +165,60 @@ __global__ void pieces_cols_kernel(const double *__restrict__ X, int m, int64_t 
     const int rl = e >> 4, kl = 2 * (e & 15);
     const int64_t r = r0 + rl, k = k0 + kl;
     if (r >= R || k >= dld) continue;
-    double a[8], b[8];
-    for (int j = 0; j < m; ++j) {
+    double a[MW], b[MW];
+#pragma unroll
+    for (int j = 0; j < MW; ++j) {
       a[j] = tile[(j * 32 + kl) * 33 + rl];
       b[j] = tile[(j * 32 + kl + 1) * 33 + rl];
     }
     const int F = w * S - 2 - E[r];
-    cut_pair<NL, Out>(a, b, k < K, k + 1 < K, m, F, w, S, digits + r * dld + k, R * dld, status);
+    cut_pair<MW, NL, Out>(a, b, F, w, S, digits + r * dld + k, R * dld, status);
   }
 }
 
-template <typename Out, int NL>
+template <int MW, typename Out, int NL>
 int launch_pieces(const SplitArgs &a, cudaStream_t s) {
   Out *dig = static_cast<Out *>(a.digits);
   if (!a.trans) {
     const int64_t n = a.R * (a.digit_ld / 2);
     const int threads = 256;
-    pieces_rows_kernel<NL, Out><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
-        a.X, a.m, a.R, a.K, a.ld, a.plane_stride, a.w, a.S, dig, a.digit_ld, a.exps,
-        status_ptr());
+    pieces_rows_kernel<MW, NL, Out><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        a.X, a.R, a.K, a.ld, a.plane_stride, a.w, a.S, dig, a.digit_ld, a.exps, status_ptr());
   } else {
     dim3 grid((unsigned)((a.R + 31) / 32), (unsigned)((a.digit_ld + 31) / 32));
-    const size_t sm = (size_t)a.m * 32 * 33 * sizeof(double);
+    const size_t sm = (size_t)MW * 32 * 33 * sizeof(double);
     static bool attr_set = false;  // once per instantiation
     if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(pieces_cols_kernel<NL, Out>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           8 * 32 * 33 * (int)sizeof(double));
+      cudaError_t e = cudaFuncSetAttribute(pieces_cols_kernel<MW, NL, Out>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return cuda_fail(e, "split smem attribute");
       attr_set = true;
     }
-    pieces_cols_kernel<NL, Out><<<grid, dim3(32, 8), sm, s>>>(
-        a.X, a.m, a.R, a.K, a.ld, a.plane_stride, a.w, a.S, dig, a.digit_ld, a.exps,
-        status_ptr());
+    pieces_cols_kernel<MW, NL, Out><<<grid, dim3(32, 8), sm, s>>>(
+        a.X, a.R, a.K, a.ld, a.plane_stride, a.w, a.S, dig, a.digit_ld, a.exps, status_ptr());
   }
   return cuda_fail(cudaGetLastError(), "split pieces launch");
 }
 
-template <typename Out>
+template <int MW, typename Out>
 int launch_pieces_nl(const SplitArgs &a, cudaStream_t s) {
   const int bits = a.w * a.S + 3;  // |T| < m 2^(wS-2) < 2^(wS+1), one sign bit
-  if (bits <= 128) return launch_pieces<Out, 2>(a, s);
-  if (bits <= 256) return launch_pieces<Out, 4>(a, s);
-  if (bits <= 384) return launch_pieces<Out, 6>(a, s);
-  if (bits <= 512) return launch_pieces<Out, 8>(a, s);
-  if (bits <= 640) return launch_pieces<Out, 10>(a, s);
+  if (bits <= 128) return launch_pieces<MW, Out, 2>(a, s);
+  if (bits <= 256) return launch_pieces<MW, Out, 4>(a, s);
+  if (bits <= 384) return launch_pieces<MW, Out, 6>(a, s);
+  if (bits <= 512) return launch_pieces<MW, Out, 8>(a, s);
+  if (bits <= 640) return launch_pieces<MW, Out, 10>(a, s);
   return fail(MW_EUNSUPPORTED, "w*S = %d too large (at most 637 bits)", a.w * a.S);
+}
+
+template <typename Out>
+int launch_pieces_m(const SplitArgs &a, cudaStream_t s) {
+  switch (a.m) {
+    case 2: return launch_pieces_nl<2, Out>(a, s);
+    case 4: return launch_pieces_nl<4, Out>(a, s);
+    case 8: return launch_pieces_nl<8, Out>(a, s);
+  }
+  return fail(MW_EINVAL, "m must be 2, 4 or 8");
 }
 
 }  // namespace
@@ -230,8 +241,8 @@ int launch_split(const SplitArgs &a, bool exponents_only, cudaStream_t s) {
       a.R, a.exps, a.spread, a.max_spread, a.range, status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split finalize launch");
   if (exponents_only) return MW_OK;
-  if (a.format == MW_DIGITS_BF16) return launch_pieces_nl<__nv_bfloat16>(a, s);
-  return launch_pieces_nl<double>(a, s);
+  if (a.format == MW_DIGITS_BF16) return launch_pieces_m<__nv_bfloat16>(a, s);
+  return launch_pieces_m<double>(a, s);
 }
 
 }  // namespace mw
