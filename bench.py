@@ -63,6 +63,20 @@ def dist_setup(n):
     return None, 0, 1
 
 
+def aggregate(t_local_s: float, flops_per_step: float, steps: int, dist=None, device=None):
+    """Whole-job throughput of N replicas: every rank did the same work, the job
+    took as long as the slowest rank.  Returns (value GFLOP/s, max time s)."""
+    t = t_local_s
+    world = 1
+    if dist is not None:
+        import torch
+        world = dist.get_world_size()
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return world * flops_per_step * steps / t / 1e9, t
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -216,12 +230,7 @@ def main():
     mw.check_status()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     kern_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    t_step = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([t_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = world * flops * args.steps / t_step / 1e9
+    value, t_step = aggregate(sum(step_ms) / 1e3, flops, args.steps, dist, dev)
 
     # plain FP64 form on the same operands and bound (the comparison of the metric)
     pplan = mw.plan_for(tA, tB, "plain")
