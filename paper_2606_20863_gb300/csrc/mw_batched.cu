@@ -36,6 +36,8 @@ constexpr int BM = 128, BN = 128, BK = 64;
 struct Layout {
   size_t header, info, eA, spA, eB, spB, pieceA, pieceB, partials, total;
   int64_t Kpitch;
+  bool narrow;   // int32 diagonal sums (D planes) or int64 group sums (G planes)
+  int planes;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -53,7 +55,9 @@ Layout layout_of(const mw_plan &p, const mw_batch &b) {
   L.pieceA = off; off = a256(off + 2 * (size_t)p.S_A * b.sum_M * L.Kpitch);
   L.pieceB = off; off = a256(off + 2 * (size_t)p.S_B * b.sum_N * L.Kpitch);
   L.partials = off;
-  off = a256(off + 8 * (size_t)n_groups(p.D, p.group) * b.sum_MN);
+  L.narrow = narrow_partials(p.S_A, p.S_B, p.w, b.max_K);
+  L.planes = L.narrow ? p.D : n_groups(p.D, p.group);
+  off = a256(off + (L.narrow ? 4 : 8) * (size_t)L.planes * b.sum_MN);
   L.total = off;
   return L;
 }
@@ -86,7 +90,8 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t *sh) {
 }
 
 __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs, int count,
-                                                        int G, int S_A, int S_B, int64_t Kpitch,
+                                                        int G, int planes, int S_A, int S_B,
+                                                        int64_t Kpitch,
                                                         mw_batch want, BInfo *info, BHeader *hdr,
                                                         unsigned int *status) {
   __shared__ int64_t sh[33];
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
       b.B = p.B; b.ldb = p.ldb; b.psb = p.plane_stride_b;
       b.C = p.C; b.ldc = p.ldc; b.psc = p.plane_stride_c;
       b.rowA = (int64_t)S_A * pM; b.rowB = (int64_t)S_B * pN;
-      b.eA = pM; b.eB = pN; b.part = (int64_t)G * pMN; b.work = pW;
+      b.eA = pM; b.eB = pN; b.part = (int64_t)planes * pMN; b.work = pW;
       b.tiles_m = tm; b.tiles_n = tn; b.KB = (int)((K + BK - 1) / BK);
       info[i] = b;
     }
@@ -203,9 +208,9 @@ __global__ void __launch_bounds__(256) batch_split_kernel(
 }
 
 // ---- 4. fusion ------------------------------------------------------------------------
-template <int MW, int NL>
+template <int MW, int NL, bool NARROW>
 __global__ void __launch_bounds__(256) batch_combine_kernel(const BInfo *info, const BHeader *hdr,
-                                                            int count, const int64_t *partials,
+                                                            int count, const void *partials,
                                                             const int32_t *eA, const int32_t *eB,
                                                             int G, int group, int D, int w) {
   if (hdr->bad) return;
@@ -221,9 +226,16 @@ __global__ void __launch_bounds__(256) batch_combine_kernel(const BInfo *info, c
       uint64_t X[NL];
 #pragma unroll
       for (int k = 0; k < NL; ++k) X[k] = 0;
-      for (int g = 0; g < G; ++g) {
-        const int t1 = min(D, (g + 1) * group) - 1;
-        add_shifted<NL>(X, partials[b.part + ((int64_t)g * b.M + r) * b.N + j], w * (D - 1 - t1));
+      if constexpr (NARROW) {
+        const int32_t *p = static_cast<const int32_t *>(partials) + b.part;
+        for (int t = 0; t < D; ++t)
+          add_shifted<NL>(X, p[((int64_t)t * b.M + r) * b.N + j], w * (D - 1 - t));
+      } else {
+        const int64_t *p = static_cast<const int64_t *>(partials) + b.part;
+        for (int g = 0; g < G; ++g) {
+          const int t1 = min(D, (g + 1) * group) - 1;
+          add_shifted<NL>(X, p[((int64_t)g * b.M + r) * b.N + j], w * (D - 1 - t1));
+        }
       }
       double words[MW];
       round_words<MW, NL>(X, ea + eB[b.eB + j] + 4 - w * (D + 1), words);
@@ -278,8 +290,8 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
   BHeader *hdr = reinterpret_cast<BHeader *>(w8 + L.header);
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(BHeader), s);
   if (e != cudaSuccess) return cuda_fail(e, "batch header memset");
-  prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, n_groups(p.D, p.group), p.S_A, p.S_B,
-                                     L.Kpitch, b, info, hdr, status_ptr());
+  prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, n_groups(p.D, p.group), L.planes, p.S_A,
+                                     p.S_B, L.Kpitch, b, info, hdr, status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch prologue launch");
   const int bits = p.w * std::max(p.S_A, p.S_B) + 3;
   int nl = bits <= 128 ? 2 : bits <= 256 ? 4 : bits <= 384 ? 6 : bits <= 512 ? 8 : bits <= 640 ? 10 : 0;
@@ -296,10 +308,14 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
 template <int MW, int NL>
 void launch_combine_b(const BInfo *info, const BHeader *hdr, const mw_batch &b,
                       const mw_plan &p, uint8_t *w8, const Layout &L, cudaStream_t s) {
-  batch_combine_kernel<MW, NL><<<grid_for(8), 256, 0, s>>>(
-      info, hdr, b.count, reinterpret_cast<const int64_t *>(w8 + L.partials),
-      reinterpret_cast<const int32_t *>(w8 + L.eA), reinterpret_cast<const int32_t *>(w8 + L.eB),
-      n_groups(p.D, p.group), p.group, p.D, p.w);
+  const int32_t *eA = reinterpret_cast<const int32_t *>(w8 + L.eA);
+  const int32_t *eB = reinterpret_cast<const int32_t *>(w8 + L.eB);
+  if (L.narrow)
+    batch_combine_kernel<MW, NL, true><<<grid_for(8), 256, 0, s>>>(
+        info, hdr, b.count, w8 + L.partials, eA, eB, n_groups(p.D, p.group), p.group, p.D, p.w);
+  else
+    batch_combine_kernel<MW, NL, false><<<grid_for(8), 256, 0, s>>>(
+        info, hdr, b.count, w8 + L.partials, eA, eB, n_groups(p.D, p.group), p.group, p.D, p.w);
 }
 
 template <int MW>
@@ -389,7 +405,8 @@ int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem
   P.rowsA = (int64_t)p.S_A * b.sum_M; P.rowsB = (int64_t)p.S_B * b.sum_N; P.Kpitch = L.Kpitch;
   P.S_A = p.S_A; P.S_B = p.S_B; P.D = p.D; P.w = p.w; P.group = p.group; P.chunk = p.chunk;
   P.info = w8 + L.info; P.hdr = w8 + L.header; P.count = b.count;
-  P.partials = reinterpret_cast<int64_t *>(w8 + L.partials);
+  P.partials = w8 + L.partials;
+  P.narrow = L.narrow;
   P.next_item = &reinterpret_cast<BHeader *>(w8 + L.header)->next_item;
   if ((rc = launch_product(P, s))) return rc;
   const BInfo *info = reinterpret_cast<const BInfo *>(w8 + L.info);

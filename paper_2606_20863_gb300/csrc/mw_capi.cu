@@ -89,7 +89,9 @@ Layout layout(const mw_plan &p, int64_t M, int64_t N, int64_t K) {
   L.digB = off;
   off = align256(off + (size_t)p.S_B * N * L.Kp * elem);
   L.partials = off;
-  if (p.mode == MW_OZAKI) off = align256(off + ozaki_partials_bytes(M, N, p.D, p.group));
+  if (p.mode == MW_OZAKI)
+    off = align256(off + ozaki_partials_bytes(M, N, p.D, p.group,
+                                              narrow_partials(p.S_A, p.S_B, p.w, L.Kp)));
   L.total = off;
   return L;
 }
@@ -344,7 +346,7 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
   a.m = p.m; a.w = p.w; a.S_A = p.S_A; a.S_B = p.S_B; a.D = p.D; a.group = p.group;
   a.chunk = p.chunk; a.M = M; a.N = N; a.Kp = L.Kp;
   a.dA = w8 + L.digA; a.dB = w8 + L.digB; a.eA = o.eA; a.eB = o.eB;
-  a.partials = reinterpret_cast<int64_t *>(w8 + L.partials);
+  a.partials = w8 + L.partials;
   a.C = C; a.ldc = ldc; a.psc = psc;
   rc = launch_ozaki(a, s, [&] { phase(2, s); });
   phase(3, s);

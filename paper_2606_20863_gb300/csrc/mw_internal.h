@@ -46,7 +46,7 @@ struct OzakiArgs {
   int64_t M, N, Kp;
   const void *dA, *dB;          // bf16 pieces, S x rows x Kp
   const int32_t *eA, *eB;
-  int64_t *partials;            // [group][M][N], then the work counter
+  void *partials;               // partial sums (see narrow_partials), then the work counter
   double *C;
   int64_t ldc, psc;
 };
@@ -59,14 +59,18 @@ struct ProductLaunch {
   const void *info, *hdr;
   int count;
   int64_t M, N, K;
-  int64_t *partials;
+  void *partials;                 // int32 [t][M][N] (narrow) or int64 [g][M][N]
+  bool narrow;
   unsigned long long *next_item;  // work counter (reset by launch_product)
 };
 int launch_product(const ProductLaunch &a, cudaStream_t s);
 
 // between_kernels runs after the product kernel is launched, before the combine.
 int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels);
-size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group);
+// Every diagonal sum s_t fits in int32: S_min * K * 2^(2w-2) < 2^31.  Then the
+// partial sums are the int32 s_t [t][M][N]; otherwise int64 group sums [g][M][N].
+bool narrow_partials(int S_A, int S_B, int w, int64_t max_K);
+size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 
 // Number of diagonal groups.
 inline int n_groups(int D, int group) { return (D + group - 1) / group; }

@@ -32,6 +32,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "mw_device.cuh"
 #include "mw_fuse.cuh"
@@ -50,9 +51,16 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int STAGES = MW_STAGES;
 constexpr int NBUF = MW_ACC_BUFS;
-constexpr int NUM_DRAIN_WARPS = 8;
-constexpr int NUM_THREADS = 64 + 32 * NUM_DRAIN_WARPS;
 constexpr int TMEM_COLS = NBUF * BN;
+// Two drain modes.  Narrow: every diagonal sum s_t fits in int32 (checked by
+// the host), 16 drain warps of 32 columns accumulate each diagonal in 32-bit
+// registers (arithmetic mod 2^32) and store it as int32.  Wide: 8 drain warps
+// of 64 columns accumulate a group of diagonals by Horner's rule in int64.
+template <bool NARROW> struct Drain {
+  static constexpr int WARPS = NARROW ? 16 : 8;
+  static constexpr int COLS = NARROW ? 32 : 64;
+  static constexpr int THREADS = 64 + 32 * WARPS;
+};
 static_assert(NBUF == 2 || NBUF == 4, "2 or 4 accumulator buffers");
 constexpr uint32_t STAGE_A = BM * BK * 2, STAGE_B = BN * BK * 2;
 constexpr uint32_t MAGIC_BITS = 0x4B400000u;  // bit pattern of 1.5 * 2^23
@@ -68,7 +76,7 @@ struct PParams {
   int count;
   int S_A, S_B, D, w, group, G, chunk_kb;
   int64_t single_work;    // work items of `single`
-  int64_t *partials;
+  void *partials;         // int32 [t][M][N] (narrow) or int64 [g][M][N] (wide)
   unsigned long long *next_item;  // work counter, zero before the launch
   unsigned int *status;
   int gorder[MAX_GROUPS]; // diagonal groups, most expensive first
@@ -107,9 +115,11 @@ __device__ __forceinline__ int nsteps(const PParams &P, int t, int KB) {
   return n > 0 ? n * KB : 0;
 }
 
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+template <bool NARROW>
+__global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
     ozaki_kernel(const __grid_constant__ CUtensorMap mapA,
-                       const __grid_constant__ CUtensorMap mapB, const PParams P) {
+                 const __grid_constant__ CUtensorMap mapB, const PParams P) {
+  constexpr int NUM_DRAIN_WARPS = Drain<NARROW>::WARPS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;
@@ -229,12 +239,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mbar_wait(done, 0, P.status, &never);
     }
   } else {
-    const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
+    constexpr int COLS = Drain<NARROW>::COLS;
+    const int quarter = warp & 3;                 // TMEM lanes this warp may read
+    const int slice = (warp - 2) >> 2;            // which COLS columns of the tile
     const int row = quarter * 32 + lane;
-    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + half * 64;
+    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + slice * COLS;
     uint32_t ch = 0;
-    uint64_t acc[64];
     bool ok = true;
     for (uint32_t k = 0; ok; ++k) {
       const uint32_t slot = k % RING, rph = (k / RING) & 1;
@@ -244,49 +254,84 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (lane == 0) mbar_arrive(&ue[slot]);
       if (u < 0) break;
       const Item x = decode_item(P, u);
-#pragma unroll
-      for (int i = 0; i < 64; ++i) acc[i] = 0;
-      uint64_t bias = 0;
-      for (int t = x.t0; t <= x.t1 && ok; ++t) {
-        if (t > x.t0) {
-#pragma unroll
-          for (int i = 0; i < 64; ++i) acc[i] <<= P.w;
-          bias <<= P.w;
-        }
-        const int nch = (nsteps(P, t, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
-        bias += (uint64_t)nch * MAGIC_BITS;
-        for (int c = 0; c < nch; ++c, ++ch) {
-          const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
-          if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], bph, P.status, abort))) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          uint32_t v[32];
-          tc_ld32(tbase + b * BN, v);
-          tc_wait_ld();
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            acc[i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
-          tc_ld32(tbase + b * BN + 32, v);
-          tc_wait_ld();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acce[b]);
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            acc[32 + i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
-        }
-      }
-      if (!ok) break;
-      // partial sums of this group, compact per problem: [g][M][N]
       const int64_t r = (int64_t)x.tm * BM + row;
-      if (r < x.M) {
-        int64_t *dst = P.partials + x.part + ((int64_t)x.g * x.M + r) * x.N;
-        const int64_t c0 = (int64_t)x.tn * BN + half * 64;
+      const int64_t c0 = (int64_t)x.tn * BN + slice * COLS;
+      if constexpr (NARROW) {
+        // one diagonal at a time in 32-bit accumulators, stored as int32 s_t
+        for (int t = x.t0; t <= x.t1 && ok; ++t) {
+          uint32_t acc[32];
 #pragma unroll
-        for (int i = 0; i < 64; ++i)
-          if (c0 + i < x.N) dst[c0 + i] = (int64_t)(acc[i] - bias);
+          for (int i = 0; i < 32; ++i) acc[i] = 0;
+          const int nch = (nsteps(P, t, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
+          for (int c = 0; c < nch; ++c, ++ch) {
+            const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], bph, P.status, abort))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            uint32_t v[32];
+            tc_ld32(tbase + b * BN, v);
+            tc_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
+          }
+          if (!ok) break;
+          if (r < x.M) {
+            const uint32_t bias = (uint32_t)nch * MAGIC_BITS;
+            int32_t *dst = static_cast<int32_t *>(P.partials) + x.part + ((int64_t)t * x.M + r) * x.N;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < x.N) dst[c0 + i] = (int32_t)(acc[i] - bias);
+          }
+        }
+      } else {
+        uint64_t acc[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) acc[i] = 0;
+        uint64_t bias = 0;
+        for (int t = x.t0; t <= x.t1 && ok; ++t) {
+          if (t > x.t0) {
+#pragma unroll
+            for (int i = 0; i < 64; ++i) acc[i] <<= P.w;
+            bias <<= P.w;
+          }
+          const int nch = (nsteps(P, t, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
+          bias += (uint64_t)nch * MAGIC_BITS;
+          for (int c = 0; c < nch; ++c, ++ch) {
+            const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], bph, P.status, abort))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            uint32_t v[32];
+            tc_ld32(tbase + b * BN, v);
+            tc_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              acc[i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
+            tc_ld32(tbase + b * BN + 32, v);
+            tc_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              acc[32 + i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
+          }
+        }
+        if (!ok) break;
+        // the group's Horner sum, int64 [g][M][N]
+        if (r < x.M) {
+          int64_t *dst = static_cast<int64_t *>(P.partials) + x.part + ((int64_t)x.g * x.M + r) * x.N;
+#pragma unroll
+          for (int i = 0; i < 64; ++i)
+            if (c0 + i < x.N) dst[c0 + i] = (int64_t)(acc[i] - bias);
+        }
       }
     }
   }
@@ -306,9 +351,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
-// ---- fusion of one product: thread per output, partial sums [g][M][N] ---------
-template <int MW, int NL>
-__global__ void combine_kernel(const int64_t *__restrict__ partials, const int32_t *eA,
+// ---- fusion of one product: thread per output ---------------------------------
+// Narrow: D planes of int32 diagonal sums s_t, weight 2^(w (D-1-t)).
+// Wide:   G planes of int64 group sums, weight 2^(w (D-1-t1_g)).
+template <int MW, int NL, bool NARROW>
+__global__ void combine_kernel(const void *__restrict__ partials, const int32_t *eA,
                                const int32_t *eB, int64_t M, int64_t N, int G, int group, int D,
                                int w, double *C, int64_t ldc, int64_t psc) {
   const int64_t j = (int64_t)blockIdx.x * 128 + threadIdx.x, i = blockIdx.y;
@@ -316,9 +363,15 @@ __global__ void combine_kernel(const int64_t *__restrict__ partials, const int32
   uint64_t X[NL];
 #pragma unroll
   for (int k = 0; k < NL; ++k) X[k] = 0;
-  for (int g = 0; g < G; ++g) {
-    const int t1 = min(D, (g + 1) * group) - 1;
-    add_shifted<NL>(X, partials[((int64_t)g * M + i) * N + j], w * (D - 1 - t1));
+  if constexpr (NARROW) {
+    const int32_t *p = static_cast<const int32_t *>(partials);
+    for (int t = 0; t < D; ++t) add_shifted<NL>(X, p[((int64_t)t * M + i) * N + j], w * (D - 1 - t));
+  } else {
+    const int64_t *p = static_cast<const int64_t *>(partials);
+    for (int g = 0; g < G; ++g) {
+      const int t1 = min(D, (g + 1) * group) - 1;
+      add_shifted<NL>(X, p[((int64_t)g * M + i) * N + j], w * (D - 1 - t1));
+    }
   }
   double words[MW];
   round_words<MW, NL>(X, eA[i] + eB[j] + 4 - w * (D + 1), words);
@@ -327,21 +380,25 @@ __global__ void combine_kernel(const int64_t *__restrict__ partials, const int32
 }
 
 template <int MW, int NL>
-int launch_combine(const OzakiArgs &a, int G, cudaStream_t s) {
+int launch_combine(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
   dim3 grid((unsigned)((a.N + 127) / 128), (unsigned)a.M);
-  combine_kernel<MW, NL><<<grid, 128, 0, s>>>(a.partials, a.eA, a.eB, a.M, a.N, G, a.group, a.D,
-                                               a.w, a.C, a.ldc, a.psc);
+  if (narrow)
+    combine_kernel<MW, NL, true><<<grid, 128, 0, s>>>(a.partials, a.eA, a.eB, a.M, a.N, G, a.group,
+                                                      a.D, a.w, a.C, a.ldc, a.psc);
+  else
+    combine_kernel<MW, NL, false><<<grid, 128, 0, s>>>(a.partials, a.eA, a.eB, a.M, a.N, G,
+                                                       a.group, a.D, a.w, a.C, a.ldc, a.psc);
   return cuda_fail(cudaGetLastError(), "combine launch");
 }
 
 template <int MW>
-int launch_combine_nl(const OzakiArgs &a, int G, cudaStream_t s) {
+int launch_combine_nl(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
   // |X| < 2^(63 + w (D-1)) plus a sign bit
   const int bits = 64 + a.w * (a.D - 1) + 1;
-  if (bits <= 256) return launch_combine<MW, 4>(a, G, s);
-  if (bits <= 384) return launch_combine<MW, 6>(a, G, s);
-  if (bits <= 512) return launch_combine<MW, 8>(a, G, s);
-  if (bits <= 640) return launch_combine<MW, 10>(a, G, s);
+  if (bits <= 256) return launch_combine<MW, 4>(a, G, narrow, s);
+  if (bits <= 384) return launch_combine<MW, 6>(a, G, narrow, s);
+  if (bits <= 512) return launch_combine<MW, 8>(a, G, narrow, s);
+  if (bits <= 640) return launch_combine<MW, 10>(a, G, narrow, s);
   return fail(MW_EUNSUPPORTED, "D = %d diagonals of %d bits too many for the fusion", a.D, a.w);
 }
 
@@ -418,8 +475,11 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   if ((rc = make_map_2d(&mB, a.pieceB, a.Kpitch, a.rowsB))) return rc;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(ozaki_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ozaki_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SMEM_BYTES);
     if (e != cudaSuccess) return cuda_fail(e, "product kernel smem attribute");
     attr_set = true;
   }
@@ -430,18 +490,27 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int grid = nsm;
   if (!a.info) grid = (int)std::min<int64_t>(P.single_work, nsm);
-  ozaki_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(mA, mB, P);
+  if (a.narrow)
+    ozaki_kernel<true><<<grid, Drain<true>::THREADS, SMEM_BYTES, s>>>(mA, mB, P);
+  else
+    ozaki_kernel<false><<<grid, Drain<false>::THREADS, SMEM_BYTES, s>>>(mA, mB, P);
   return cuda_fail(cudaGetLastError(), "product kernel launch");
 }
 
-size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group) {
-  // partial sums [group][M][N], then the work counter
-  return (size_t)n_groups(D, group) * M * N * sizeof(int64_t) + 256;
+bool narrow_partials(int S_A, int S_B, int w, int64_t max_K) {
+  const int64_t S_min = std::min(S_A, S_B);
+  return (double)S_min * (double)max_K * std::ldexp(1.0, 2 * w - 2) < 2147483648.0;
+}
+
+size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow) {
+  // partial sums (int32 [t][M][N] or int64 [g][M][N]), then the work counter
+  return (narrow ? (size_t)D * 4 : (size_t)n_groups(D, group) * 8) * M * N + 256;
 }
 
 int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels) {
   if (a.Kp % BK) return fail(MW_EINVAL, "padded K must be a multiple of %d", BK);
   const int G = n_groups(a.D, a.group);
+  const bool narrow = narrow_partials(a.S_A, a.S_B, a.w, a.Kp);
   ProductLaunch L{};
   L.pieceA = a.dA; L.pieceB = a.dB;
   L.rowsA = (int64_t)a.S_A * a.M; L.rowsB = (int64_t)a.S_B * a.N; L.Kpitch = a.Kp;
@@ -449,15 +518,16 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
   L.info = nullptr; L.hdr = nullptr; L.count = 1;
   L.M = a.M; L.N = a.N; L.K = a.Kp;
   L.partials = a.partials;
+  L.narrow = narrow;
   L.next_item = reinterpret_cast<unsigned long long *>(
-      reinterpret_cast<uint8_t *>(a.partials) + (size_t)G * a.M * a.N * sizeof(int64_t));
+      reinterpret_cast<uint8_t *>(a.partials) + ozaki_partials_bytes(a.M, a.N, a.D, a.group, narrow) - 256);
   int rc = launch_product(L, s);
   if (rc) return rc;
   if (between_kernels) between_kernels();
   switch (a.m) {
-    case 2: return launch_combine_nl<2>(a, G, s);
-    case 4: return launch_combine_nl<4>(a, G, s);
-    case 8: return launch_combine_nl<8>(a, G, s);
+    case 2: return launch_combine_nl<2>(a, G, narrow, s);
+    case 4: return launch_combine_nl<4>(a, G, narrow, s);
+    case 8: return launch_combine_nl<8>(a, G, narrow, s);
   }
   return fail(MW_EINVAL, "m must be 2, 4 or 8");
 }

@@ -35,15 +35,26 @@ def run(mw, dev, A, B, plan, transA=False, transB=False):
     return C.cpu().numpy(), ws, off, (M, N, K)
 
 
-def partial_sums(ws, off, plan, M, N):
-    """The int64 partial sums of every diagonal group, shape (G, M, N)."""
+def narrow(plan, K):
+    """The library keeps int32 diagonal sums when they cannot overflow."""
+    Kp = -(-K // 64) * 64
+    return min(plan.S_A, plan.S_B) * Kp * 2 ** (2 * plan.w - 2) < 2 ** 31
+
+
+def partial_sums(ws, off, plan, M, N, K):
+    """Partial sums as the library stores them: (D, M, N) int32 diagonal sums or
+    (G, M, N) int64 group sums."""
+    if narrow(plan, K):
+        n = plan.D * M * N
+        return ws[off[3]:off[3] + 4 * n].view(torch.int32).cpu().numpy().astype(np.int64).reshape(plan.D, M, N)
     G = -(-plan.D // plan.group)
     n = G * M * N
-    raw = ws[off[3]:off[3] + 8 * n].view(torch.int64).cpu().numpy()
-    return raw.reshape(G, M, N)
+    return ws[off[3]:off[3] + 8 * n].view(torch.int64).cpu().numpy().reshape(G, M, N)
 
 
-def oracle_groups(sp, plan, a, b):
+def oracle_partials(sp, plan, K, a, b):
+    if narrow(plan, K):
+        return [int(x) for x in sp.s[:, a, b]]
     bounds = [(g * plan.group, min(plan.D, (g + 1) * plan.group) - 1)
               for g in range(-(-plan.D // plan.group))]
     return slicing.group_values(sp.s[:, a, b], plan.w, bounds)
@@ -57,12 +68,12 @@ def check_ozaki(mw, cuda, A, B, plan, transA=False, transB=False, rows=None, col
     cols = list(range(N)) if cols is None else cols
     sp = slicing.SlicedProduct(LA, LB, plan.w, plan.S_A, plan.S_B, plan.D, rows=rows, cols=cols)
     assert sp.A.in_range and sp.B.in_range
-    part = partial_sums(ws, off, plan, M, N)
+    part = partial_sums(ws, off, plan, M, N, K)
     ref = sp.result()
     for a, i in enumerate(rows):
         for b, j in enumerate(cols):
             got = [int(part[g, i, j]) for g in range(part.shape[0])]
-            assert got == oracle_groups(sp, plan, a, b), (i, j)
+            assert got == oracle_partials(sp, plan, K, a, b), (i, j)
     assert np.array_equal(C[:, rows][:, :, cols], ref)
     if bound:
         ratio = exact.ExactProduct(LA, LB, rows, cols).error_ratio(C)
@@ -101,15 +112,25 @@ def test_ozaki_transposes(mw, cuda, transA, transB):
 
 
 def test_ozaki_every_diagonal_sum(mw, cuda):
-    """group = 1: each partial sum is one diagonal sum s_t (Section 2 s_i)."""
+    """Each stored partial sum is one diagonal sum s_t (Section 2 s_i), both when
+    the library keeps them in 32 bits and, with group = 1, in 64 bits."""
     rng = SplitMix64(320)
     A, B = uniform_mdouble(rng, 2, 20, 300), uniform_mdouble(rng, 2, 300, 24)
     plan = mw.plan_for(to_dev(A, cuda), to_dev(B, cuda), "ozaki", group=1)
     C, ws, off, (M, N, K) = run(mw, cuda, A, B, plan)
     sp = slicing.SlicedProduct(A, B, plan.w, plan.S_A, plan.S_B, plan.D)
-    part = partial_sums(ws, off, plan, M, N)
-    assert np.array_equal(part, sp.s)
+    assert np.array_equal(partial_sums(ws, off, plan, M, N, K), sp.s)
     assert np.array_equal(C, sp.result())
+
+
+def test_ozaki_wide_partial_sums(mw, cuda):
+    """K long enough that diagonal sums may pass 2^31: 64-bit Horner groups."""
+    rng = SplitMix64(321)
+    K = 9000
+    A, B = uniform_mdouble(rng, 4, 40, K), uniform_mdouble(rng, 4, K, 30)
+    plan = mw.plan_for(to_dev(A, cuda), to_dev(B, cuda), "ozaki")
+    assert not narrow(plan, K) and plan.group > 1
+    check_ozaki(mw, cuda, A, B, plan, rows=[0, 17, 39], cols=[0, 29])
 
 
 @pytest.mark.parametrize("w,chunk", [(7, 1024), (7, 64), (8, 64), (6, 4096)])
