@@ -126,9 +126,10 @@ int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
  * offsets[1] pieces of op(A): S_A planes of M x Kp (Kp = K rounded up to 64),
  *            bfloat16 (MW_OZAKI) or double (MW_PLAIN), layout as in mw_split;
  * offsets[2] pieces of op(B)^T: S_B planes of N x Kp;
- * offsets[3] (MW_OZAKI) partial sums.  When min(S_A, S_B) * Kp * 2^(2w-2) < 2^31
- *            every diagonal sum fits in 32 bits and they are the int32 s_t,
- *            [t][M][N] for t < D; otherwise int64 [g][M][N], entry (g, i, j)
+ * offsets[3] (MW_OZAKI) partial sums, one column-major plane per entry (entry
+ *            (i, j) of a plane at j*M + i).  When min(S_A, S_B) * Kp * 2^(2w-2)
+ *            < 2^31 every diagonal sum fits in 32 bits and the planes are the
+ *            int32 s_t, t < D; otherwise int64 planes g < G holding
  *            V = sum_t s_t 2^(w (t1 - t)) over the diagonals of group g,
  *            [g*group, t1 = min(D, (g+1)*group) - 1].
  * bytes = total workspace size (same as mw_gemm_workspace_size). */

@@ -38,6 +38,7 @@ struct Layout {
   int64_t Kpitch;
   bool narrow;   // int32 diagonal sums (D planes) or int64 group sums (G planes)
   int planes;
+  int sched;     // diagonals per work item
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -57,6 +58,7 @@ Layout layout_of(const mw_plan &p, const mw_batch &b) {
   L.partials = off;
   L.narrow = narrow_partials(p.S_A, p.S_B, p.w, b.max_K);
   L.planes = L.narrow ? p.D : n_groups(p.D, p.group);
+  L.sched = sched_group(p.D, p.group, L.narrow);
   off = a256(off + (L.narrow ? 4 : 8) * (size_t)L.planes * b.sum_MN);
   L.total = off;
   return L;
@@ -216,29 +218,31 @@ __global__ void __launch_bounds__(256) batch_combine_kernel(const BInfo *info, c
   if (hdr->bad) return;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  // one warp per output column of some C_i, lanes along the rows (the partial
+  // planes are column-major, so the loads are contiguous)
   for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       task < hdr->sum_M; task += nwarps) {
-    const int i = find_problem(info, count, task, [](const BInfo &b) { return b.eA; });
+       task < hdr->sum_N; task += nwarps) {
+    const int i = find_problem(info, count, task, [](const BInfo &b) { return b.eB; });
     const BInfo &b = info[i];
-    const int64_t r = task - b.eA;
-    const int ea = eA[task];
-    for (int64_t j = lane; j < b.N; j += 32) {
+    const int64_t j = task - b.eB;
+    const int eb = eB[task];
+    for (int64_t r = lane; r < b.M; r += 32) {
       uint64_t X[NL];
 #pragma unroll
       for (int k = 0; k < NL; ++k) X[k] = 0;
       if constexpr (NARROW) {
         const int32_t *p = static_cast<const int32_t *>(partials) + b.part;
         for (int t = 0; t < D; ++t)
-          add_shifted<NL>(X, p[((int64_t)t * b.M + r) * b.N + j], w * (D - 1 - t));
+          add_shifted<NL>(X, p[((int64_t)t * b.N + j) * b.M + r], w * (D - 1 - t));
       } else {
         const int64_t *p = static_cast<const int64_t *>(partials) + b.part;
         for (int g = 0; g < G; ++g) {
           const int t1 = min(D, (g + 1) * group) - 1;
-          add_shifted<NL>(X, p[((int64_t)g * b.M + r) * b.N + j], w * (D - 1 - t1));
+          add_shifted<NL>(X, p[((int64_t)g * b.N + j) * b.M + r], w * (D - 1 - t1));
         }
       }
       double words[MW];
-      round_words<MW, NL>(X, ea + eB[b.eB + j] + 4 - w * (D + 1), words);
+      round_words<MW, NL>(X, eA[b.eA + r] + eb + 4 - w * (D + 1), words);
 #pragma unroll
       for (int k = 0; k < MW; ++k) b.C[k * b.psc + r * b.ldc + j] = words[k];
     }
@@ -290,7 +294,7 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
   BHeader *hdr = reinterpret_cast<BHeader *>(w8 + L.header);
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(BHeader), s);
   if (e != cudaSuccess) return cuda_fail(e, "batch header memset");
-  prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, n_groups(p.D, p.group), L.planes, p.S_A,
+  prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, n_groups(p.D, L.sched), L.planes, p.S_A,
                                      p.S_B, L.Kpitch, b, info, hdr, status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch prologue launch");
   const int bits = p.w * std::max(p.S_A, p.S_B) + 3;
@@ -403,7 +407,7 @@ int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem
   ProductLaunch P{};
   P.pieceA = w8 + L.pieceA; P.pieceB = w8 + L.pieceB;
   P.rowsA = (int64_t)p.S_A * b.sum_M; P.rowsB = (int64_t)p.S_B * b.sum_N; P.Kpitch = L.Kpitch;
-  P.S_A = p.S_A; P.S_B = p.S_B; P.D = p.D; P.w = p.w; P.group = p.group; P.chunk = p.chunk;
+  P.S_A = p.S_A; P.S_B = p.S_B; P.D = p.D; P.w = p.w; P.group = L.sched; P.chunk = p.chunk;
   P.info = w8 + L.info; P.hdr = w8 + L.header; P.count = b.count;
   P.partials = w8 + L.partials;
   P.narrow = L.narrow;

@@ -68,11 +68,20 @@ int launch_product(const ProductLaunch &a, cudaStream_t s);
 // between_kernels runs after the product kernel is launched, before the combine.
 int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels);
 // Every diagonal sum s_t fits in int32: S_min * K * 2^(2w-2) < 2^31.  Then the
-// partial sums are the int32 s_t [t][M][N]; otherwise int64 group sums [g][M][N].
+// partial sums are the int32 s_t, otherwise int64 group sums; every plane is
+// column-major (entry (i, j) at j M + i).
 bool narrow_partials(int S_A, int S_B, int w, int64_t max_K);
+size_t ozaki_partials_planes_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 
 // Number of diagonal groups.
 inline int n_groups(int D, int group) { return (D + group - 1) / group; }
+
+// Diagonals per work item of the product kernel.  Narrow partial sums are per
+// diagonal, so a work item can be a single diagonal (fine-grained load
+// balance, at most 64 items per tile); wide ones need the plan's int64 group.
+inline int sched_group(int D, int group, bool narrow) {
+  return narrow ? (D + 63) / 64 : group;
+}
 
 }  // namespace mw

@@ -281,11 +281,12 @@ __global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
           }
           if (!ok) break;
           if (r < x.M) {
+            // plane t is column-major: lanes (consecutive rows) store consecutive words
             const uint32_t bias = (uint32_t)nch * MAGIC_BITS;
-            int32_t *dst = static_cast<int32_t *>(P.partials) + x.part + ((int64_t)t * x.M + r) * x.N;
+            int32_t *dst = static_cast<int32_t *>(P.partials) + x.part + (int64_t)t * x.N * x.M + r;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (c0 + i < x.N) dst[c0 + i] = (int32_t)(acc[i] - bias);
+              if (c0 + i < x.N) dst[(c0 + i) * x.M] = (int32_t)(acc[i] - bias);
           }
         }
       } else {
@@ -325,12 +326,12 @@ __global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
           }
         }
         if (!ok) break;
-        // the group's Horner sum, int64 [g][M][N]
+        // the group's Horner sum, plane g column-major
         if (r < x.M) {
-          int64_t *dst = static_cast<int64_t *>(P.partials) + x.part + ((int64_t)x.g * x.M + r) * x.N;
+          int64_t *dst = static_cast<int64_t *>(P.partials) + x.part + (int64_t)x.g * x.N * x.M + r;
 #pragma unroll
           for (int i = 0; i < 64; ++i)
-            if (c0 + i < x.N) dst[c0 + i] = (int64_t)(acc[i] - bias);
+            if (c0 + i < x.N) dst[(c0 + i) * x.M] = (int64_t)(acc[i] - bias);
         }
       }
     }
@@ -354,23 +355,24 @@ __global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
 // ---- fusion of one product: thread per output ---------------------------------
 // Narrow: D planes of int32 diagonal sums s_t, weight 2^(w (D-1-t)).
 // Wide:   G planes of int64 group sums, weight 2^(w (D-1-t1_g)).
+// Planes are column-major (entry (i, j) at j M + i): threads run along i.
 template <int MW, int NL, bool NARROW>
 __global__ void combine_kernel(const void *__restrict__ partials, const int32_t *eA,
                                const int32_t *eB, int64_t M, int64_t N, int G, int group, int D,
                                int w, double *C, int64_t ldc, int64_t psc) {
-  const int64_t j = (int64_t)blockIdx.x * 128 + threadIdx.x, i = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
   if (i >= M || j >= N) return;
   uint64_t X[NL];
 #pragma unroll
   for (int k = 0; k < NL; ++k) X[k] = 0;
   if constexpr (NARROW) {
     const int32_t *p = static_cast<const int32_t *>(partials);
-    for (int t = 0; t < D; ++t) add_shifted<NL>(X, p[((int64_t)t * M + i) * N + j], w * (D - 1 - t));
+    for (int t = 0; t < D; ++t) add_shifted<NL>(X, p[((int64_t)t * N + j) * M + i], w * (D - 1 - t));
   } else {
     const int64_t *p = static_cast<const int64_t *>(partials);
     for (int g = 0; g < G; ++g) {
       const int t1 = min(D, (g + 1) * group) - 1;
-      add_shifted<NL>(X, p[((int64_t)g * M + i) * N + j], w * (D - 1 - t1));
+      add_shifted<NL>(X, p[((int64_t)g * N + j) * M + i], w * (D - 1 - t1));
     }
   }
   double words[MW];
@@ -381,7 +383,7 @@ __global__ void combine_kernel(const void *__restrict__ partials, const int32_t 
 
 template <int MW, int NL>
 int launch_combine(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
-  dim3 grid((unsigned)((a.N + 127) / 128), (unsigned)a.M);
+  dim3 grid((unsigned)((a.M + 127) / 128), (unsigned)a.N);
   if (narrow)
     combine_kernel<MW, NL, true><<<grid, 128, 0, s>>>(a.partials, a.eA, a.eB, a.M, a.N, G, a.group,
                                                       a.D, a.w, a.C, a.ldc, a.psc);
@@ -502,9 +504,14 @@ bool narrow_partials(int S_A, int S_B, int w, int64_t max_K) {
   return (double)S_min * (double)max_K * std::ldexp(1.0, 2 * w - 2) < 2147483648.0;
 }
 
+size_t ozaki_partials_planes_bytes(int64_t M, int64_t N, int D, int group, bool narrow) {
+  return (narrow ? (size_t)D * 4 : (size_t)n_groups(D, group) * 8) * M * N;
+}
+
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow) {
-  // partial sums (int32 [t][M][N] or int64 [g][M][N]), then the work counter
-  return (narrow ? (size_t)D * 4 : (size_t)n_groups(D, group) * 8) * M * N + 256;
+  // partial sums, then the 8-byte work counter at the next 256-byte boundary
+  const size_t planes = ozaki_partials_planes_bytes(M, N, D, group, narrow);
+  return ((planes + 255) & ~(size_t)255) + 256;
 }
 
 int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels) {
@@ -514,13 +521,15 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
   ProductLaunch L{};
   L.pieceA = a.dA; L.pieceB = a.dB;
   L.rowsA = (int64_t)a.S_A * a.M; L.rowsB = (int64_t)a.S_B * a.N; L.Kpitch = a.Kp;
-  L.S_A = a.S_A; L.S_B = a.S_B; L.D = a.D; L.w = a.w; L.group = a.group; L.chunk = a.chunk;
+  L.S_A = a.S_A; L.S_B = a.S_B; L.D = a.D; L.w = a.w; L.chunk = a.chunk;
+  L.group = sched_group(a.D, a.group, narrow);
   L.info = nullptr; L.hdr = nullptr; L.count = 1;
   L.M = a.M; L.N = a.N; L.K = a.Kp;
   L.partials = a.partials;
   L.narrow = narrow;
+  const size_t planes = ozaki_partials_planes_bytes(a.M, a.N, a.D, a.group, narrow);
   L.next_item = reinterpret_cast<unsigned long long *>(
-      reinterpret_cast<uint8_t *>(a.partials) + ozaki_partials_bytes(a.M, a.N, a.D, a.group, narrow) - 256);
+      reinterpret_cast<uint8_t *>(a.partials) + ((planes + 255) & ~(size_t)255));
   int rc = launch_product(L, s);
   if (rc) return rc;
   if (between_kernels) between_kernels();

@@ -46,10 +46,12 @@ def partial_sums(ws, off, plan, M, N, K):
     (G, M, N) int64 group sums."""
     if narrow(plan, K):
         n = plan.D * M * N
-        return ws[off[3]:off[3] + 4 * n].view(torch.int32).cpu().numpy().astype(np.int64).reshape(plan.D, M, N)
+        raw = ws[off[3]:off[3] + 4 * n].view(torch.int32).cpu().numpy().astype(np.int64)
+        return raw.reshape(plan.D, N, M).transpose(0, 2, 1)       # planes are column-major
     G = -(-plan.D // plan.group)
     n = G * M * N
-    return ws[off[3]:off[3] + 8 * n].view(torch.int64).cpu().numpy().reshape(G, M, N)
+    raw = ws[off[3]:off[3] + 8 * n].view(torch.int64).cpu().numpy()
+    return raw.reshape(G, N, M).transpose(0, 2, 1)
 
 
 def oracle_partials(sp, plan, K, a, b):
