@@ -49,6 +49,10 @@ def parse():
                     help="end-to-end runs from host memory (-1 = steps/4, at least 3; 0 = leave out)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows in the CPU sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--workload", default="qd1024",
+                    choices=["qd1024", "dd4096", "qd4096", "od_batch"],
+                    help="qd1024 (default): the benchmark line; the others measure the other "
+                         "configurations of the method")
     return ap.parse_args()
 
 
@@ -181,28 +185,82 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    import torch
-    import paper_2606_20863_gb300 as mw
+WORKLOADS = {
+    # name: (m, n, generator, description)
+    "qd1024": (4, 1024, "qd_1024", WORKLOAD),
+    "dd4096": (2, 4096, "ozaki_4096", "double-double GEMM M=N=K=4096, leading words 2^U[-20,20) "
+               "random sign, lower words x2^-53 U[-1,1), seed 2"),
+    "qd4096": (4, 4096, "ozaki_4096", "quad-double GEMM M=N=K=4096, leading words 2^U[-20,20) "
+               "random sign, lower words x2^-53 U[-1,1), seed 2"),
+}
 
-    dist, rank, world = dist_setup(args.gpus)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    A, B = make_inputs()
+
+def single_inputs(name):
+    import synthetic
+    m, n, gen, _ = WORKLOADS[name]
+    if gen == "qd_1024":
+        return synthetic.qd_1024(seed=1, n=n)
+    return synthetic.ozaki_4096(m, seed=2, n=n)
+
+
+def timed(step, steps, flush, mw, dist, dev, phase=True):
+    """Run `steps` steps with an untimed L2 flush before each; CUDA events on the
+    current stream; returns (per-step ms, product-kernel ms, clocks)."""
+    import torch
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    clocks = Clocks(dev.index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for s in range(steps):
+        flush.fill_(float(s))
+        if phase:
+            mw.set_phase_events(ev[s])
+        else:
+            ev[s][0].record()
+        step()
+        if not phase:
+            ev[s][3].record()
+    mw.set_phase_events(None)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    mw.check_status()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    kern_ms = [e[1].elapsed_time(e[2]) for e in ev] if phase else []
+    return step_ms, kern_ms, clk
+
+
+def roofline_of(pairs, flops_per_pair, kern_ms):
+    bf16_burst, _, _, peak_src = load_peaks()
+    kern_s = statistics.mean(kern_ms) / 1e3
+    achieved = pairs * flops_per_pair / kern_s / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
+            "frac": achieved / bf16_burst, "traffic": None,
+            "kernel": "ozaki_kernel (tcgen05 kind::f16, bf16 integer slices)",
+            "peak_source": f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json)",
+            "algorithmic": f"{pairs} slice pairs x {flops_per_pair:.4g} flop = "
+                           f"{pairs * flops_per_pair:.3e} flop per launch"}
+
+
+def count_pairs(plan):
+    return sum(1 for t in range(plan.D) for p in range(plan.S_A) if 0 <= t - p < plan.S_B)
+
+
+def run_single(args, name, mw, torch, dist, rank, world, dev):
+    m, n, _, desc = WORKLOADS[name]
+    A, B = single_inputs(name)
     tA = torch.from_numpy(A).to(dev)
     tB = torch.from_numpy(B).to(dev)
-    M = N = K = N_DIM
+    M = N = K = n
     flops = 2.0 * M * N * K
-
     plan = mw.plan_for(tA, tB, "ozaki")
     ws = torch.empty(mw.workspace_size(plan, M, N, K), dtype=torch.uint8, device=dev)
-    C = torch.empty((M_WORDS, M, N), dtype=torch.float64, device=dev)
+    C = torch.empty((m, M, N), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-    pairs = sum(1 for t in range(plan.D) for p in range(plan.S_A) if 0 <= t - p < plan.S_B)
+    pairs = count_pairs(plan)
 
     def step():
         mw.mw_gemm(tA, tB, plan, C=C, ws=ws, check=False)
@@ -211,25 +269,7 @@ def main():
         step()
     mw.check_status()
     torch.cuda.synchronize()
-
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    clocks = Clocks(dev.index)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    for s in range(args.steps):
-        flush.fill_(float(s))                                  # untimed L2 flush
-        mw.set_phase_events(ev[s])
-        step()
-    mw.set_phase_events(None)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    mw.check_status()
-    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
-    kern_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    step_ms, kern_ms, clk = timed(step, args.steps, flush, mw, dist, dev)
     value, t_step = aggregate(sum(step_ms) / 1e3, flops, args.steps, dist, dev)
 
     # plain FP64 form on the same operands and bound (the comparison of the metric)
@@ -239,16 +279,9 @@ def main():
         pws = torch.empty(mw.workspace_size(pplan, M, N, K), dtype=torch.uint8, device=dev)
         Cp = torch.empty_like(C)
         mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws)
-        pe = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.plain_steps)]
-        for s in range(args.plain_steps):
-            flush.fill_(float(s))
-            pe[2 * s].record()
-            mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws, check=False)
-            pe[2 * s + 1].record()
-        torch.cuda.synchronize()
-        mw.check_status()
-        plain_s = sum(pe[2 * s].elapsed_time(pe[2 * s + 1]) for s in range(args.plain_steps)) / 1e3
-        plain_gflops = flops * args.plain_steps / plain_s / 1e9
+        pms, _, _ = timed(lambda: mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws, check=False),
+                          args.plain_steps, flush, mw, None, dev, phase=False)
+        plain_gflops = flops * args.plain_steps / (sum(pms) / 1e3) / 1e9
         del pws, Cp
 
     # end to end through the public call: pinned host operands in, host result out
@@ -257,7 +290,7 @@ def main():
     if e2e_steps > 0:
         hA = torch.from_numpy(A).pin_memory()
         hB = torch.from_numpy(B).pin_memory()
-        hC = torch.empty((M_WORDS, M, N), dtype=torch.float64).pin_memory()
+        hC = torch.empty((m, M, N), dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
@@ -271,33 +304,102 @@ def main():
                "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
                "d2h_bytes_per_step": int(hC.numel() * 8)}
 
-    bf16_burst, bf16_sust, hbm, peak_src = load_peaks()
     kern_s = statistics.mean(kern_ms) / 1e3
-    achieved = pairs * flops / kern_s / 1e12
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
-                "frac": achieved / bf16_burst, "traffic": None,
-                "kernel": "ozaki_kernel (tcgen05 kind::f16, bf16 integer slices)",
-                "peak_source": f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json)",
-                "algorithmic": f"{pairs} slice pairs x 2MNK = {pairs * flops:.3e} flop per launch"}
-
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": M_WORDS, "M": M, "N": N, "K": K,
-                       "form": "Ozaki: bf16 integer slices on tcgen05, fp32 drained to int64",
+            "config": {"workload": desc, "m": m, "M": M, "N": N, "K": K,
+                       "form": "Ozaki: bf16 integer slices on tcgen05, fp32 drained to integers",
                        "plan": plan.as_dict(), "slice_pairs": pairs,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "plain_fp64_gflops": plain_gflops, "plain_plan": pplan.as_dict(),
                        "speedup_vs_plain": (value / world / plain_gflops) if plain_gflops else None,
-                       "product_kernel_ms": kern_s * 1e3,
-                       "step_ms_min": min(step_ms)},
-            "roofline": roofline, "clocks": clk, "e2e": e2e,
+                       "product_kernel_ms": kern_s * 1e3, "step_ms_min": min(step_ms)},
+            "roofline": roofline_of(pairs, flops, kern_ms), "clocks": clk, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps}
     if rank == 0 and not args.no_cpu:
         rows = args.cpu_rows or auto_rows(A, B)
-        line["cpu_baseline"] = cpu_baseline(A, B, rows, "quad double")
+        line["cpu_baseline"] = cpu_baseline(A, B, rows, desc.split(",")[0])
+    return line
+
+
+def run_batch(args, mw, torch, dist, rank, world, dev):
+    """20,000 octo-double products, n ~ U{8..128}, seed 3, one batched call
+    replayed from a CUDA graph per step."""
+    import synthetic
+    sizes = synthetic.batch_sizes(20000, 8, 128, seed=3)
+    FA, FB, offs = synthetic.batch_flat(sizes, m=8, seed=3)
+    dA, dB = torch.from_numpy(FA).to(dev), torch.from_numpy(FB).to(dev)
+    order = np.argsort(-sizes, kind="stable")
+    As, Bs = [], []
+    for i in order:
+        n, o = int(sizes[i]), int(offs[i])
+        As.append(dA[:, o:o + n * n].view(8, n, n))
+        Bs.append(dB[:, o:o + n * n].view(8, n, n))
+    batch = mw.Batch(As, Bs)
+    plan = batch.plan_
+    flops = float(np.sum(2.0 * sizes.astype(np.float64) ** 3))
+    pairs = count_pairs(plan)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    batch.run()
+    torch.cuda.synchronize()
+    mw.check_status()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            batch.run()
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    step_ms, _, clk = timed(g.replay, args.steps, flush, mw, dist, dev, phase=False)
+    value, t_step = aggregate(sum(step_ms) / 1e3, flops, args.steps, dist, dev)
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "20,000 octo-double products, n ~ U{8..128} square, entries "
+                                   "U[-1,1) with lower words x2^-53 U[-1,1), seed 3, one batched "
+                                   "call replayed from a CUDA graph",
+                       "m": 8, "count": 20000, "plan": plan.as_dict(), "slice_pairs": pairs,
+                       "useful_flop_per_step": flops,
+                       "l2": "flushed (256 MiB write) before every timed step"},
+            "roofline": None, "clocks": clk, "e2e": None, "gpu_launches": 4 * args.steps}
+    if rank == 0 and not args.no_cpu:
+        from oracle import textbook
+        tc = textbook.TextbookC()
+        sample = [int(i) for i in order[-400:]]          # 400 of the problems, small ones
+        t0 = time.perf_counter()
+        fl = 0.0
+        for i in sample:
+            n, o = int(sizes[i]), int(offs[i])
+            a = np.ascontiguousarray(FA[:, o:o + n * n].reshape(8, n, n))
+            b = np.ascontiguousarray(FB[:, o:o + n * n].reshape(8, n, n))
+            tc.gemm(a, b)
+            fl += 2.0 * n ** 3
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": fl / dt / 1e9, "unit": "GFLOP/s",
+                                "cores": tc.max_threads(), "kind": "oracle",
+                                "sample": f"400 smallest of the 20,000 problems, {dt:.2f} s"}
+    return line
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2606_20863_gb300 as mw
+
+    dist, rank, world = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if args.workload == "od_batch":
+        line = run_batch(args, mw, torch, dist, rank, world, dev)
+    else:
+        line = run_single(args, args.workload, mw, torch, dist, rank, world, dev)
     if rank == 0:
         print(json.dumps(line))
     if dist:

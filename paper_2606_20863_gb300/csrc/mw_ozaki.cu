@@ -42,30 +42,30 @@
 namespace mw {
 namespace {
 
-#ifndef MW_STAGES
-#define MW_STAGES 6      // TMA pipeline depth (32 KB per stage)
+#ifndef MW_WIDE_TILE
+#define MW_WIDE_TILE 1   // 0: always 128 x 128 tiles (build knob for comparisons)
 #endif
-#ifndef MW_ACC_BUFS
-#define MW_ACC_BUFS 2    // accumulators in tensor memory (128 columns each)
-#endif
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = MW_STAGES;
-constexpr int NBUF = MW_ACC_BUFS;
-constexpr int TMEM_COLS = NBUF * BN;
-// Two drain modes.  Narrow: every diagonal sum s_t fits in int32 (checked by
-// the host), 16 drain warps of 32 columns accumulate each diagonal in 32-bit
-// registers (arithmetic mod 2^32) and store it as int32.  Wide: 8 drain warps
-// of 64 columns accumulate a group of diagonals by Horner's rule in int64.
-template <bool NARROW> struct Drain {
-  static constexpr int WARPS = NARROW ? 16 : 8;
-  static constexpr int COLS = NARROW ? 32 : 64;
-  static constexpr int THREADS = 64 + 32 * WARPS;
-};
-static_assert(NBUF == 2 || NBUF == 4, "2 or 4 accumulator buffers");
-constexpr uint32_t STAGE_A = BM * BK * 2, STAGE_B = BN * BK * 2;
+constexpr int BM = 128, BK = 64;
+constexpr int NBUF = 2;             // accumulators in tensor memory
+constexpr uint32_t STAGE_A = BM * BK * 2;
 constexpr uint32_t MAGIC_BITS = 0x4B400000u;  // bit pattern of 1.5 * 2^23
-constexpr size_t SMEM_BYTES = 1024 + STAGES * (STAGE_A + STAGE_B) + 512;
-constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
+// Kernel shapes.  Tile 128 x BN (BN = 128 or 256); NBUF accumulators of BN fp32
+// columns in tensor memory.  Two drain modes.  Narrow: every diagonal sum s_t
+// fits in int32 (checked by the host), each diagonal is accumulated in 32-bit
+// registers (arithmetic mod 2^32) and stored as int32.  Wide: a group of
+// diagonals is accumulated by Horner's rule in int64 (BN = 128 only).
+template <int BN_, bool NARROW> struct Shape {
+  static constexpr int BN = BN_;
+  static constexpr int STAGES = BN == 256 ? 4 : 6;            // 48 KB / 32 KB per stage
+  static constexpr uint32_t STAGE_B = BN * BK * 2;
+  static constexpr int WARPS = (NARROW && BN == 128) ? 16 : 8;  // drain warps
+  static constexpr int COLS = BN * 4 / WARPS;                 // columns per drain thread
+  static constexpr int THREADS = 64 + 32 * WARPS;
+  static constexpr int TMEM_COLS = NBUF * BN;
+  static constexpr size_t SMEM = 1024 + STAGES * (STAGE_A + STAGE_B) + 512;
+  static_assert(NARROW || BN == 128, "wide drain only with 128-column tiles");
+  static_assert(TMEM_COLS <= 512, "tensor memory holds 512 columns");
+};
 
 constexpr int MAX_GROUPS = 64;
 constexpr int RING = 4;   // work items the producer may run ahead
@@ -115,11 +115,15 @@ __device__ __forceinline__ int nsteps(const PParams &P, int t, int KB) {
   return n > 0 ? n * KB : 0;
 }
 
-template <bool NARROW>
-__global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
+template <int BN_, bool NARROW>
+__global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
     ozaki_kernel(const __grid_constant__ CUtensorMap mapA,
                  const __grid_constant__ CUtensorMap mapB, const PParams P) {
-  constexpr int NUM_DRAIN_WARPS = Drain<NARROW>::WARPS;
+  using SH = Shape<BN_, NARROW>;
+  constexpr int BN = SH::BN, STAGES = SH::STAGES, TMEM_COLS = SH::TMEM_COLS;
+  constexpr uint32_t STAGE_B = SH::STAGE_B;
+  constexpr int NUM_DRAIN_WARPS = SH::WARPS;
+  constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
       mbar_wait(done, 0, P.status, &never);
     }
   } else {
-    constexpr int COLS = Drain<NARROW>::COLS;
+    constexpr int COLS = SH::COLS;
     const int quarter = warp & 3;                 // TMEM lanes this warp may read
     const int slice = (warp - 2) >> 2;            // which COLS columns of the tile
     const int row = quarter * 32 + lane;
@@ -259,9 +263,9 @@ __global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
       if constexpr (NARROW) {
         // one diagonal at a time in 32-bit accumulators, stored as int32 s_t
         for (int t = x.t0; t <= x.t1 && ok; ++t) {
-          uint32_t acc[32];
+          uint32_t acc[COLS];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[i] = 0;
+          for (int i = 0; i < COLS; ++i) acc[i] = 0;
           const int nch = (nsteps(P, t, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
           for (int c = 0; c < nch; ++c, ++ch) {
             const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
@@ -270,14 +274,20 @@ __global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
               break;
             }
             tc_fence_after();
-            uint32_t v[32];
-            tc_ld32(tbase + b * BN, v);
-            tc_wait_ld();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[b]);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
+            for (int h = 0; h < COLS / 32; ++h) {
+              uint32_t v[32];
+              tc_ld32(tbase + b * BN + 32 * h, v);
+              tc_wait_ld();
+              if (h == COLS / 32 - 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[b]);
+              }
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                acc[32 * h + i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
+            }
           }
           if (!ok) break;
           if (r < x.M) {
@@ -285,7 +295,7 @@ __global__ void __launch_bounds__(Drain<NARROW>::THREADS, 1)
             const uint32_t bias = (uint32_t)nch * MAGIC_BITS;
             int32_t *dst = static_cast<int32_t *>(P.partials) + x.part + (int64_t)t * x.N * x.M + r;
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
+            for (int i = 0; i < COLS; ++i)
               if (c0 + i < x.N) dst[(c0 + i) * x.M] = (int32_t)(acc[i] - bias);
           }
         }
@@ -411,7 +421,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 // 2D map over a bf16 array of `rows` rows of `pitch` elements; boxes of 64 x 128,
 // 128-byte swizzle (the layout sw128_desc describes).
-int make_map_2d(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows) {
+int make_map_2d(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows, int box_rows) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -424,7 +434,7 @@ int make_map_2d(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows)
   if (!fn) return fail(MW_ECUDA, "cuTensorMapEncodeTiled not available");
   cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
-  cuuint32_t box[2] = {BK, BM};
+  cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -443,6 +453,9 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
     return fail(MW_EINVAL, "chunk * 2^(2w-2) must not exceed 2^22 (w=%d chunk=%d)", a.w, a.chunk);
   if (a.rowsA > 0x7fffffffLL || a.rowsB > 0x7fffffffLL)
     return fail(MW_EUNSUPPORTED, "more than 2^31 piece rows");
+  // 128 x 256 tiles for a single wide product in narrow mode (half the A-operand
+  // traffic per flop); batches of small products keep 128 x 128.
+  const int bn = (MW_WIDE_TILE && a.narrow && !a.info && a.N >= 256) ? 256 : 128;
   PParams P{};
   P.info = static_cast<const BInfo *>(a.info);
   P.hdr = static_cast<const BHeader *>(a.hdr);
@@ -456,7 +469,7 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
     BInfo &b = P.single;
     b.M = a.M; b.N = a.N; b.K = a.K;
     b.tiles_m = (int)((a.M + BM - 1) / BM);
-    b.tiles_n = (int)((a.N + BN - 1) / BN);
+    b.tiles_n = (int)((a.N + bn - 1) / bn);
     b.KB = (int)((a.K + BK - 1) / BK);
     P.single_work = (int64_t)G * b.tiles_m * b.tiles_n;
   }
@@ -472,16 +485,20 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
     for (int j = i; j > 0 && cost[P.gorder[j]] > cost[P.gorder[j - 1]]; --j)
       std::swap(P.gorder[j], P.gorder[j - 1]);
   CUtensorMap mA, mB;
-  int rc = make_map_2d(&mA, a.pieceA, a.Kpitch, a.rowsA);
+  int rc = make_map_2d(&mA, a.pieceA, a.Kpitch, a.rowsA, BM);
   if (rc) return rc;
-  if ((rc = make_map_2d(&mB, a.pieceB, a.Kpitch, a.rowsB))) return rc;
+  if ((rc = make_map_2d(&mB, a.pieceB, a.Kpitch, a.rowsB, bn))) return rc;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(ozaki_kernel<128, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Shape<128, true>::SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ozaki_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)SMEM_BYTES);
+      e = cudaFuncSetAttribute(ozaki_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Shape<128, false>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ozaki_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Shape<256, true>::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "product kernel smem attribute");
     attr_set = true;
   }
@@ -492,10 +509,12 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int grid = nsm;
   if (!a.info) grid = (int)std::min<int64_t>(P.single_work, nsm);
-  if (a.narrow)
-    ozaki_kernel<true><<<grid, Drain<true>::THREADS, SMEM_BYTES, s>>>(mA, mB, P);
+  if (a.narrow && bn == 256)
+    ozaki_kernel<256, true><<<grid, Shape<256, true>::THREADS, Shape<256, true>::SMEM, s>>>(mA, mB, P);
+  else if (a.narrow)
+    ozaki_kernel<128, true><<<grid, Shape<128, true>::THREADS, Shape<128, true>::SMEM, s>>>(mA, mB, P);
   else
-    ozaki_kernel<false><<<grid, Drain<false>::THREADS, SMEM_BYTES, s>>>(mA, mB, P);
+    ozaki_kernel<128, false><<<grid, Shape<128, false>::THREADS, Shape<128, false>::SMEM, s>>>(mA, mB, P);
   return cuda_fail(cudaGetLastError(), "product kernel launch");
 }
 
