@@ -204,7 +204,10 @@ __global__ void __launch_bounds__(256) batch_split_kernel(
         x0[j] = v0 ? base[j * ps + k * kstride] : 0.0;
         x1[j] = v1 ? base[j * ps + (k + 1) * kstride] : 0.0;
       }
-      cut_pair<MW, NL, __nv_bfloat16>(x0, x1, F, w, S, dst + k, rows * Kpitch, status);
+      if (w == 8)
+        cut_pair_w8<MW, NL, __nv_bfloat16>(x0, x1, F, S, dst + k, rows * Kpitch, status);
+      else
+        cut_pair<MW, NL, __nv_bfloat16>(x0, x1, F, w, S, dst + k, rows * Kpitch, status);
     }
   }
 }

@@ -118,5 +118,42 @@ __device__ __forceinline__ void cut_pair(const double (&w0)[MW], const double (&
   store2<Out>(dst, (int)t0 + c0, (int)t1 + c1);
 }
 
+// The same for w = 8: the digits are the bytes of T (byte k = limb k/8, byte
+// k%8, least significant first), so no multi-limb shifts are needed.
+template <int MW, int NL, typename Out>
+__device__ __forceinline__ void cut_pair_w8(const double (&w0)[MW], const double (&w1)[MW], int F,
+                                            int S, Out *dst, int64_t plane, unsigned int *status) {
+  uint64_t T0[NL], T1[NL];
+  fixed_point<MW, NL>(w0, F, T0);
+  fixed_point<MW, NL>(w1, F, T1);
+  int c0 = 0, c1 = 0;
+  bool ok = true;
+  int top0 = 0, top1 = 0;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = 8 * i + j;
+      const int b0 = (int)((T0[i] >> (8 * j)) & 0xFF), b1 = (int)((T1[i] >> (8 * j)) & 0xFF);
+      if (k < S - 1) {
+        int r0 = b0 + c0, r1 = b1 + c1;
+        c0 = r0 >= 128;
+        c1 = r1 >= 128;
+        r0 -= c0 << 8;
+        r1 -= c1 << 8;
+        store2<Out>(dst + (int64_t)(S - 1 - k) * plane, r0, r1);
+      } else if (k == S - 1) {
+        top0 = (int)(int8_t)b0;  // T >> 8(S-1) must be a signed byte
+        top1 = (int)(int8_t)b1;
+      } else {
+        // bytes above the top digit: sign extension of the top byte
+        ok &= b0 == (top0 < 0 ? 0xFF : 0) && b1 == (top1 < 0 ? 0xFF : 0);
+      }
+    }
+  }
+  if (!ok) raise_status(status, MW_ERANGE);
+  store2<Out>(dst, top0 + c0, top1 + c1);
+}
+
 }  // namespace
 }  // namespace mw

@@ -138,7 +138,10 @@ __global__ void pieces_rows_kernel(const double *__restrict__ X, int64_t R, int6
     }
   }
   const int F = w * S - 2 - E[r];
-  cut_pair<MW, NL, Out>(a, b, F, w, S, digits + r * dld + k, R * dld, status);
+  if (w == 8)
+    cut_pair_w8<MW, NL, Out>(a, b, F, S, digits + r * dld + k, R * dld, status);
+  else
+    cut_pair<MW, NL, Out>(a, b, F, w, S, digits + r * dld + k, R * dld, status);
 }
 
 // trans = 1: 32 x 32 tiles (32 rows r, 32 columns k of the logical operand)
@@ -172,7 +175,10 @@ __global__ void pieces_cols_kernel(const double *__restrict__ X, int64_t R, int6
       b[j] = tile[(j * 32 + kl + 1) * 33 + rl];
     }
     const int F = w * S - 2 - E[r];
-    cut_pair<MW, NL, Out>(a, b, F, w, S, digits + r * dld + k, R * dld, status);
+    if (w == 8)
+      cut_pair_w8<MW, NL, Out>(a, b, F, S, digits + r * dld + k, R * dld, status);
+    else
+      cut_pair<MW, NL, Out>(a, b, F, w, S, digits + r * dld + k, R * dld, status);
   }
 }
 
