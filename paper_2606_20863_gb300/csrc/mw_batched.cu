@@ -234,15 +234,8 @@ __global__ void __launch_bounds__(256) batch_combine_kernel(const BInfo *info, c
 #pragma unroll
       for (int k = 0; k < NL; ++k) X[k] = 0;
       if constexpr (NARROW) {
-        // Horner in int64 over each group of diagonals, then one multi-limb add
-        const int32_t *p = static_cast<const int32_t *>(partials) + b.part + j * b.M + r;
-        const int64_t plane = b.N * b.M;
-        for (int g = 0; g < G; ++g) {
-          const int t0 = g * group, t1 = min(D, t0 + group) - 1;
-          int64_t V = 0;
-          for (int t = t0; t <= t1; ++t) V = (int64_t)((uint64_t)V << w) + p[t * plane];
-          add_shifted<NL>(X, V, w * (D - 1 - t1));
-        }
+        fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + b.part + j * b.M + r,
+                           b.N * b.M, D, group, w);
       } else {
         const int64_t *p = static_cast<const int64_t *>(partials) + b.part;
         for (int g = 0; g < G; ++g) {

@@ -60,6 +60,34 @@ __device__ __forceinline__ void add_shifted(uint64_t (&X)[NL], int64_t V, int sh
   }
 }
 
+// X += sum_t s_t 2^(w (D-1-t)) for the int32 diagonal sums s_t = p[t * plane]:
+// 32 independent loads at a time, then Horner in int64 over each group of
+// `group` consecutive diagonals (exact for the planner's group size) and one
+// multi-limb add per group.
+template <int NL>
+__device__ __forceinline__ void fuse_diagonals(uint64_t (&X)[NL], const int32_t *p, int64_t plane,
+                                               int D, int group, int w) {
+  int64_t V = 0;
+  int in_group = 0;
+  for (int t0 = 0; t0 < D; t0 += 32) {
+    int32_t s[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) s[u] = (t0 + u < D) ? p[(int64_t)(t0 + u) * plane] : 0;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int t = t0 + u;
+      if (t < D) {
+        V = (int64_t)((uint64_t)V << w) + s[u];
+        if (++in_group == group || t == D - 1) {
+          add_shifted<NL>(X, V, w * (D - 1 - t));
+          V = 0;
+          in_group = 0;
+        }
+      }
+    }
+  }
+}
+
 template <int MW, int NL>
 __device__ __forceinline__ void round_words(uint64_t (&X)[NL], int ex, double (&words)[MW]) {
 #pragma unroll

@@ -376,16 +376,7 @@ __global__ void combine_kernel(const void *__restrict__ partials, const int32_t 
 #pragma unroll
   for (int k = 0; k < NL; ++k) X[k] = 0;
   if constexpr (NARROW) {
-    // Horner in int64 over each group of diagonals (exact: the planner's group
-    // bound), then one multi-limb add per group
-    const int32_t *p = static_cast<const int32_t *>(partials) + j * M + i;
-    const int64_t plane = N * M;
-    for (int g = 0; g < G; ++g) {
-      const int t0 = g * group, t1 = min(D, t0 + group) - 1;
-      int64_t V = 0;
-      for (int t = t0; t <= t1; ++t) V = (int64_t)((uint64_t)V << w) + p[t * plane];
-      add_shifted<NL>(X, V, w * (D - 1 - t1));
-    }
+    fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + j * M + i, N * M, D, group, w);
   } else {
     const int64_t *p = static_cast<const int64_t *>(partials);
     for (int g = 0; g < G; ++g) {
