@@ -58,7 +58,9 @@ Layout layout_of(const mw_plan &p, const mw_batch &b) {
   L.partials = off;
   L.narrow = narrow_partials(p.S_A, p.S_B, p.w, b.max_K);
   L.planes = L.narrow ? p.D : n_groups(p.D, p.group);
-  L.sched = sched_group(p.D, p.group, L.narrow);
+  // one work item per (problem, tile) with every diagonal: batches hold many
+  // small problems, and every item costs a search of the problem table
+  L.sched = L.narrow ? p.D : p.group;
   off = a256(off + (L.narrow ? 4 : 8) * (size_t)L.planes * b.sum_MN);
   L.total = off;
   return L;
