@@ -245,6 +245,33 @@ def roofline_of(pairs, flops_per_pair, kern_ms):
                            f"{pairs * flops_per_pair:.3e} flop per launch"}
 
 
+TABLE1_MUL_ADD = {2: 43, 4: 425, 8: 2011}   # Table 1: double ops of one m-double add + mul
+
+
+def measure_pipes(torch, dev):
+    """FP64 and INT8 throughput of this GPU through the library GEMMs of torch
+    (cuBLAS): the denominators of the plain form and the INT8 context."""
+    def best(f, flops, n=3):
+        f(); torch.cuda.synchronize()
+        t = []
+        for _ in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(); f(); b.record(); b.synchronize()
+            t.append(a.elapsed_time(b) / 1e3)
+        return flops / min(t) / 1e12
+    n = 4096
+    x = torch.randn(n, n, dtype=torch.float64, device=dev)
+    fp64 = best(lambda: x @ x, 2.0 * n ** 3)
+    del x
+    xi = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
+    yi = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev).t().contiguous().t()
+    try:
+        int8 = best(lambda: torch._int_mm(xi, yi), 2.0 * n ** 3)
+    except Exception:
+        int8 = None
+    return fp64, int8
+
+
 def count_pairs(plan):
     return sum(1 for t in range(plan.D) for p in range(plan.S_A) if 0 <= t - p < plan.S_B)
 
@@ -305,6 +332,16 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
                "d2h_bytes_per_step": int(hC.numel() * 8)}
 
     kern_s = statistics.mean(kern_ms) / 1e3
+    fp64_peak, int8_peak = measure_pipes(torch, dev)
+    plain_roof = None
+    if plain_gflops:
+        ppairs = count_pairs(pplan)
+        roof = 2.0 * fp64_peak * 1e3 / TABLE1_MUL_ADD[m]          # GFLOP/s of m-double flops
+        plain_roof = {"bound": "fp64", "achieved": plain_gflops, "unit": "GFLOP/s",
+                      "peak_from_table1": roof, "frac_of_table1_roofline": plain_gflops / roof,
+                      "fp64_pipe_tflops": ppairs * flops * plain_gflops / flops / 1e3,
+                      "fp64_pipe_frac": ppairs * plain_gflops / 1e3 / fp64_peak,
+                      "fp64_peak_tflops_measured": fp64_peak}
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
@@ -316,7 +353,11 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "plain_fp64_gflops": plain_gflops, "plain_plan": pplan.as_dict(),
                        "speedup_vs_plain": (value / world / plain_gflops) if plain_gflops else None,
-                       "product_kernel_ms": kern_s * 1e3, "step_ms_min": min(step_ms)},
+                       "product_kernel_ms": kern_s * 1e3, "step_ms_min": min(step_ms),
+                       "plain_roofline": plain_roof,
+                       "int8_peak_tops_measured": int8_peak,
+                       "slice_ops_per_s_over_int8_peak":
+                           (pairs * flops / kern_s / 1e12 / int8_peak) if int8_peak else None},
             "roofline": roofline_of(pairs, flops, kern_ms), "clocks": clk, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps}
     if rank == 0 and not args.no_cpu:

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
                                                         mw_batch want, BInfo *info, BHeader *hdr,
                                                         unsigned int *status) {
   __shared__ int64_t sh[33];
-  int64_t cM = 0, cN = 0, cMN = 0, cW = 0;
+  int64_t cM = 0, cN = 0, cMN = 0, cW = 0, cS = 0;
   int bad = 0;
   for (int base = 0; base < count; base += 1024) {
     const int i = base + threadIdx.x;
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
     const int64_t pN = block_exclusive_scan(N, sh) + cN; const int64_t tN = sh[32];
     const int64_t pMN = block_exclusive_scan(M * N, sh) + cMN; const int64_t tMN = sh[32];
     const int64_t pW = block_exclusive_scan(w, sh) + cW; const int64_t tW = sh[32];
+    const int64_t pS = block_exclusive_scan((N + 31) / 32, sh) + cS; const int64_t tS = sh[32];
     if (i < count) {
       BInfo b{};
       b.M = M; b.N = N; b.K = K;
@@ -127,53 +128,46 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
       b.B = p.B; b.ldb = p.ldb; b.psb = p.plane_stride_b;
       b.C = p.C; b.ldc = p.ldc; b.psc = p.plane_stride_c;
       b.rowA = (int64_t)S_A * pM; b.rowB = (int64_t)S_B * pN;
-      b.eA = pM; b.eB = pN; b.part = (int64_t)planes * pMN; b.work = pW;
+      b.eA = pM; b.eB = pN; b.part = (int64_t)planes * pMN; b.work = pW; b.outs = pMN; b.stripes = pS;
       b.tiles_m = tm; b.tiles_n = tn; b.KB = (int)((K + BK - 1) / BK);
       info[i] = b;
     }
-    cM += tM; cN += tN; cMN += tMN; cW += tW;
+    cM += tM; cN += tN; cMN += tMN; cW += tW; cS += tS;
   }
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     if (cM != want.sum_M || cN != want.sum_N || cMN != want.sum_MN) bad = 1;
     hdr->sum_M = cM; hdr->sum_N = cN; hdr->sum_MN = cMN; hdr->total_work = bad ? 0 : cW;
+    hdr->sum_stripes = cS;
     hdr->bad = bad;
     if (bad) raise_status(status, MW_EINVAL);
   }
 }
 
 // ---- 2. split ---------------------------------------------------------------------
-// One warp per row of some A_i (tasks [0, sum_M)) or column of some B_i
-// (tasks [sum_M, sum_M + sum_N)).
+// Rows of the A_i: one warp per row (k contiguous, coalesced reads); the shared
+// exponent by a warp reduction, then the balanced pieces of the row.
 template <int MW, int NL>
-__global__ void __launch_bounds__(256) batch_split_kernel(
-    const BInfo *info, const BHeader *hdr, int count, int w, int S_A, int S_B,
-    int64_t Kpitch, __nv_bfloat16 *pieceA, __nv_bfloat16 *pieceB, int32_t *eA, int32_t *spA,
-    int32_t *eB, int32_t *spB, int32_t *max_spread, int range_A, int range_B, int exps_only,
-    unsigned int *status) {
+__global__ void __launch_bounds__(256) batch_split_rows_kernel(
+    const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
+    __nv_bfloat16 *pieceA, int32_t *eA, int32_t *spA, int32_t *max_spread, int range,
+    int exps_only, unsigned int *status) {
   if (hdr->bad) return;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t sum_M = hdr->sum_M, total = hdr->sum_M + hdr->sum_N;
-  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < total;
-       task += nwarps) {
-    const bool isA = task < sum_M;
-    const int i = isA ? find_problem(info, count, task, [](const BInfo &b) { return b.eA; })
-                      : find_problem(info, count, task - sum_M,
-                                     [](const BInfo &b) { return b.eB; });
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       task < hdr->sum_M; task += nwarps) {
+    const int i = find_problem(info, count, task, [](const BInfo &b) { return b.eA; });
     const BInfo &b = info[i];
-    const int64_t r = isA ? task - b.eA : task - sum_M - b.eB;  // row of A_i / column of B_i
-    const int64_t K = b.K;
-    // entry k of the row: A_i[r][k] or B_i[k][r]
-    const double *base = isA ? b.A + r * b.lda : b.B + r;
-    const int64_t kstride = isA ? 1 : b.ldb, ps = isA ? b.psa : b.psb;
+    const int64_t r = task - b.eA, K = b.K;
+    const double *base = b.A + r * b.lda;
     int emax = kExpZero, emin = -kExpZero;
     bool nonfinite = false;
     for (int64_t k = lane; k < K; k += 32) {
       int e = kExpZero;
 #pragma unroll
       for (int j = 0; j < MW; ++j) {
-        const int x = exp_plus1(base[j * ps + k * kstride]);
+        const int x = exp_plus1(base[j * b.psa + k]);
         if (x == kExpNonFinite) nonfinite = true;
         else e = max(e, x);
       }
@@ -187,69 +181,168 @@ __global__ void __launch_bounds__(256) batch_split_kernel(
     const int E = emax == kExpZero ? 0 : emax;
     const int sp = emax == kExpZero ? 0 : emax - emin;
     if (lane == 0) {
-      (isA ? eA : eB)[task - (isA ? 0 : sum_M)] = E;
-      (isA ? spA : spB)[task - (isA ? 0 : sum_M)] = sp;
-      atomicMax(max_spread + (isA ? 0 : 1), sp);
-      const int rg = isA ? range_A : range_B;
-      if (rg >= 0 && sp > rg) raise_status(status, MW_WRANGE);
+      eA[task] = E;
+      spA[task] = sp;
+      atomicMax(max_spread, sp);
+      if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
     }
     if (exps_only) continue;
-    const int S = isA ? S_A : S_B;
-    const int64_t rows = isA ? b.M : b.N;
-    __nv_bfloat16 *dst = (isA ? pieceA + (b.rowA + r) * Kpitch : pieceB + (b.rowB + r) * Kpitch);
+    __nv_bfloat16 *dst = pieceA + (b.rowA + r) * Kpitch;
+    const int64_t plane = b.M * Kpitch;
     const int F = w * S - 2 - E;
     for (int64_t k = 2 * lane; k < Kpitch; k += 64) {
+      if (k >= K) {  // zero padding: no arithmetic
+        for (int p = 0; p < S; ++p) store2<__nv_bfloat16>(dst + k + p * plane, 0, 0);
+        continue;
+      }
       double x0[MW], x1[MW];
-      const bool v0 = k < K, v1 = k + 1 < K;
+      const bool v1 = k + 1 < K;
 #pragma unroll
       for (int j = 0; j < MW; ++j) {
-        x0[j] = v0 ? base[j * ps + k * kstride] : 0.0;
-        x1[j] = v1 ? base[j * ps + (k + 1) * kstride] : 0.0;
+        x0[j] = base[j * b.psa + k];
+        x1[j] = v1 ? base[j * b.psa + k + 1] : 0.0;
       }
       if (w == 8)
-        cut_pair_w8<MW, NL, __nv_bfloat16>(x0, x1, F, S, dst + k, rows * Kpitch, status);
+        cut_pair_w8<MW, NL, __nv_bfloat16>(x0, x1, F, S, dst + k, plane, status);
       else
-        cut_pair<MW, NL, __nv_bfloat16>(x0, x1, F, w, S, dst + k, rows * Kpitch, status);
+        cut_pair<MW, NL, __nv_bfloat16>(x0, x1, F, w, S, dst + k, plane, status);
     }
   }
 }
 
+// Columns of the B_i: one CTA (32 x 8 threads) per 32-column stripe of one
+// problem.  Pass 1 reads rows of the stripe (coalesced) and reduces the column
+// exponents in shared memory; pass 2 stages 32 x 32 tiles of the stripe in
+// shared memory and cuts them so that the pieces are written k-contiguous.
+template <int MW, int NL>
+__global__ void __launch_bounds__(256) batch_split_cols_kernel(
+    const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
+    __nv_bfloat16 *pieceB, int32_t *eB, int32_t *spB, int32_t *max_spread, int range,
+    int exps_only, unsigned int *status) {
+  extern __shared__ double tile[];              // [MW][32 k][33]
+  __shared__ int smax[8][32], smin[8][32], sE[32];
+  if (hdr->bad) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t task = blockIdx.x; task < hdr->sum_stripes; task += gridDim.x) {
+    const int i = find_problem(info, count, task, [](const BInfo &b) { return b.stripes; });
+    const BInfo &b = info[i];
+    const int64_t j0 = (task - b.stripes) * 32, K = b.K;
+    const int64_t j = j0 + tx;
+    int emax = kExpZero, emin = -kExpZero;
+    bool nonfinite = false;
+    if (j < b.N)
+      for (int64_t k = ty; k < K; k += 8) {
+        int e = kExpZero;
+#pragma unroll
+        for (int q = 0; q < MW; ++q) {
+          const int x = exp_plus1(b.B[q * b.psb + k * b.ldb + j]);
+          if (x == kExpNonFinite) nonfinite = true;
+          else e = max(e, x);
+        }
+        if (e != kExpZero) { emax = max(emax, e); emin = min(emin, e); }
+      }
+    if (nonfinite) raise_status(status, MW_ENONFINITE);
+    smax[ty][tx] = emax;
+    smin[ty][tx] = emin;
+    __syncthreads();
+    if (ty == 0) {
+      for (int y = 1; y < 8; ++y) {
+        emax = max(emax, smax[y][tx]);
+        emin = min(emin, smin[y][tx]);
+      }
+      const int E = emax == kExpZero ? 0 : emax;
+      const int sp = emax == kExpZero ? 0 : emax - emin;
+      sE[tx] = E;
+      if (j < b.N) {
+        eB[b.eB + j] = E;
+        spB[b.eB + j] = sp;
+        atomicMax(max_spread, sp);
+        if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
+      }
+    }
+    __syncthreads();
+    if (!exps_only) {
+      const int64_t plane = b.N * Kpitch;
+      for (int64_t k0 = 0; k0 < Kpitch; k0 += 32) {
+#pragma unroll
+        for (int q = 0; q < MW; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int kl = ty + 8 * u;
+            const int64_t k = k0 + kl;
+            tile[(q * 32 + kl) * 33 + tx] = (k < K && j < b.N) ? b.B[q * b.psb + k * b.ldb + j] : 0.0;
+          }
+        __syncthreads();
+        for (int it = 0; it < 2; ++it) {
+          const int e = threadIdx.x + 256 * it;   // 512 pairs per tile
+          const int jl = e >> 4, kl = 2 * (e & 15);
+          const int64_t jj = j0 + jl, k = k0 + kl;
+          if (jj >= b.N) continue;
+          __nv_bfloat16 *dst = pieceB + (b.rowB + jj) * Kpitch + k;
+          if (k >= K) {
+            for (int p = 0; p < S; ++p) store2<__nv_bfloat16>(dst + p * plane, 0, 0);
+            continue;
+          }
+          double x0[MW], x1[MW];
+#pragma unroll
+          for (int q = 0; q < MW; ++q) {
+            x0[q] = tile[(q * 32 + kl) * 33 + jl];
+            x1[q] = tile[(q * 32 + kl + 1) * 33 + jl];
+          }
+          const int F = w * S - 2 - sE[jl];
+          if (w == 8)
+            cut_pair_w8<MW, NL, __nv_bfloat16>(x0, x1, F, S, dst, plane, status);
+          else
+            cut_pair<MW, NL, __nv_bfloat16>(x0, x1, F, w, S, dst, plane, status);
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---- 4. fusion ------------------------------------------------------------------------
+// One thread per output, outputs numbered problem by problem and, inside a
+// problem, column by column (the order of the column-major partial planes),
+// so consecutive threads read consecutive partial sums whatever the sizes.
 template <int MW, int NL, bool NARROW>
 __global__ void __launch_bounds__(256) batch_combine_kernel(const BInfo *info, const BHeader *hdr,
                                                             int count, const void *partials,
                                                             const int32_t *eA, const int32_t *eB,
                                                             int G, int group, int D, int w) {
   if (hdr->bad) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  // one warp per output column of some C_i, lanes along the rows (the partial
-  // planes are column-major, so the loads are contiguous)
-  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       task < hdr->sum_N; task += nwarps) {
-    const int i = find_problem(info, count, task, [](const BInfo &b) { return b.eB; });
+  __shared__ int first;
+  const int64_t total = hdr->sum_MN;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) first = find_problem(info, count, base, [](const BInfo &b) { return b.outs; });
+    __syncthreads();
+    const int64_t f = base + threadIdx.x;
+    if (f >= total) continue;
+    int i = first;
+    while (i + 1 < count && info[i + 1].outs <= f) ++i;   // at most a few steps
     const BInfo &b = info[i];
-    const int64_t j = task - b.eB;
-    const int eb = eB[task];
-    for (int64_t r = lane; r < b.M; r += 32) {
-      uint64_t X[NL];
+    const int64_t o = f - b.outs;                           // = j * M + r
+    const int64_t j = o / b.M, r = o - j * b.M;
+    uint64_t X[NL];
 #pragma unroll
-      for (int k = 0; k < NL; ++k) X[k] = 0;
-      if constexpr (NARROW) {
-        fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + b.part + j * b.M + r,
-                           b.N * b.M, D, group, w);
-      } else {
-        const int64_t *p = static_cast<const int64_t *>(partials) + b.part;
-        for (int g = 0; g < G; ++g) {
-          const int t1 = min(D, (g + 1) * group) - 1;
-          add_shifted<NL>(X, p[((int64_t)g * b.N + j) * b.M + r], w * (D - 1 - t1));
-        }
+    for (int k = 0; k < NL; ++k) X[k] = 0;
+    if constexpr (NARROW) {
+      fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + b.part + o, b.N * b.M, D,
+                         group, w);
+    } else {
+      const int64_t *p = static_cast<const int64_t *>(partials) + b.part + o;
+      for (int g = 0; g < G; ++g) {
+        const int t1 = min(D, (g + 1) * group) - 1;
+        add_shifted<NL>(X, p[(int64_t)g * b.N * b.M], w * (D - 1 - t1));
       }
-      double words[MW];
-      round_words<MW, NL>(X, eA[b.eA + r] + eb + 4 - w * (D + 1), words);
-#pragma unroll
-      for (int k = 0; k < MW; ++k) b.C[k * b.psc + r * b.ldc + j] = words[k];
     }
+    double words[MW];
+    round_words<MW, NL>(X, eA[b.eA + r] + eB[b.eB + j] + 4 - w * (D + 1), words);
+#pragma unroll
+    for (int k = 0; k < MW; ++k) b.C[k * b.psc + r * b.ldc + j] = words[k];
   }
 }
 
@@ -279,16 +372,26 @@ int check_batch(const mw_plan *p, const mw_batch *b) {
 }
 
 template <int MW, int NL>
-void launch_split_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
-                     uint8_t *w8, const Layout &L, int exps_only, cudaStream_t s) {
-  batch_split_kernel<MW, NL><<<grid_for(8), 256, 0, s>>>(
-      info, hdr, b.count, p.w, p.S_A, p.S_B, L.Kpitch,
-      reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceA),
-      reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceB), reinterpret_cast<int32_t *>(w8 + L.eA),
-      reinterpret_cast<int32_t *>(w8 + L.spA), reinterpret_cast<int32_t *>(w8 + L.eB),
-      reinterpret_cast<int32_t *>(w8 + L.spB),
-      reinterpret_cast<BHeader *>(w8 + L.header)->max_spread, p.range_A, p.range_B, exps_only,
-      status_ptr());
+int launch_split_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
+                    uint8_t *w8, const Layout &L, int exps_only, cudaStream_t s) {
+  BHeader *h = reinterpret_cast<BHeader *>(w8 + L.header);
+  batch_split_rows_kernel<MW, NL><<<grid_for(8), 256, 0, s>>>(
+      info, hdr, b.count, p.w, p.S_A, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceA),
+      reinterpret_cast<int32_t *>(w8 + L.eA), reinterpret_cast<int32_t *>(w8 + L.spA),
+      h->max_spread, p.range_A, exps_only, status_ptr());
+  const size_t sm = (size_t)MW * 32 * 33 * sizeof(double);
+  static bool attr_set = false;  // once per instantiation
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(batch_split_cols_kernel<MW, NL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_fail(e, "batched split smem attribute");
+    attr_set = true;
+  }
+  batch_split_cols_kernel<MW, NL><<<grid_for(4), 256, sm, s>>>(
+      info, hdr, b.count, p.w, p.S_B, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceB),
+      reinterpret_cast<int32_t *>(w8 + L.eB), reinterpret_cast<int32_t *>(w8 + L.spB),
+      h->max_spread + 1, p.range_B, exps_only, status_ptr());
+  return MW_OK;
 }
 
 int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void *ws,
@@ -305,7 +408,7 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
   int nl = bits <= 128 ? 2 : bits <= 256 ? 4 : bits <= 384 ? 6 : bits <= 512 ? 8 : bits <= 640 ? 10 : 0;
   if (!nl) return fail(MW_EUNSUPPORTED, "w*S too large");
 #define MW_SPLIT_CASE(MWV, NLV) \
-  if (p.m == MWV && nl == NLV) launch_split_nl<MWV, NLV>(info, hdr, b, p, w8, L, exps_only, s);
+  if (p.m == MWV && nl == NLV) { int rc = launch_split_nl<MWV, NLV>(info, hdr, b, p, w8, L, exps_only, s); if (rc) return rc; }
   MW_SPLIT_CASE(2, 2) MW_SPLIT_CASE(2, 4) MW_SPLIT_CASE(2, 6) MW_SPLIT_CASE(2, 8) MW_SPLIT_CASE(2, 10)
   MW_SPLIT_CASE(4, 2) MW_SPLIT_CASE(4, 4) MW_SPLIT_CASE(4, 6) MW_SPLIT_CASE(4, 8) MW_SPLIT_CASE(4, 10)
   MW_SPLIT_CASE(8, 2) MW_SPLIT_CASE(8, 4) MW_SPLIT_CASE(8, 6) MW_SPLIT_CASE(8, 8) MW_SPLIT_CASE(8, 10)

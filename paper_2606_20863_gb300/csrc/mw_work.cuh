@@ -19,6 +19,8 @@ struct BInfo {            // one problem, filled by the prologue
   int64_t eA, eB;         // prefix sums of M and N: exponent offsets
   int64_t part;           // offset of the partial sums (int64 units)
   int64_t work;           // first work item
+  int64_t outs;           // prefix sum of M*N: first output in the flat output order
+  int64_t stripes;        // prefix sum of ceil(N/32): first 32-column stripe of B
   int32_t tiles_m, tiles_n, KB, pad;
 };
 
@@ -28,6 +30,7 @@ struct BHeader {          // written by the prologue
   int32_t max_spread[2];
   int32_t pad;
   unsigned long long next_item;  // work counter of the product kernel
+  int64_t sum_stripes;           // 32-column stripes of all B_i
 };
 
 // problem owning flat index x, given a field that holds exclusive prefix sums
