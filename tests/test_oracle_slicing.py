@@ -231,3 +231,22 @@ def test_paper_pattern_diagonal_sums_are_exact_in_double():
             s_double += float(np.dot(xq[j], yq[i - j]))
             s_exact += sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(xq[j], yq[i - j]))
         assert Fraction(s_double) == s_exact
+
+
+def test_group_values_recombine_to_the_fused_integer():
+    """The 64-bit group sums the wide GPU mode stores recombine, with weights
+    2^(w (D-1-t1)), to the fused integer X, which the full-coverage test pins to
+    the exact product; one group spanning every diagonal is X itself."""
+    rng = SplitMix64(44)
+    A, B = uniform_mdouble(rng, 2, 3, 40), uniform_mdouble(rng, 2, 40, 2)
+    w, S, D = 8, 16, 24
+    sp = slicing.SlicedProduct(A, B, w, S, S, D)
+    for group in (1, 3, 5, D):
+        bounds = [(g * group, min(D, (g + 1) * group) - 1) for g in range(-(-D // group))]
+        for a in range(3):
+            for b in range(2):
+                V = slicing.group_values(sp.s[:, a, b], w, bounds)
+                X = sum(v << (w * (D - 1 - t1)) for v, (_, t1) in zip(V, bounds))
+                assert X == slicing.fuse_integer(sp.s[:, a, b], w, D)
+                if group == D:
+                    assert V == [X]
