@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows in the CPU sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--workload", default="qd1024",
-                    choices=["qd1024", "dd4096", "qd4096", "od_batch"],
+                    choices=["qd1024", "dd4096", "qd4096", "od_batch", "adjoint"],
                     help="qd1024 (default): the benchmark line; the others measure the other "
                          "configurations of the method")
     return ap.parse_args()
@@ -427,6 +427,104 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
     return line
 
 
+def run_adjoint(args, mw, torch, dist, rank, world, dev):
+    """Double-double A 2048 x 1024, B 1024 x 2048, W 2048 x 2048 (seed 4): one
+    step is the forward product C = A B and the adjoint dA = W B^T, dB = A^T W
+    through mw_gemm and mw_gemm_backward, all three in the Ozaki form."""
+    import synthetic
+    A, B, W = synthetic.adjoint_case()
+    m, M, K = A.shape
+    N = B.shape[2]
+    Wm = np.zeros((m, M, N))
+    Wm[0] = W
+    tA, tB, tG = (torch.from_numpy(x).to(dev) for x in (A, B, Wm))
+    pf = mw.plan_for(tA, tB, "ozaki")
+    pa = mw.plan_for(tG, tB, "ozaki", False, True)
+    pb = mw.plan_for(tA, tG, "ozaki", True, False)
+    ws = torch.empty(mw.workspace_size(pf, M, N, K), dtype=torch.uint8, device=dev)
+    C = torch.empty((m, M, N), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flops = 3 * 2.0 * M * N * K
+
+    def step():
+        mw.mw_gemm(tA, tB, pf, C=C, ws=ws, check=False)
+        mw.mw_gemm_backward(tA, tB, tG, pa, pb, check=False)
+
+    for _ in range(args.warmup):
+        step()
+    mw.check_status()
+    torch.cuda.synchronize()
+    step_ms, _, clk = timed(step, args.steps, flush, mw, dist, dev, phase=False)
+    value, t_step = aggregate(sum(step_ms) / 1e3, flops, args.steps, dist, dev)
+
+    # product-kernel time of each of the three products (phase events, own loop)
+    calls = [(lambda c=None: mw.mw_gemm(tA, tB, pf, C=C, ws=ws, check=False), pf),
+             (lambda: mw.mw_gemm(tG, tB, pa, transB=True, check=False), pa),
+             (lambda: mw.mw_gemm(tA, tG, pb, transA=True, check=False), pb)]
+    work, kern = 0.0, 0.0
+    for f, pl in calls:
+        _, kms, _ = timed(f, max(3, args.steps), flush, mw, None, dev)
+        work += count_pairs(pl) * 2.0 * M * N * K
+        kern += statistics.mean(kms)
+    roof = roofline_of(1, work, [kern])
+    roof["algorithmic"] = (f"forward, dA and dB: {count_pairs(pf)}, {count_pairs(pa)} and "
+                           f"{count_pairs(pb)} slice pairs x {2.0 * M * N * K:.4g} flop; "
+                           "achieved over the sum of the three product-kernel times")
+
+    e2e_steps = args.e2e_steps if args.e2e_steps >= 0 else max(3, args.steps // 4)
+    e2e = None
+    if e2e_steps > 0:
+        hA, hB, hW = (torch.from_numpy(x).pin_memory() for x in (A, B, Wm))
+        hgA = torch.empty_like(hA).pin_memory()
+        hgB = torch.empty_like(hB).pin_memory()
+        hL = torch.empty((m,), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            a = hA.to(dev, non_blocking=True).requires_grad_(True)
+            b = hB.to(dev, non_blocking=True).requires_grad_(True)
+            w = hW.to(dev, non_blocking=True)
+            Cg = mw.MWGemm.apply(a, b)
+            loss = (Cg * w).sum(dim=(1, 2))        # per-plane sums: the loss's m words
+            loss.sum().backward()
+            hL.copy_(loss.detach(), non_blocking=True)
+            hgA.copy_(a.grad, non_blocking=True)
+            hgB.copy_(b.grad, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int((hA.numel() + hB.numel() + hW.numel()) * 8),
+               "d2h_bytes_per_step": int((hL.numel() + hgA.numel() + hgB.numel()) * 8)}
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "double-double forward C=A*B and adjoint dA=W*B^T, dB=A^T*W, "
+                                   "A 2048x1024, B 1024x2048, W 2048x2048, entries U[-1,1) with "
+                                   "lower words x2^-53 U[-1,1), seed 4",
+                       "m": m, "M": M, "N": N, "K": K,
+                       "plans": {"forward": pf.as_dict(), "dA": pa.as_dict(), "dB": pb.as_dict()},
+                       "flop_per_step": flops,
+                       "l2": "flushed (256 MiB write) before every timed step"},
+            "roofline": roof, "clocks": clk, "e2e": e2e,
+            "gpu_launches": 3 * KERNELS_PER_STEP * args.steps}
+    if rank == 0 and not args.no_cpu:
+        from oracle import textbook
+        tc = textbook.TextbookC()
+        BT = np.ascontiguousarray(B.transpose(0, 2, 1))
+        AT = np.ascontiguousarray(A.transpose(0, 2, 1))
+        fl, t0 = 0.0, time.perf_counter()
+        for X, Y in ((A, B), (Wm, BT), (AT, Wm)):
+            tc.gemm(X, Y, threads=tc.max_threads())
+            fl += 2.0 * X.shape[1] * X.shape[2] * Y.shape[2]
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": fl / dt / 1e9, "unit": "GFLOP/s",
+                                "cores": tc.max_threads(), "kind": "oracle",
+                                "sample": f"the whole step (C, dA and dB), {dt:.2f} s"}
+    return line
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -439,6 +537,8 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     if args.workload == "od_batch":
         line = run_batch(args, mw, torch, dist, rank, world, dev)
+    elif args.workload == "adjoint":
+        line = run_adjoint(args, mw, torch, dist, rank, world, dev)
     else:
         line = run_single(args, args.workload, mw, torch, dist, rank, world, dev)
     if rank == 0:

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256) batch_split_cols_kernel(
 // problem, column by column (the order of the column-major partial planes),
 // so consecutive threads read consecutive partial sums whatever the sizes.
 template <int MW, int NL, bool NARROW>
-__global__ void __launch_bounds__(256) batch_combine_kernel(const BInfo *info, const BHeader *hdr,
+__global__ void __launch_bounds__(256, 3) batch_combine_kernel(const BInfo *info, const BHeader *hdr,
                                                             int count, const void *partials,
                                                             const int32_t *eA, const int32_t *eB,
                                                             int G, int group, int D, int w) {
@@ -326,23 +326,29 @@ __global__ void __launch_bounds__(256) batch_combine_kernel(const BInfo *info, c
     const BInfo &b = info[i];
     const int64_t o = f - b.outs;                           // = j * M + r
     const int64_t j = o / b.M, r = o - j * b.M;
-    uint64_t X[NL];
-#pragma unroll
-    for (int k = 0; k < NL; ++k) X[k] = 0;
-    if constexpr (NARROW) {
-      fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + b.part + o, b.N * b.M, D,
-                         group, w);
+    uint32_t U[2 * NL];
+    if (NARROW && w == 8) {
+      fuse_w8<2 * NL>(U, static_cast<const int32_t *>(partials) + b.part + o, b.N * b.M, D);
     } else {
-      const int64_t *p = static_cast<const int64_t *>(partials) + b.part + o;
-      for (int g = 0; g < G; ++g) {
-        const int t1 = min(D, (g + 1) * group) - 1;
-        add_shifted<NL>(X, p[(int64_t)g * b.N * b.M], w * (D - 1 - t1));
-      }
-    }
-    double words[MW];
-    round_words<MW, NL>(X, eA[b.eA + r] + eB[b.eB + j] + 4 - w * (D + 1), words);
+      uint64_t X[NL];
 #pragma unroll
-    for (int k = 0; k < MW; ++k) b.C[k * b.psc + r * b.ldc + j] = words[k];
+      for (int k = 0; k < NL; ++k) X[k] = 0;
+      if constexpr (NARROW) {
+        fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + b.part + o, b.N * b.M, D,
+                           group, w);
+      } else {
+        const int64_t *p = static_cast<const int64_t *>(partials) + b.part + o;
+        for (int g = 0; g < G; ++g) {
+          const int t1 = min(D, (g + 1) * group) - 1;
+          add_shifted<NL>(X, p[(int64_t)g * b.N * b.M], w * (D - 1 - t1));
+        }
+      }
+      to_limbs32<NL>(X, U);
+    }
+    double *c = b.C + r * b.ldc + j;
+    const int64_t psc = b.psc;
+    round_words32<MW, 2 * NL>(U, eA[b.eA + r] + eB[b.eB + j] + 4 - w * (D + 1),
+                              [&](int k, double v) { c[k * psc] = v; });
   }
 }
 

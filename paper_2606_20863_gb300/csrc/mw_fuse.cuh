@@ -1,45 +1,16 @@
-// Exact fusion of 64-bit partial sums and rounding to m words (device side,
+// Exact fusion of the partial sums and rounding to m words (device side,
 // shared by the single and batched combine kernels).
-//   add_shifted: X += V 2^sh on an NL-limb two's complement integer;
-//   round_words: the m nonoverlapping doubles of X 2^ex, each the value
-//                rounded to nearest (ties to even) of what the previous words
-//                left over (greedy), computed on the exact integer.
+//   add_shifted:    X += V 2^sh on an NL-limb (64-bit) two's complement integer;
+//   fuse_diagonals: X += sum_t s_t 2^(w (D-1-t)), any w, 64-bit limbs;
+//   fuse_w8:        the same sum for w = 8 straight into 32-bit limbs;
+//   round_words32:  the m nonoverlapping doubles of X 2^ex, each the value
+//                   rounded to nearest (ties to even) of what the previous
+//                   words left over (greedy), computed on the exact integer.
 #pragma once
 #include <cstdint>
 
 namespace mw {
 namespace {
-
-template <int NL>
-__device__ __forceinline__ bool is_zero(const uint64_t (&x)[NL]) {
-  uint64_t o = 0;
-#pragma unroll
-  for (int i = 0; i < NL; ++i) o |= x[i];
-  return o == 0;
-}
-
-// Shift left so that bit 63 of the top limb is set; returns the shift.
-template <int NL>
-__device__ __forceinline__ int normalize(uint64_t (&x)[NL]) {
-  int sh = 0;
-  // whole limbs first
-#pragma unroll
-  for (int k = 0; k < NL; ++k) {
-    if (x[NL - 1] == 0) {
-#pragma unroll
-      for (int i = NL - 1; i > 0; --i) x[i] = x[i - 1];
-      x[0] = 0;
-      sh += 64;
-    }
-  }
-  const int b = __clzll((long long)x[NL - 1]);
-  if (b) {
-#pragma unroll
-    for (int i = NL - 1; i > 0; --i) x[i] = (x[i] << b) | (x[i - 1] >> (64 - b));
-    x[0] <<= b;
-  }
-  return sh + b;
-}
 
 template <int NL>
 __device__ __forceinline__ void add_shifted(uint64_t (&X)[NL], int64_t V, int sh) {
@@ -60,21 +31,21 @@ __device__ __forceinline__ void add_shifted(uint64_t (&X)[NL], int64_t V, int sh
   }
 }
 
-// X += sum_t s_t 2^(w (D-1-t)) for the int32 diagonal sums s_t = p[t * plane]:
-// 32 independent loads at a time, then Horner in int64 over each group of
-// `group` consecutive diagonals (exact for the planner's group size) and one
+// X += sum_t s_t 2^(w (D-1-t)) for the int32 diagonal sums s_t = p[t * plane]
+// (any w): 8 independent loads at a time, then Horner in int64 over each group
+// of `group` consecutive diagonals (exact for the planner's group size) and one
 // multi-limb add per group.
 template <int NL>
 __device__ __forceinline__ void fuse_diagonals(uint64_t (&X)[NL], const int32_t *p, int64_t plane,
                                                int D, int group, int w) {
   int64_t V = 0;
   int in_group = 0;
-  for (int t0 = 0; t0 < D; t0 += 32) {
-    int32_t s[32];
+  for (int t0 = 0; t0 < D; t0 += 8) {
+    int32_t s[8];
 #pragma unroll
-    for (int u = 0; u < 32; ++u) s[u] = (t0 + u < D) ? p[(int64_t)(t0 + u) * plane] : 0;
+    for (int u = 0; u < 8; ++u) s[u] = (t0 + u < D) ? p[(int64_t)(t0 + u) * plane] : 0;
 #pragma unroll
-    for (int u = 0; u < 32; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int t = t0 + u;
       if (t < D) {
         V = (int64_t)((uint64_t)V << w) + s[u];
@@ -88,52 +59,111 @@ __device__ __forceinline__ void fuse_diagonals(uint64_t (&X)[NL], const int32_t 
   }
 }
 
-template <int MW, int NL>
-__device__ __forceinline__ void round_words(uint64_t (&X)[NL], int ex, double (&words)[MW]) {
+// The same integer as 2 NL 32-bit limbs (two's complement).
+template <int NL>
+__device__ __forceinline__ void to_limbs32(const uint64_t (&X)[NL], uint32_t (&U)[2 * NL]) {
 #pragma unroll
-  for (int k = 0; k < MW; ++k) words[k] = 0.0;
-  // magnitude and sign
-  bool neg = (int64_t)X[NL - 1] < 0;
+  for (int k = 0; k < NL; ++k) {
+    U[2 * k] = (uint32_t)X[k];
+    U[2 * k + 1] = (uint32_t)(X[k] >> 32);
+  }
+}
+
+// X = sum_t s_t 2^(8 (D-1-t)) for w = 8 and the int32 diagonal sums
+// s_t = p[t * plane], as NL32 32-bit limbs (two's complement), built from the
+// least significant end: limb j takes the four sums of weights 2^(32j),
+// 2^(32j+8), 2^(32j+16), 2^(32j+24), joined by Horner in 64 bits (|.| < 2^56),
+// plus the signed carry out of limb j-1.
+template <int NL32>
+__device__ __forceinline__ void fuse_w8(uint32_t (&U)[NL32], const int32_t *p, int64_t plane,
+                                        int D) {
+  static_assert(NL32 % 2 == 0, "limbs in pairs");
+  const int32_t *last = p + (int64_t)(D - 1) * plane;   // s_{D-1}, weight 2^0
+  int64_t R = 0;
+#pragma unroll
+  for (int j = 0; j < NL32; j += 2) {
+    int32_t s[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int u = 4 * j + k;                            // s_{D-1-u}, weight 2^(8u)
+      s[k] = u < D ? last[-(int64_t)u * plane] : 0;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int64_t V = s[4 * h + 3];
+      V = V * 256 + s[4 * h + 2];
+      V = V * 256 + s[4 * h + 1];
+      V = V * 256 + s[4 * h];
+      R += V;
+      U[j + h] = (uint32_t)R;
+      R >>= 32;
+    }
+  }
+}
+
+// Greedy rounding of X 2^ex, X given as NL32 32-bit limbs (two's complement),
+// into MW nonoverlapping doubles: word k is the remainder left by words
+// 0..k-1 rounded to nearest (ties to even), all on the exact integer.
+// store(k, v) receives word k; words after an exact remainder are zero.
+// Per word: find the top nonzero limb h, take a 96-bit window from limbs h,
+// h-1, h-2 (53 bits, the rounding bit, the rest sticky with every lower
+// limb), then keep the bits below the last mantissa bit, or 2^cut minus them
+// with the sign flipped when the mantissa was rounded up.
+template <int MW, int NL32, class Store>
+__device__ __forceinline__ void round_words32(uint32_t (&U)[NL32], int ex, Store store) {
+  bool neg = (int32_t)U[NL32 - 1] < 0;
   if (neg) {
-    uint64_t c = 1;
+    uint32_t c = 1;
 #pragma unroll
-    for (int k = 0; k < NL; ++k) {
-      const uint64_t s = ~X[k] + c;
-      c = (s == 0 && c) ? 1 : 0;
-      X[k] = s;
+    for (int i = 0; i < NL32; ++i) {
+      const uint32_t s = ~U[i] + c;
+      c &= (uint32_t)(s == 0);
+      U[i] = s;
     }
   }
+  int k = 0;
+#pragma unroll 1
+  for (; k < MW; ++k) {
+    int h = -1;
 #pragma unroll
-  for (int k = 0; k < MW; ++k) {
-    if (is_zero<NL>(X)) break;
-    ex -= normalize<NL>(X);
-    const uint64_t top = X[NL - 1];
-    uint64_t mant = top >> 11;
-    const uint64_t rbit = (top >> 10) & 1;
-    uint64_t sticky = top & 0x3FF;
+    for (int i = 0; i < NL32; ++i)
+      if (U[i] != 0) h = i;
+    if (h < 0) break;
+    uint32_t a = 0, b = 0, c = 0, below = 0;
 #pragma unroll
-    for (int q = 0; q < NL - 1; ++q) sticky |= X[q];
-    const uint64_t up = rbit & ((sticky != 0) | (mant & 1));
-    mant += up;
-    const double mag = scalbn((double)mant, ex + 64 * (NL - 1) + 11);
-    words[k] = neg ? -mag : mag;
-    // remainder: low bits minus (up ? 2^pos : 0), pos = 64 (NL-1) + 11
-    X[NL - 1] = top & 0x7FF;
-    if (up) {
-      // X <- 2^pos - low, and the sign flips
-      X[NL - 1] = (~X[NL - 1]) & 0x7FF;
-#pragma unroll
-      for (int q = 0; q < NL - 1; ++q) X[q] = ~X[q];
-      uint64_t c = 1;
-#pragma unroll
-      for (int q = 0; q < NL; ++q) {
-        const uint64_t s = X[q] + c;
-        c = (s == 0 && c) ? 1 : 0;
-        X[q] = s;
+    for (int i = 0; i < NL32; ++i) {
+      if (i <= h) {
+        below |= c;
+        c = b;
+        b = a;
+        a = U[i];
       }
-      neg = !neg;
     }
+    const int lz = __clz(a);
+    const uint64_t ab = ((uint64_t)a << 32) | b;
+    const uint64_t top = lz ? (ab << lz) | (c >> (32 - lz)) : ab;
+    const uint32_t c_low = c << lz;                       // bits of c below the window
+    uint64_t mant = top >> 11;
+    const uint32_t rbit = (uint32_t)(top >> 10) & 1u;
+    const bool sticky = ((top & 0x3FF) | c_low | below) != 0;
+    const uint32_t up = rbit & (uint32_t)(sticky | (mant & 1));
+    mant += up;
+    const int cut = 32 * h - 21 - lz;                     // weight of the mantissa's last bit
+    const double mag = scalbn((double)mant, ex + cut);
+    store(k, neg ? -mag : mag);
+    uint32_t carry = up;
+#pragma unroll
+    for (int i = 0; i < NL32; ++i) {
+      const int lo = 32 * i;
+      uint32_t x = up ? ~U[i] : U[i];
+      x += carry;
+      carry &= (uint32_t)(x == 0);
+      const uint32_t keep = lo >= cut ? 0u : (lo + 32 <= cut ? ~0u : (1u << (cut - lo)) - 1u);
+      U[i] = x & keep;
+    }
+    if (up) neg = !neg;
   }
+  for (; k < MW; ++k) store(k, 0.0);
 }
 
 }  // namespace

@@ -83,6 +83,18 @@ struct PParams {
   BInfo single;
 };
 
+// Tensor maps over the two piece arrays with boxes of 16, 32, 64, 128 and 256
+// rows: a tile loads only the rows its problem has (rows past them would only
+// feed outputs that are never stored).
+constexpr int NBOX = 5;
+struct Maps {
+  CUtensorMap a[NBOX], b[NBOX];
+};
+__host__ __device__ constexpr int box_rows(int i) { return 16 << i; }
+__device__ __forceinline__ int box_index(int64_t rows) {
+  return rows <= 16 ? 0 : rows <= 32 ? 1 : rows <= 64 ? 2 : rows <= 128 ? 3 : 4;
+}
+
 __device__ __forceinline__ const BInfo &problem(const PParams &P, int i) {
   return P.info ? P.info[i] : P.single;
 }
@@ -117,13 +129,12 @@ __device__ __forceinline__ int nsteps(const PParams &P, int t, int KB) {
 
 template <int BN_, bool NARROW>
 __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
-    ozaki_kernel(const __grid_constant__ CUtensorMap mapA,
-                 const __grid_constant__ CUtensorMap mapB, const PParams P) {
+    ozaki_kernel(const __grid_constant__ Maps maps, const PParams P) {
   using SH = Shape<BN_, NARROW>;
   constexpr int BN = SH::BN, STAGES = SH::STAGES, TMEM_COLS = SH::TMEM_COLS;
   constexpr uint32_t STAGE_B = SH::STAGE_B;
   constexpr int NUM_DRAIN_WARPS = SH::WARPS;
-  constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
+
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;
@@ -159,8 +170,10 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
     *abort = 0;
     counters[0] = counters[1] = 0;
     fence_barrier_init();
-    prefetch_map(&mapA);
-    prefetch_map(&mapB);
+    for (int i = 0; i < NBOX; ++i) {
+      prefetch_map(&maps.a[i]);
+      prefetch_map(&maps.b[i]);
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -186,6 +199,9 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         mbar_arrive(&uf[slot]);
         if (u < 0) break;
         const Item x = decode_item(P, u);
+        const int ia = box_index(min((int64_t)BM, x.M - (int64_t)x.tm * BM));
+        const int ib = box_index(min((int64_t)BN, x.N - (int64_t)x.tn * BN));
+        const uint32_t bytes = (uint32_t)(box_rows(ia) + box_rows(ib)) * BK * 2;
         for (int t = x.t0; t <= x.t1 && !*abort; ++t) {
           for (int p = plo(P, t); p <= phi(P, t) && !*abort; ++p) {
             const int q = t - p;
@@ -194,9 +210,9 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             for (int kb = 0; kb < x.KB; ++kb, ++it) {
               const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
               if (!mbar_wait(&empty[s], ph ^ 1, P.status, abort)) break;
-              mbar_arrive_expect_tx(&full[s], STAGE_A + STAGE_B);
-              tma_load_2d(smem_u32(sA + s * STAGE_A), &mapA, kb * BK, ra, smem_u32(&full[s]));
-              tma_load_2d(smem_u32(sB + s * STAGE_B), &mapB, kb * BK, rb, smem_u32(&full[s]));
+              mbar_arrive_expect_tx(&full[s], bytes);
+              tma_load_2d(smem_u32(sA + s * STAGE_A), &maps.a[ia], kb * BK, ra, smem_u32(&full[s]));
+              tma_load_2d(smem_u32(sB + s * STAGE_B), &maps.b[ib], kb * BK, rb, smem_u32(&full[s]));
               counters[0] = (int)it + 1;
             }
           }
@@ -213,6 +229,9 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         mbar_arrive(&ue[slot]);
         if (u < 0) break;
         const Item x = decode_item(P, u);
+        // N of the MMA: the tile's valid columns rounded up to 16
+        const int ncols = (int)min((int64_t)BN, x.N - (int64_t)x.tn * BN);
+        const uint32_t idesc = idesc_bf16(BM, (ncols + 15) & ~15);
         for (int t = x.t0; t <= x.t1 && !*abort; ++t) {
           const int tot = nsteps(P, t, x.KB);
           for (int j = 0; j < tot && !*abort; ++ch) {
@@ -229,7 +248,7 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
               const uint64_t bd = sw128_desc(smem_u32(sB + s * STAGE_B));
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk)
-                tc_mma(d, ad + 2 * kk, bd + 2 * kk, kIdesc, (jj | kk) ? 1u : 0u);
+                tc_mma(d, ad + 2 * kk, bd + 2 * kk, idesc, (jj | kk) ? 1u : 0u);
               tc_commit(&empty[s]);
               counters[1] = (int)it + 1;
             }
@@ -372,22 +391,27 @@ __global__ void combine_kernel(const void *__restrict__ partials, const int32_t 
                                int w, double *C, int64_t ldc, int64_t psc) {
   const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
   if (i >= M || j >= N) return;
-  uint64_t X[NL];
-#pragma unroll
-  for (int k = 0; k < NL; ++k) X[k] = 0;
-  if constexpr (NARROW) {
-    fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + j * M + i, N * M, D, group, w);
+  uint32_t U[2 * NL];
+  if (NARROW && w == 8) {
+    fuse_w8<2 * NL>(U, static_cast<const int32_t *>(partials) + j * M + i, N * M, D);
   } else {
-    const int64_t *p = static_cast<const int64_t *>(partials);
-    for (int g = 0; g < G; ++g) {
-      const int t1 = min(D, (g + 1) * group) - 1;
-      add_shifted<NL>(X, p[((int64_t)g * N + j) * M + i], w * (D - 1 - t1));
-    }
-  }
-  double words[MW];
-  round_words<MW, NL>(X, eA[i] + eB[j] + 4 - w * (D + 1), words);
+    uint64_t X[NL];
 #pragma unroll
-  for (int k = 0; k < MW; ++k) C[k * psc + i * ldc + j] = words[k];
+    for (int k = 0; k < NL; ++k) X[k] = 0;
+    if constexpr (NARROW) {
+      fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + j * M + i, N * M, D, group, w);
+    } else {
+      const int64_t *p = static_cast<const int64_t *>(partials);
+      for (int g = 0; g < G; ++g) {
+        const int t1 = min(D, (g + 1) * group) - 1;
+        add_shifted<NL>(X, p[((int64_t)g * N + j) * M + i], w * (D - 1 - t1));
+      }
+    }
+    to_limbs32<NL>(X, U);
+  }
+  double *c = C + i * ldc + j;
+  round_words32<MW, 2 * NL>(U, eA[i] + eB[j] + 4 - w * (D + 1),
+                            [&](int k, double v) { c[k * psc] = v; });
 }
 
 template <int MW, int NL>
@@ -483,10 +507,13 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   for (int i = 1; i < G; ++i)
     for (int j = i; j > 0 && cost[P.gorder[j]] > cost[P.gorder[j - 1]]; --j)
       std::swap(P.gorder[j], P.gorder[j - 1]);
-  CUtensorMap mA, mB;
-  int rc = make_map_2d(&mA, a.pieceA, a.Kpitch, a.rowsA, BM);
+  Maps maps;
+  int rc = MW_OK;
+  for (int i = 0; i < NBOX && !rc; ++i) {
+    rc = make_map_2d(&maps.a[i], a.pieceA, a.Kpitch, a.rowsA, std::min(box_rows(i), BM));
+    if (!rc) rc = make_map_2d(&maps.b[i], a.pieceB, a.Kpitch, a.rowsB, std::min(box_rows(i), bn));
+  }
   if (rc) return rc;
-  if ((rc = make_map_2d(&mB, a.pieceB, a.Kpitch, a.rowsB, bn))) return rc;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(ozaki_kernel<128, true>,
@@ -509,11 +536,11 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   int grid = nsm;
   if (!a.info) grid = (int)std::min<int64_t>(P.single_work, nsm);
   if (a.narrow && bn == 256)
-    ozaki_kernel<256, true><<<grid, Shape<256, true>::THREADS, Shape<256, true>::SMEM, s>>>(mA, mB, P);
+    ozaki_kernel<256, true><<<grid, Shape<256, true>::THREADS, Shape<256, true>::SMEM, s>>>(maps, P);
   else if (a.narrow)
-    ozaki_kernel<128, true><<<grid, Shape<128, true>::THREADS, Shape<128, true>::SMEM, s>>>(mA, mB, P);
+    ozaki_kernel<128, true><<<grid, Shape<128, true>::THREADS, Shape<128, true>::SMEM, s>>>(maps, P);
   else
-    ozaki_kernel<128, false><<<grid, Shape<128, false>::THREADS, Shape<128, false>::SMEM, s>>>(mA, mB, P);
+    ozaki_kernel<128, false><<<grid, Shape<128, false>::THREADS, Shape<128, false>::SMEM, s>>>(maps, P);
   return cuda_fail(cudaGetLastError(), "product kernel launch");
 }
 

@@ -148,6 +148,28 @@ def test_ozaki_other_widths_and_chunks(mw, cuda, w, chunk):
     check_ozaki(mw, cuda, A, B, plan, rows=[0, 33, 69], cols=[0, 44, 89])
 
 
+@pytest.mark.parametrize("a,b,want", [
+    # a long run of zero bits between the two words
+    ([1.0, 2.0 ** -200], [1.0 + 2.0 ** -52, 3.0], [1.0 + 2.0 ** -52, 3 * 2.0 ** -200]),
+    # exact tie, even mantissa kept
+    ([1.0, 2.0 ** -53], [1.0, 1.0], [1.0, 2.0 ** -53]),
+    # exact tie, odd mantissa rounded up, remainder negative
+    ([1.0 + 2.0 ** -52, 2.0 ** -53], [1.0, 1.0], [1.0 + 2.0 ** -51, -2.0 ** -53]),
+    # negative sum that one double holds exactly
+    ([-1.0, 2.0 ** -53], [1.0, 1.0], [-1.0 + 2.0 ** -53]),
+    # cancellation down to the last bits
+    ([1.0, -1.0], [1.0 + 2.0 ** -52, 1.0], [2.0 ** -52]),
+])
+def test_ozaki_rounding_edge_cases(mw, cuda, a, b, want):
+    """C = a . b (1 x 2 times 2 x 1, quad double): greedy words with ties to
+    even and long zero runs, against the closed form and the oracle."""
+    A = np.zeros((4, 1, 2)); A[0, 0, :] = a
+    B = np.zeros((4, 2, 1)); B[0, :, 0] = b
+    plan = mw.plan_for(to_dev(A, cuda), to_dev(B, cuda), "ozaki")
+    C, _ = check_ozaki(mw, cuda, A, B, plan)
+    assert list(C[:, 0, 0]) == want + [0.0] * (4 - len(want))
+
+
 def test_double_double_n64_exact_check(mw, cuda):
     """Double double, n = 64, seed 0: every entry checked against the exact
     rational product, both forms."""
