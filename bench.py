@@ -49,6 +49,8 @@ def parse():
                     help="end-to-end runs from host memory (-1 = steps/4, at least 3; 0 = leave out)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows in the CPU sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--count", type=int, default=20000,
+                    help="od_batch: number of products (20,000 is the benchmark; fewer for profiling)")
     ap.add_argument("--workload", default="qd1024",
                     choices=["qd1024", "dd4096", "qd4096", "od_batch", "adjoint"],
                     help="qd1024 (default): the benchmark line; the others measure the other "
@@ -370,7 +372,7 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
     """20,000 octo-double products, n ~ U{8..128}, seed 3, one batched call
     replayed from a CUDA graph per step."""
     import synthetic
-    sizes = synthetic.batch_sizes(20000, 8, 128, seed=3)
+    sizes = synthetic.batch_sizes(args.count, 8, 128, seed=3)
     FA, FB, offs = synthetic.batch_flat(sizes, m=8, seed=3)
     dA, dB = torch.from_numpy(FA).to(dev), torch.from_numpy(FB).to(dev)
     order = np.argsort(-sizes, kind="stable")
@@ -401,10 +403,10 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic",
-            "config": {"workload": "20,000 octo-double products, n ~ U{8..128} square, entries "
-                                   "U[-1,1) with lower words x2^-53 U[-1,1), seed 3, one batched "
-                                   "call replayed from a CUDA graph",
-                       "m": 8, "count": 20000, "plan": plan.as_dict(), "slice_pairs": pairs,
+            "config": {"workload": f"{args.count:,} octo-double products, n ~ U{{8..128}} square, "
+                                   "entries U[-1,1) with lower words x2^-53 U[-1,1), seed 3, one "
+                                   "batched call replayed from a CUDA graph",
+                       "m": 8, "count": args.count, "plan": plan.as_dict(), "slice_pairs": pairs,
                        "useful_flop_per_step": flops,
                        "l2": "flushed (256 MiB write) before every timed step"},
             "roofline": None, "clocks": clk, "e2e": None, "gpu_launches": 4 * args.steps}

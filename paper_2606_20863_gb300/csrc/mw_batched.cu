@@ -11,8 +11,9 @@
 //      exponent by a warp reduction, then the balanced pieces of the row;
 //   3. product: persistent CTAs walk the work items (problem, output tile,
 //      diagonal group) -- the kernel of the single product with the tile's
-//      coordinates looked up per item;
-//   4. fusion: one warp per output row, exact integer fusion and greedy
+//      coordinates looked up per item in a table of the items' problems
+//      (written by a grid-wide search after the prologue);
+//   4. fusion: one thread per output, exact integer fusion and greedy
 //      rounding as for the single product.
 // The pieces of all problems share two row-major arrays of pitch Kpitch (the
 // largest K rounded up to 64), so one tensor map per operand covers the batch;
@@ -32,10 +33,12 @@ namespace mw {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
+constexpr double kL2Budget = 48.0 * (1 << 20);  // bytes of pieces in flight
 
 struct Layout {
-  size_t header, info, eA, spA, eB, spB, pieceA, pieceB, partials, total;
+  size_t header, info, eA, spA, eB, spB, pieceA, pieceB, items, partials, total;
   int64_t Kpitch;
+  int64_t items_max;  // bound on the work items, from the batch sums
   bool narrow;   // int32 diagonal sums (D planes) or int64 group sums (G planes)
   int planes;
   int sched;     // diagonals per work item
@@ -55,12 +58,27 @@ Layout layout_of(const mw_plan &p, const mw_batch &b) {
   L.spB = off;    off = a256(off + 4 * (size_t)b.sum_N);
   L.pieceA = off; off = a256(off + 2 * (size_t)p.S_A * b.sum_M * L.Kpitch);
   L.pieceB = off; off = a256(off + 2 * (size_t)p.S_B * b.sum_N * L.Kpitch);
-  L.partials = off;
   L.narrow = narrow_partials(p.S_A, p.S_B, p.w, b.max_K);
   L.planes = L.narrow ? p.D : n_groups(p.D, p.group);
-  // one work item per (problem, tile) with every diagonal: batches hold many
-  // small problems, and every item costs a search of the problem table
-  L.sched = L.narrow ? p.D : p.group;
+  // Diagonals per work item.  The items of one tile are handed out one after
+  // another, so the CTAs at work share ceil(D / sched) items per tile; the
+  // pieces of the tiles in flight (row panel of A and column panel of B, every
+  // slice) should fit in a share of L2, or every slice pair is read from HBM.
+  if (L.narrow) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const double tile_bytes = 2.0 * L.Kpitch * ((double)p.S_A * BM + (double)p.S_B * BN);
+    const int per_tile = (int)std::min<double>(p.D, std::ceil(nsm * tile_bytes / kL2Budget));
+    L.sched = (p.D + std::max(per_tile, 1) - 1) / std::max(per_tile, 1);
+  } else {
+    L.sched = p.group;
+  }
+  // ceil(M/BM) ceil(N/BN) <= MN/(BM BN) + M/BM + N/BN + 1 for every problem
+  L.items_max = (int64_t)n_groups(p.D, L.sched) *
+                (b.sum_MN / (BM * BN) + b.sum_M / BM + b.sum_N / BN + b.count + 3);
+  L.items = off;  off = a256(off + 4 * (size_t)L.items_max);
+  L.partials = off;
   off = a256(off + (L.narrow ? 4 : 8) * (size_t)L.planes * b.sum_MN);
   L.total = off;
   return L;
@@ -95,7 +113,7 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t *sh) {
 
 __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs, int count,
                                                         int G, int planes, int S_A, int S_B,
-                                                        int64_t Kpitch,
+                                                        int64_t Kpitch, int64_t items_max,
                                                         mw_batch want, BInfo *info, BHeader *hdr,
                                                         unsigned int *status) {
   __shared__ int64_t sh[33];
@@ -136,12 +154,23 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
   }
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
-    if (cM != want.sum_M || cN != want.sum_N || cMN != want.sum_MN) bad = 1;
+    if (cM != want.sum_M || cN != want.sum_N || cMN != want.sum_MN || cW > items_max) bad = 1;
     hdr->sum_M = cM; hdr->sum_N = cN; hdr->sum_MN = cMN; hdr->total_work = bad ? 0 : cW;
     hdr->sum_stripes = cS;
     hdr->bad = bad;
     if (bad) raise_status(status, MW_EINVAL);
   }
+}
+
+// The problem of every work item (items are numbered problem by problem), so
+// that the product kernel finds an item's problem with one load.
+__global__ void __launch_bounds__(256) item_table_kernel(const BInfo *info, const BHeader *hdr,
+                                                         int count, int32_t *table) {
+  if (hdr->bad) return;
+  const int64_t total = hdr->total_work;   // at most items_max (the prologue checks)
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total;
+       u += (int64_t)gridDim.x * blockDim.x)
+    table[u] = find_problem(info, count, u, [](const BInfo &b) { return b.work; });
 }
 
 // ---- 2. split ---------------------------------------------------------------------
@@ -408,8 +437,13 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(BHeader), s);
   if (e != cudaSuccess) return cuda_fail(e, "batch header memset");
   prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, n_groups(p.D, L.sched), L.planes, p.S_A,
-                                     p.S_B, L.Kpitch, b, info, hdr, status_ptr());
+                                     p.S_B, L.Kpitch, L.items_max, b, info, hdr, status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch prologue launch");
+  if (!exps_only) {
+    item_table_kernel<<<grid_for(4), 256, 0, s>>>(info, hdr, b.count,
+                                                  reinterpret_cast<int32_t *>(w8 + L.items));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch item table launch");
+  }
   const int bits = p.w * std::max(p.S_A, p.S_B) + 3;
   int nl = bits <= 128 ? 2 : bits <= 256 ? 4 : bits <= 384 ? 6 : bits <= 512 ? 8 : bits <= 640 ? 10 : 0;
   if (!nl) return fail(MW_EUNSUPPORTED, "w*S too large");
@@ -522,6 +556,7 @@ int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem
   P.rowsA = (int64_t)p.S_A * b.sum_M; P.rowsB = (int64_t)p.S_B * b.sum_N; P.Kpitch = L.Kpitch;
   P.S_A = p.S_A; P.S_B = p.S_B; P.D = p.D; P.w = p.w; P.group = L.sched; P.chunk = p.chunk;
   P.info = w8 + L.info; P.hdr = w8 + L.header; P.count = b.count;
+  P.item_problem = reinterpret_cast<const int32_t *>(w8 + L.items);
   P.partials = w8 + L.partials;
   P.narrow = L.narrow;
   P.next_item = &reinterpret_cast<BHeader *>(w8 + L.header)->next_item;

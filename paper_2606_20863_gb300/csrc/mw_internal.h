@@ -57,6 +57,7 @@ struct ProductLaunch {
   int64_t rowsA, rowsB, Kpitch;
   int S_A, S_B, D, w, group, chunk;
   const void *info, *hdr;
+  const int32_t *item_problem;    // batches: problem of every work item, or nullptr
   int count;
   int64_t M, N, K;
   void *partials;                 // int32 [t][M][N] (narrow) or int64 [g][M][N]

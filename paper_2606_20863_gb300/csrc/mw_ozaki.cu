@@ -73,6 +73,7 @@ constexpr int RING = 4;   // work items the producer may run ahead
 struct PParams {
   const BInfo *info;      // device array of problems, or nullptr: the one problem `single`
   const BHeader *hdr;     // totals (batched) or nullptr
+  const int32_t *item_problem;  // batched: the problem of every work item
   int count;
   int S_A, S_B, D, w, group, G, chunk_kb;
   int64_t single_work;    // work items of `single`
@@ -106,7 +107,8 @@ struct Item {
 
 __device__ __forceinline__ Item decode_item(const PParams &P, int64_t u) {
   Item x;
-  x.i = P.info ? find_problem(P.info, P.count, u, [](const BInfo &b) { return b.work; }) : 0;
+  x.i = P.item_problem ? P.item_problem[u]
+      : P.info ? find_problem(P.info, P.count, u, [](const BInfo &b) { return b.work; }) : 0;
   const BInfo &b = problem(P, x.i);
   const int64_t local = u - b.work;
   const int tiles = b.tiles_m * b.tiles_n;
@@ -482,6 +484,7 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   PParams P{};
   P.info = static_cast<const BInfo *>(a.info);
   P.hdr = static_cast<const BHeader *>(a.hdr);
+  P.item_problem = a.item_problem;
   P.count = a.count;
   P.S_A = a.S_A; P.S_B = a.S_B; P.D = a.D; P.w = a.w; P.group = a.group; P.G = G;
   P.chunk_kb = a.chunk / BK;
