@@ -219,22 +219,19 @@ __global__ void __launch_bounds__(256) batch_split_rows_kernel(
     __nv_bfloat16 *dst = pieceA + (b.rowA + r) * Kpitch;
     const int64_t plane = b.M * Kpitch;
     const int F = w * S - 2 - E;
-    for (int64_t k = 2 * lane; k < Kpitch; k += 64) {
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    for (int64_t k = lane; k < Kpitch; k += 32) {
       if (k >= K) {  // zero padding: no arithmetic
-        for (int p = 0; p < S; ++p) store2<__nv_bfloat16>(dst + k + p * plane, 0, 0);
+        for (int p = 0; p < S; ++p) dst[k + p * plane] = zero;
         continue;
       }
-      double x0[MW], x1[MW];
-      const bool v1 = k + 1 < K;
+      double x[MW];
 #pragma unroll
-      for (int j = 0; j < MW; ++j) {
-        x0[j] = base[j * b.psa + k];
-        x1[j] = v1 ? base[j * b.psa + k + 1] : 0.0;
-      }
+      for (int j = 0; j < MW; ++j) x[j] = base[j * b.psa + k];
       if (w == 8)
-        cut_pair_w8<MW, NL, __nv_bfloat16>(x0, x1, F, S, dst + k, plane, status);
+        cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst + k, plane, status);
       else
-        cut_pair<MW, NL, __nv_bfloat16>(x0, x1, F, w, S, dst + k, plane, status);
+        cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst + k, plane, status);
     }
   }
 }
@@ -302,27 +299,25 @@ __global__ void __launch_bounds__(256) batch_split_cols_kernel(
             tile[(q * 32 + kl) * 33 + tx] = (k < K && j < b.N) ? b.B[q * b.psb + k * b.ldb + j] : 0.0;
           }
         __syncthreads();
-        for (int it = 0; it < 2; ++it) {
-          const int e = threadIdx.x + 256 * it;   // 512 pairs per tile
-          const int jl = e >> 4, kl = 2 * (e & 15);
+        for (int it = 0; it < 4; ++it) {
+          const int e = threadIdx.x + 256 * it;   // 1024 entries per tile, k fastest
+          const int jl = e >> 5, kl = e & 31;
           const int64_t jj = j0 + jl, k = k0 + kl;
           if (jj >= b.N) continue;
           __nv_bfloat16 *dst = pieceB + (b.rowB + jj) * Kpitch + k;
           if (k >= K) {
-            for (int p = 0; p < S; ++p) store2<__nv_bfloat16>(dst + p * plane, 0, 0);
+            const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+            for (int p = 0; p < S; ++p) dst[p * plane] = zero;
             continue;
           }
-          double x0[MW], x1[MW];
+          double x[MW];
 #pragma unroll
-          for (int q = 0; q < MW; ++q) {
-            x0[q] = tile[(q * 32 + kl) * 33 + jl];
-            x1[q] = tile[(q * 32 + kl + 1) * 33 + jl];
-          }
+          for (int q = 0; q < MW; ++q) x[q] = tile[(q * 32 + kl) * 33 + jl];
           const int F = w * S - 2 - sE[jl];
           if (w == 8)
-            cut_pair_w8<MW, NL, __nv_bfloat16>(x0, x1, F, S, dst, plane, status);
+            cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst, plane, status);
           else
-            cut_pair<MW, NL, __nv_bfloat16>(x0, x1, F, w, S, dst, plane, status);
+            cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst, plane, status);
         }
         __syncthreads();
       }

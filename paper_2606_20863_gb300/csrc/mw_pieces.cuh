@@ -3,7 +3,9 @@
 //   fixed_point: T = sum_j trunc(x_j 2^F) in NL 64-bit limbs, two's complement;
 //   cut_pair:    the balanced base-2^w digits of two entries, least significant
 //                first with a carry, stored as bfloat16 or double; raises
-//                MW_ERANGE when T leaves [-2^(wS-1), 2^(wS-1)).
+//                MW_ERANGE when T leaves [-2^(wS-1), 2^(wS-1));
+//   cut_one, cut_one_w8: the same for one entry (w = 8: digits straight from
+//                the bytes of T plus a bias, no carry chain).
 #pragma once
 #include <cuda_bf16.h>
 
@@ -118,41 +120,128 @@ __device__ __forceinline__ void cut_pair(const double (&w0)[MW], const double (&
   store2<Out>(dst, (int)t0 + c0, (int)t1 + c1);
 }
 
-// The same for w = 8: the digits are the bytes of T (byte k = limb k/8, byte
-// k%8, least significant first), so no multi-limb shifts are needed.
+// The same for w = 8, digits from the bytes of T + H (see cut_one_w8).
+template <int NL>
+__device__ __forceinline__ bool in_range_w8(const uint64_t (&T)[NL], int S);
+template <int NL>
+__device__ __forceinline__ bool add_bias_w8(uint64_t (&T)[NL], int S);
+
 template <int MW, int NL, typename Out>
 __device__ __forceinline__ void cut_pair_w8(const double (&w0)[MW], const double (&w1)[MW], int F,
                                             int S, Out *dst, int64_t plane, unsigned int *status) {
   uint64_t T0[NL], T1[NL];
   fixed_point<MW, NL>(w0, F, T0);
   fixed_point<MW, NL>(w1, F, T1);
-  int c0 = 0, c1 = 0;
-  bool ok = true;
-  int top0 = 0, top1 = 0;
+  if (!(in_range_w8<NL>(T0, S) && in_range_w8<NL>(T1, S))) raise_status(status, MW_ERANGE);
+  const bool n0 = add_bias_w8<NL>(T0, S), n1 = add_bias_w8<NL>(T1, S);
+  Out *q = dst + (int64_t)(S - 1) * plane;
 #pragma unroll
   for (int i = 0; i < NL; ++i) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int k = 8 * i + j;
-      const int b0 = (int)((T0[i] >> (8 * j)) & 0xFF), b1 = (int)((T1[i] >> (8 * j)) & 0xFF);
+      const int u0 = (int)((T0[i] >> (8 * j)) & 0xFF), u1 = (int)((T1[i] >> (8 * j)) & 0xFF);
       if (k < S - 1) {
-        int r0 = b0 + c0, r1 = b1 + c1;
-        c0 = r0 >= 128;
-        c1 = r1 >= 128;
-        r0 -= c0 << 8;
-        r1 -= c1 << 8;
-        store2<Out>(dst + (int64_t)(S - 1 - k) * plane, r0, r1);
+        store2<Out>(q, u0 - 128, u1 - 128);
+        q -= plane;
       } else if (k == S - 1) {
-        top0 = (int)(int8_t)b0;  // T >> 8(S-1) must be a signed byte
-        top1 = (int)(int8_t)b1;
-      } else {
-        // bytes above the top digit: sign extension of the top byte
-        ok &= b0 == (top0 < 0 ? 0xFF : 0) && b1 == (top1 < 0 ? 0xFF : 0);
+        store2<Out>(q, n0 ? u0 - 256 : u0, n1 ? u1 - 256 : u1);
       }
     }
   }
+}
+
+// One entry, any w: the digits least significant first with a carry.
+template <int MW, int NL, typename Out>
+__device__ __forceinline__ void cut_one(const double (&x)[MW], int F, int w, int S, Out *dst,
+                                        int64_t plane, unsigned int *status) {
+  uint64_t T[NL];
+  fixed_point<MW, NL>(x, F, T);
+  const uint64_t mask = (1ull << w) - 1;
+  const int half = 1 << (w - 1);
+  int c = 0;
+  Out *q = dst + (int64_t)(S - 1) * plane;
+  for (int p = S - 1; p >= 1; --p, q -= plane) {
+    int r = (int)(T[0] & mask) + c;
+    c = r >= half;
+    r -= c << w;
+    *q = to_out<Out>(r);
+    shr<NL>(T, w);
+  }
+  bool ok = true;
+  const int64_t t0 = (int64_t)T[0];
+#pragma unroll
+  for (int i = 1; i < NL; ++i) ok &= T[i] == (uint64_t)(t0 >> 63);
+  ok &= t0 >= -half && t0 < half;
   if (!ok) raise_status(status, MW_ERANGE);
-  store2<Out>(dst, top0 + c0, top1 + c1);
+  *dst = to_out<Out>((int)t0 + c);
+}
+
+// One entry, w = 8.  Balanced digits d_k in [-128, 128) for k < S-1 are the
+// bytes of T + H minus 128, H = 128 (1 + 2^8 + ... + 2^(8(S-2))): adding 128 to
+// every low digit maps [-128, 128) onto the byte range, so no carry links the
+// digits.  The top digit is (T + H) >> 8(S-1), in [-128, 128] when T lies in
+// [-2^(8S-1), 2^(8S-1)) (checked on T first).
+template <int NL>
+__device__ __forceinline__ bool in_range_w8(const uint64_t (&T)[NL], int S) {
+  // the bits of T from 8S-1 up are all equal
+  const int b = 8 * S - 1, lb = b >> 6, ob = b & 63;
+  int64_t v = 0;
+#pragma unroll
+  for (int i = 0; i < NL; ++i)
+    if (i == lb) v = (int64_t)T[i] >> ob;
+  bool ok = v == 0 || v == -1;
+#pragma unroll
+  for (int i = 0; i < NL; ++i)
+    if (i > lb) ok &= T[i] == (uint64_t)v;
+  return ok;
+}
+
+// T += H = 128 (1 + 2^8 + ... + 2^(8(S-2))); returns the sign of the sum.
+template <int NL>
+__device__ __forceinline__ bool add_bias_w8(uint64_t (&T)[NL], int S) {
+  uint64_t carry = 0;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const int nb = min(max(S - 1 - 8 * i, 0), 8);          // biased bytes in limb i
+    const uint64_t h = nb == 8 ? 0x8080808080808080ull
+                               : (0x8080808080808080ull & ((1ull << (8 * nb)) - 1));
+    const uint64_t s1 = T[i] + h;
+    const uint64_t c1 = s1 < h;
+    const uint64_t s2 = s1 + carry;
+    carry = c1 | (s2 < carry);
+    T[i] = s2;
+  }
+  return (int64_t)T[NL - 1] < 0;
+}
+
+// One entry, w = 8.  Balanced digits d_k in [-128, 128) for k < S-1 are the
+// bytes of T + H minus 128: adding 128 to every low digit maps [-128, 128)
+// onto the byte range, so no carry links the digits.  The top digit is
+// (T + H) >> 8(S-1), in [-128, 128] when T lies in [-2^(8S-1), 2^(8S-1))
+// (checked on T first): byte S-1, less 256 when the sum is negative.
+template <int MW, int NL, typename Out>
+__device__ __forceinline__ void cut_one_w8(const double (&x)[MW], int F, int S, Out *dst,
+                                           int64_t plane, unsigned int *status) {
+  uint64_t T[NL];
+  fixed_point<MW, NL>(x, F, T);
+  if (!in_range_w8<NL>(T, S)) raise_status(status, MW_ERANGE);
+  const bool neg = add_bias_w8<NL>(T, S);
+  Out *q = dst + (int64_t)(S - 1) * plane;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = 8 * i + j;
+      const int u = (int)((T[i] >> (8 * j)) & 0xFF);
+      if (k < S - 1) {
+        *q = to_out<Out>(u - 128);
+        q -= plane;
+      } else if (k == S - 1) {
+        *q = to_out<Out>(neg ? u - 256 : u);
+      }
+    }
+  }
 }
 
 }  // namespace
