@@ -235,12 +235,38 @@ def timed(step, steps, flush, mw, dist, dev, phase=True):
     return step_ms, kern_ms, clk
 
 
-def roofline_of(pairs, flops_per_pair, kern_ms):
+# DRAM bytes (read + write) of one product-kernel launch, from the ncu captures
+# summarised in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), with
+# the digest of the kernel's sources at capture time: a changed kernel reports
+# no traffic until it is captured again.
+KERNEL_SOURCES = ("mw_ozaki.cu", "mw_tc.cuh", "mw_device.cuh", "mw_work.cuh")
+TRAFFIC = {   # profiles/dram_traffic_ozaki_kernel.md
+    "qd1024": {"bytes": 395499264 + 91631872, "digest": "66423667f2ce8377"},
+    "dd4096": {"bytes": 41846217472 + 1610730496, "digest": "66423667f2ce8377"},
+    "qd4096": {"bytes": 126157516800 + 2541103872, "digest": "66423667f2ce8377"},
+}
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2606_20863_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(workload):
+    t = TRAFFIC.get(workload)
+    return t["bytes"] if t and t["digest"] == kernel_digest() else None
+
+
+def roofline_of(pairs, flops_per_pair, kern_ms, workload=None):
     bf16_burst, _, _, peak_src = load_peaks()
     kern_s = statistics.mean(kern_ms) / 1e3
     achieved = pairs * flops_per_pair / kern_s / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
-            "frac": achieved / bf16_burst, "traffic": None,
+            "frac": achieved / bf16_burst, "traffic": traffic_of(workload),
             "kernel": "ozaki_kernel (tcgen05 kind::f16, bf16 integer slices)",
             "peak_source": f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json)",
             "algorithmic": f"{pairs} slice pairs x {flops_per_pair:.4g} flop = "
@@ -360,7 +386,7 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
                        "int8_peak_tops_measured": int8_peak,
                        "slice_ops_per_s_over_int8_peak":
                            (pairs * flops / kern_s / 1e12 / int8_peak) if int8_peak else None},
-            "roofline": roofline_of(pairs, flops, kern_ms), "clocks": clk, "e2e": e2e,
+            "roofline": roofline_of(pairs, flops, kern_ms, name), "clocks": clk, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps}
     if rank == 0 and not args.no_cpu:
         rows = args.cpu_rows or auto_rows(A, B)
@@ -375,13 +401,13 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
     sizes = synthetic.batch_sizes(args.count, 8, 128, seed=3)
     FA, FB, offs = synthetic.batch_flat(sizes, m=8, seed=3)
     dA, dB = torch.from_numpy(FA).to(dev), torch.from_numpy(FB).to(dev)
-    order = np.argsort(-sizes, kind="stable")
-    As, Bs = [], []
-    for i in order:
-        n, o = int(sizes[i]), int(offs[i])
-        As.append(dA[:, o:o + n * n].view(8, n, n))
-        Bs.append(dB[:, o:o + n * n].view(8, n, n))
-    batch = mw.Batch(As, Bs)
+    total = int(np.sum(sizes.astype(np.int64) ** 2))
+    dC = torch.empty((8, total), dtype=torch.float64, device=dev)
+    order = np.argsort(-sizes, kind="stable")          # largest problems first
+    n_o = sizes[order].astype(np.int64)
+    shapes = np.stack([n_o, n_o, n_o], axis=1)
+    offsets = np.stack([offs[order]] * 3, axis=1)
+    batch = mw.Batch.packed(dA, dB, dC, shapes, offsets)
     plan = batch.plan_
     flops = float(np.sum(2.0 * sizes.astype(np.float64) ** 3))
     pairs = count_pairs(plan)
@@ -399,6 +425,37 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
     torch.cuda.synchronize()
     step_ms, _, clk = timed(g.replay, args.steps, flush, mw, dist, dev, phase=False)
     value, t_step = aggregate(sum(step_ms) / 1e3, flops, args.steps, dist, dev)
+    # product-kernel time: the same call launched directly (phase events are not
+    # recorded inside a graph), as many runs as timed steps
+    _, kern_ms, _ = timed(batch.run, max(3, args.steps), flush, mw, None, dev)
+    roof = roofline_of(pairs, flops, kern_ms)
+    roof["algorithmic"] = (f"{pairs} slice pairs x sum of 2 n^3 = {pairs * flops:.3e} flop per "
+                           "launch; kernel time from direct calls of the batch")
+    # end to end through the public API: pinned host operands in, every C_i out;
+    # the batch is described, planned (exponent spreads measured on the device)
+    # and run per step
+    e2e_steps = args.e2e_steps if args.e2e_steps >= 0 else max(3, args.steps // 4)
+    e2e = None
+    if e2e_steps > 0:
+        del batch, g, dC
+        hA = torch.from_numpy(FA).pin_memory()
+        hB = torch.from_numpy(FB).pin_memory()
+        hC = torch.empty((8, total), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            eA = hA.to(dev, non_blocking=True)
+            eB = hB.to(dev, non_blocking=True)
+            eC = torch.empty((8, total), dtype=torch.float64, device=dev)
+            eb = mw.Batch.packed(eA, eB, eC, shapes, offsets)
+            eb.run()
+            hC.copy_(eC, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
+               "d2h_bytes_per_step": int(hC.numel() * 8)}
+        mw.check_status()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
@@ -409,11 +466,13 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
                        "m": 8, "count": args.count, "plan": plan.as_dict(), "slice_pairs": pairs,
                        "useful_flop_per_step": flops,
                        "l2": "flushed (256 MiB write) before every timed step"},
-            "roofline": None, "clocks": clk, "e2e": None, "gpu_launches": 4 * args.steps}
+            "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": 6 * args.steps}
     if rank == 0 and not args.no_cpu:
         from oracle import textbook
         tc = textbook.TextbookC()
-        sample = [int(i) for i in order[-400:]]          # 400 of the problems, small ones
+        from synthetic import SplitMix64
+        pick = SplitMix64(5).next(400) % np.uint64(len(sizes))
+        sample = [int(i) for i in pick]                  # 400 problems drawn with seed 5
         t0 = time.perf_counter()
         fl = 0.0
         for i in sample:
@@ -425,7 +484,7 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": fl / dt / 1e9, "unit": "GFLOP/s",
                                 "cores": tc.max_threads(), "kind": "oracle",
-                                "sample": f"400 smallest of the 20,000 problems, {dt:.2f} s"}
+                                "sample": f"400 of the {len(sizes):,} problems (SplitMix64 seed 5), {dt:.2f} s"}
     return line
 
 

@@ -235,10 +235,10 @@ int mw_gemm_backward(const mw_plan *plan_dA, const mw_plan *plan_dB,
                      double *dB, int64_t lddb, int64_t plane_stride_db,
                      void *ws, size_t ws_bytes, mw_stream_t stream);
 
-/* Profiling hook: while set, every mw_gemm records events[0] on its stream
- * before the first launch, events[1] after the pieces are cut (before the
- * product kernel), events[2] after the product kernel and events[3] after the
- * last launch.  events are cudaEvent_t created by the caller; pass NULL (or
+/* Profiling hook: while set, every mw_gemm and mw_gemm_batched records
+ * events[0] on its stream before the first launch, events[1] after the pieces
+ * are cut (before the product kernel), events[2] after the product kernel and
+ * events[3] after the last launch.  events are cudaEvent_t created by the caller; pass NULL (or
  * n = 0) to stop.  Process-wide setting, not thread safe. */
 int mw_set_phase_events(void *const *events, int n);
 

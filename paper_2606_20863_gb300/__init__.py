@@ -18,6 +18,7 @@ import ctypes
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -335,7 +336,7 @@ class Batch:
             for a, b in zip(As, Bs)]
         count = len(As)
         host = (mw_problem * count)()
-        shapes = (ctypes.c_int64 * (3 * count))()
+        shapes = np.empty((count, 3), dtype=np.int64)
         for i, (a, b, c) in enumerate(zip(As, Bs, self.Cs)):
             if a.shape[2] != b.shape[1] or a.shape[0] != self.m or b.shape[0] != self.m:
                 raise MWError(f"problem {i}: shape mismatch")
@@ -344,11 +345,45 @@ class Batch:
             pc, ldc, psc = _mat(c, "C")
             host[i] = mw_problem(a.shape[1], b.shape[2], a.shape[2], pa.value, lda, psa,
                                  pb.value, ldb, psb, pc.value, ldc, psc)
-            shapes[3 * i:3 * i + 3] = [a.shape[1], b.shape[2], a.shape[2]]
+            shapes[i] = (a.shape[1], b.shape[2], a.shape[2])
+        self._setup(bytes(host), shapes, dev, plan)
+
+    @classmethod
+    def packed(cls, A, B, C, shapes, offsets, plan: mw_plan | None = None):
+        """A batch whose matrices lie back to back in three flat m-plane tensors
+        A, B, C of shape (m, total) (contiguous rows, ld = columns): problem i
+        is (M_i, N_i, K_i) = shapes[i], its A_i, B_i, C_i start at element
+        offsets[i] = (oA, oB, oC) of every plane.  Descriptors are built without
+        a per-problem Python loop."""
+        self = cls.__new__(cls)
+        self.m = A.shape[0]
+        for X in (A, B, C):
+            if X.dim() != 2 or X.dtype != torch.float64 or X.stride(1) != 1 or X.shape[0] != self.m:
+                raise MWError("packed operands are (m, total) float64 tensors, unit column stride")
+        shapes = np.ascontiguousarray(shapes, dtype=np.int64).reshape(-1, 3)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64).reshape(-1, 3)
+        M, N, K = shapes[:, 0], shapes[:, 1], shapes[:, 2]
+        oA, oB, oC = offsets[:, 0], offsets[:, 1], offsets[:, 2]
+        if (shapes < 1).any() or (oA < 0).any() or (oB < 0).any() or (oC < 0).any() or \
+                (oA + M * K > A.shape[1]).any() or (oB + K * N > B.shape[1]).any() or \
+                (oC + M * N > C.shape[1]).any():
+            raise MWError("packed batch: a problem lies outside its flat tensor")
+        d = np.empty((len(shapes), 12), dtype=np.int64)
+        d[:, 0], d[:, 1], d[:, 2] = M, N, K
+        d[:, 3], d[:, 4], d[:, 5] = A.data_ptr() + 8 * oA, K, A.stride(0)
+        d[:, 6], d[:, 7], d[:, 8] = B.data_ptr() + 8 * oB, N, B.stride(0)
+        d[:, 9], d[:, 10], d[:, 11] = C.data_ptr() + 8 * oC, N, C.stride(0)
+        self.As, self.Bs, self.Cs = A, B, C
+        self._setup(d.tobytes(), shapes, A.device, plan)
+        return self
+
+    def _setup(self, desc: bytes, shapes: np.ndarray, dev, plan):
+        count = len(shapes)
+        sh = np.ascontiguousarray(shapes, dtype=np.int64).reshape(-1)
         self.batch = mw_batch()
-        _check(_lib.mw_batch_describe(count, shapes, ctypes.byref(self.batch)), "mw_batch_describe")
-        raw = torch.frombuffer(bytearray(ctypes.string_at(host, ctypes.sizeof(host))),
-                               dtype=torch.uint8)
+        _check(_lib.mw_batch_describe(count, sh.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      ctypes.byref(self.batch)), "mw_batch_describe")
+        raw = torch.frombuffer(bytearray(desc), dtype=torch.uint8)
         self.d_problems = raw.to(dev)
         if plan is None:
             plan = self.plan()

@@ -545,7 +545,9 @@ int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem
     return fail(MW_ENOSPC, "workspace %zu bytes, need %zu", ws_bytes, L.total);
   cudaStream_t s = (cudaStream_t)stream;
   uint8_t *w8 = static_cast<uint8_t *>(ws);
+  phase(0, s);
   if ((rc = run_front(p, b, problems, ws, L, 0, s))) return rc;
+  phase(1, s);
   ProductLaunch P{};
   P.pieceA = w8 + L.pieceA; P.pieceB = w8 + L.pieceB;
   P.rowsA = (int64_t)p.S_A * b.sum_M; P.rowsB = (int64_t)p.S_B * b.sum_N; P.Kpitch = L.Kpitch;
@@ -556,13 +558,16 @@ int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem
   P.narrow = L.narrow;
   P.next_item = &reinterpret_cast<BHeader *>(w8 + L.header)->next_item;
   if ((rc = launch_product(P, s))) return rc;
+  phase(2, s);
   const BInfo *info = reinterpret_cast<const BInfo *>(w8 + L.info);
   const BHeader *hdr = reinterpret_cast<const BHeader *>(w8 + L.header);
   switch (p.m) {
-    case 2: return combine_nl<2>(info, hdr, b, p, w8, L, s);
-    case 4: return combine_nl<4>(info, hdr, b, p, w8, L, s);
-    default: return combine_nl<8>(info, hdr, b, p, w8, L, s);
+    case 2: rc = combine_nl<2>(info, hdr, b, p, w8, L, s); break;
+    case 4: rc = combine_nl<4>(info, hdr, b, p, w8, L, s); break;
+    default: rc = combine_nl<8>(info, hdr, b, p, w8, L, s); break;
   }
+  phase(3, s);
+  return rc;
 }
 
 }  // extern "C"

@@ -20,10 +20,11 @@ std::mutex g_status_mu;
 cudaEvent_t g_phase[4] = {nullptr, nullptr, nullptr, nullptr};
 bool g_phase_on = false;
 
+}  // namespace
+
 void phase(int i, cudaStream_t s) {
   if (g_phase_on && g_phase[i]) cudaEventRecord(g_phase[i], s);
 }
-}  // namespace
 
 int fail(int code, const char *fmt, ...) {
   char buf[512];

@@ -52,6 +52,9 @@ struct OzakiArgs {
 };
 // The product kernel for one problem (info == nullptr: M, N, K) or a batch
 // (info, hdr: device arrays written by the batched prologue, mw_work.cuh).
+// Profiling hook of mw_set_phase_events: records event i on s while set.
+void phase(int i, cudaStream_t s);
+
 struct ProductLaunch {
   const void *pieceA, *pieceB;  // bf16 pieces, rows of Kpitch elements
   int64_t rowsA, rowsB, Kpitch;

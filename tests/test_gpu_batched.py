@@ -41,6 +41,34 @@ def test_batch_of_uneven_products(mw, cuda, m):
         assert exact.ExactProduct(An, Bn, rows, cols).error_ratio(C).max() <= 1.0
 
 
+def test_packed_batch_equals_list_batch(mw, cuda):
+    """Batch.packed (descriptors from flat tensors, no per-problem loop) gives
+    the same words as the list form, with rectangular problems at offsets."""
+    rng = SplitMix64(605)
+    shapes = [(5, 7, 3), (64, 1, 130), (40, 33, 64), (1, 90, 17)]
+    m = 4
+    oA, oB, oC = [], [], []
+    a = b = c = 0
+    for M, N, K in shapes:
+        oA.append(a); oB.append(b); oC.append(c)
+        a += M * K + 3; b += K * N + 5; c += M * N + 1      # gaps between problems
+    FA = uniform_mdouble(rng, m, 1, a)[:, 0, :]
+    FB = uniform_mdouble(rng, m, 1, b)[:, 0, :]
+    dA, dB = to_dev(np.ascontiguousarray(FA), cuda), to_dev(np.ascontiguousarray(FB), cuda)
+    dC = torch.zeros((m, c), dtype=torch.float64, device=cuda)
+    As = [dA[:, o:o + M * K].view(m, M, K) for o, (M, N, K) in zip(oA, shapes)]
+    Bs = [dB[:, o:o + K * N].view(m, K, N) for o, (M, N, K) in zip(oB, shapes)]
+    ref = mw.Batch(As, Bs)
+    ref.run()
+    packed = mw.Batch.packed(dA, dB, dC, shapes, list(zip(oA, oB, oC)), plan=ref.plan_)
+    packed.run()
+    mw.check_status()
+    for o, (M, N, K), C in zip(oC, shapes, ref.Cs):
+        assert torch.equal(dC[:, o:o + M * N].view(m, M, N), C)
+    with pytest.raises(mw.MWError):
+        mw.Batch.packed(dA, dB, dC, [(5, 7, 3)], [(a, 0, 0)])       # outside A
+
+
 def test_batch_replays_in_a_cuda_graph(mw, cuda):
     rng = SplitMix64(610)
     sizes = [40, 9, 77, 128, 16]
