@@ -1,3 +1,4 @@
+import json
 import os
 import sys
 
@@ -36,3 +37,19 @@ def to_dev(x, dev):
     import numpy as np
     import torch
     return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+# Worst observed |C - C_exact| / bound per workload, written as JSON to the
+# path in MW_ERROR_REPORT at the end of the session (when set).
+_WORST = {}
+
+
+def record_worst(name, ratio):
+    _WORST[name] = max(_WORST.get(name, 0.0), float(ratio))
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("MW_ERROR_REPORT")
+    if path and _WORST:
+        with open(path, "w") as f:
+            json.dump(dict(sorted(_WORST.items())), f, indent=1)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import torch
 
-from conftest import to_dev
+from conftest import record_worst, to_dev
 from oracle import exact
 from synthetic import SplitMix64, adjoint_case, uniform_mdouble
 
@@ -102,8 +102,8 @@ def test_adjoint_case_2048(mw, cuda):
     eb = [(int(i), int(j)) for i, j in zip(rng.next(32) % np.uint64(K), rng.next(32) % np.uint64(N))]
     BT = np.ascontiguousarray(B.transpose(0, 2, 1))
     AT = np.ascontiguousarray(A.transpose(0, 2, 1))
-    check_entries(dA, Wmd, BT, ea, 2)
-    check_entries(dB, AT, Wmd, eb, 2)
+    record_worst("dd adjoint dA = W B^T, 32 sampled entries", check_entries(dA, Wmd, BT, ea, 2))
+    record_worst("dd adjoint dB = A^T W, 32 sampled entries", check_entries(dB, AT, Wmd, eb, 2))
     # central differences in quad double: L is bilinear, so (L(+h) - L(-h)) / 2h is the
     # derivative up to the quad-double rounding of the two loss values
     h = Fraction(2) ** -20
