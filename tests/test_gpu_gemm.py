@@ -91,6 +91,8 @@ def check_ozaki(mw, cuda, A, B, plan, transA=False, transB=False, rows=None, col
     (8, 33, 20, 70, None, None),
     (2, 1, 1, 1, -3, 3),
     (4, 129, 257, 65, -20, 20),
+    (2, 300, 520, 100, -6, 6),      # odd number of tile rows: the last CTA pair has an empty tile
+    (2, 520, 1000, 64, None, None),
 ])
 def test_ozaki_bit_exact(mw, cuda, m, M, N, K, lo, hi):
     rng = SplitMix64(300 + m + M)
@@ -99,8 +101,10 @@ def test_ozaki_bit_exact(mw, cuda, m, M, N, K, lo, hi):
     else:
         A, B = loguniform_mdouble(rng, m, M, K, lo, hi), loguniform_mdouble(rng, m, K, N, lo, hi)
     plan = mw.plan_for(to_dev(A, cuda), to_dev(B, cuda), "ozaki")
-    rows = None if M * N <= 64 * 64 else sorted({i for i in (0, 1, 63, 64, M - 2, M - 1) if 0 <= i < M})
-    cols = None if M * N <= 64 * 64 else sorted({j for j in (0, 5, 127, 128, N - 1) if 0 <= j < N})
+    rows = None if M * N <= 64 * 64 else sorted(
+        {i for i in (0, 1, 63, 64, 128, 255, 256, M - 2, M - 1) if 0 <= i < M})
+    cols = None if M * N <= 64 * 64 else sorted(
+        {j for j in (0, 5, 127, 128, 255, 256, 511, 512, N - 1) if 0 <= j < N})
     check_ozaki(mw, cuda, A, B, plan, rows=rows, cols=cols)
 
 
