@@ -32,13 +32,19 @@
 namespace mw {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int BM = 128, BK = 64;
 constexpr double kL2Budget = 48.0 * (1 << 20);  // bytes of pieces in flight
+// Narrow batches run 128 x 256 tiles and put up to kMaxStack B slices of a
+// problem with N <= 128 side by side in one MMA (kMaxStack - 1 zero slices
+// before and after its B slices); wide batches run 128 x 128 tiles, one slice.
+constexpr int kMaxStack = 8;
 
 struct Layout {
   size_t header, info, eA, spA, eB, spB, pieceA, pieceB, items, partials, total;
   int64_t Kpitch;
   int64_t items_max;  // bound on the work items, from the batch sums
+  int64_t rowsB;      // piece rows of B (bound: every problem with the most zero slices)
+  int bn, rmax;       // tile width, most B slices per MMA
   bool narrow;   // int32 diagonal sums (D planes) or int64 group sums (G planes)
   int planes;
   int sched;     // diagonals per work item
@@ -49,6 +55,10 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 Layout layout_of(const mw_plan &p, const mw_batch &b) {
   Layout L{};
   L.Kpitch = round_up(b.max_K, 64);
+  L.narrow = narrow_partials(p.S_A, p.S_B, p.w, b.max_K);
+  L.bn = L.narrow ? 256 : 128;
+  L.rmax = L.narrow ? std::min(kMaxStack, p.D) : 1;
+  L.rowsB = (int64_t)(p.S_B + 2 * (L.rmax - 1)) * b.sum_N;
   size_t off = 0;
   L.header = off; off = a256(off + sizeof(BHeader));
   L.info = off;   off = a256(off + sizeof(BInfo) * (size_t)b.count);
@@ -57,26 +67,28 @@ Layout layout_of(const mw_plan &p, const mw_batch &b) {
   L.eB = off;     off = a256(off + 4 * (size_t)b.sum_N);
   L.spB = off;    off = a256(off + 4 * (size_t)b.sum_N);
   L.pieceA = off; off = a256(off + 2 * (size_t)p.S_A * b.sum_M * L.Kpitch);
-  L.pieceB = off; off = a256(off + 2 * (size_t)p.S_B * b.sum_N * L.Kpitch);
-  L.narrow = narrow_partials(p.S_A, p.S_B, p.w, b.max_K);
+  L.pieceB = off; off = a256(off + 2 * (size_t)L.rowsB * L.Kpitch);
   L.planes = L.narrow ? p.D : n_groups(p.D, p.group);
-  // Diagonals per work item.  The items of one tile are handed out one after
-  // another, so the CTAs at work share ceil(D / sched) items per tile; the
-  // pieces of the tiles in flight (row panel of A and column panel of B, every
-  // slice) should fit in a share of L2, or every slice pair is read from HBM.
+  // Diagonals per work item of a problem with one B slice per MMA.  The items
+  // of one tile are handed out one after another, so the CTAs at work share
+  // ceil(D / sched) items per tile; the pieces of the tiles in flight (row panel
+  // of A and column panel of B, every slice) should fit in a share of L2, or
+  // every slice pair is read from HBM.  (Stacked problems take one block of rs
+  // diagonals per item.)
   if (L.narrow) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const double tile_bytes = 2.0 * L.Kpitch * ((double)p.S_A * BM + (double)p.S_B * BN);
+    const double tile_bytes = 2.0 * L.Kpitch * ((double)p.S_A * BM + (double)p.S_B * L.bn);
     const int per_tile = (int)std::min<double>(p.D, std::ceil(nsm * tile_bytes / kL2Budget));
     L.sched = (p.D + std::max(per_tile, 1) - 1) / std::max(per_tile, 1);
   } else {
     L.sched = p.group;
   }
-  // ceil(M/BM) ceil(N/BN) <= MN/(BM BN) + M/BM + N/BN + 1 for every problem
-  L.items_max = (int64_t)n_groups(p.D, L.sched) *
-                (b.sum_MN / (BM * BN) + b.sum_M / BM + b.sum_N / BN + b.count + 3);
+  // ceil(M/BM) ceil(N/bn) <= MN/(BM bn) + M/BM + N/bn + 1 for every problem, and
+  // at most D items per tile
+  L.items_max = (int64_t)p.D *
+                (b.sum_MN / (BM * L.bn) + b.sum_M / BM + b.sum_N / L.bn + b.count + 3);
   L.items = off;  off = a256(off + 4 * (size_t)L.items_max);
   L.partials = off;
   off = a256(off + (L.narrow ? 4 : 8) * (size_t)L.planes * b.sum_MN);
@@ -112,17 +124,18 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t *sh) {
 }
 
 __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs, int count,
-                                                        int G, int planes, int S_A, int S_B,
+                                                        int D, int sched, int bn, int rmax,
+                                                        int planes, int S_A, int S_B,
                                                         int64_t Kpitch, int64_t items_max,
                                                         mw_batch want, BInfo *info, BHeader *hdr,
                                                         unsigned int *status) {
   __shared__ int64_t sh[33];
-  int64_t cM = 0, cN = 0, cMN = 0, cW = 0, cS = 0;
+  int64_t cM = 0, cN = 0, cMN = 0, cW = 0, cS = 0, cRB = 0;
   int bad = 0;
   for (int base = 0; base < count; base += 1024) {
     const int i = base + threadIdx.x;
     int64_t M = 0, N = 0, K = 0, w = 0;
-    int tm = 0, tn = 0;
+    int tm = 0, tn = 0, rs = 1, nd = 1, G = 0;
     mw_problem p{};
     if (i < count) {
       p = probs[i];
@@ -131,7 +144,11 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
                       p.lda >= K && p.ldb >= N && p.ldc >= N;
       if (!ok) { bad = 1; M = N = K = 0; }
       tm = (int)((M + BM - 1) / BM);
-      tn = (int)((N + BN - 1) / BN);
+      tn = (int)((N + bn - 1) / bn);
+      // B slices side by side when the problem's N fits twice or more in a tile
+      rs = (rmax > 1 && N > 0) ? (int)max((int64_t)1, min((int64_t)rmax, (int64_t)bn / N)) : 1;
+      nd = rs > 1 ? rs : sched;
+      G = (D + nd - 1) / nd;
       w = (int64_t)tm * tn * G;
     }
     const int64_t pM = block_exclusive_scan(M, sh) + cM; const int64_t tM = sh[32];
@@ -139,18 +156,21 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
     const int64_t pMN = block_exclusive_scan(M * N, sh) + cMN; const int64_t tMN = sh[32];
     const int64_t pW = block_exclusive_scan(w, sh) + cW; const int64_t tW = sh[32];
     const int64_t pS = block_exclusive_scan((N + 31) / 32, sh) + cS; const int64_t tS = sh[32];
+    const int64_t pRB = block_exclusive_scan((int64_t)(S_B + 2 * (rs - 1)) * N, sh) + cRB;
+    const int64_t tRB = sh[32];
     if (i < count) {
       BInfo b{};
       b.M = M; b.N = N; b.K = K;
       b.A = p.A; b.lda = p.lda; b.psa = p.plane_stride_a;
       b.B = p.B; b.ldb = p.ldb; b.psb = p.plane_stride_b;
       b.C = p.C; b.ldc = p.ldc; b.psc = p.plane_stride_c;
-      b.rowA = (int64_t)S_A * pM; b.rowB = (int64_t)S_B * pN;
+      b.rowA = (int64_t)S_A * pM; b.rowB = pRB;
       b.eA = pM; b.eB = pN; b.part = (int64_t)planes * pMN; b.work = pW; b.outs = pMN; b.stripes = pS;
       b.tiles_m = tm; b.tiles_n = tn; b.KB = (int)((K + BK - 1) / BK);
+      b.rs = rs; b.nd = nd; b.G = G;
       info[i] = b;
     }
-    cM += tM; cN += tN; cMN += tMN; cW += tW; cS += tS;
+    cM += tM; cN += tN; cMN += tMN; cW += tW; cS += tS; cRB += tRB;
   }
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
@@ -304,9 +324,15 @@ __global__ void __launch_bounds__(256) batch_split_cols_kernel(
           const int jl = e >> 5, kl = e & 31;
           const int64_t jj = j0 + jl, k = k0 + kl;
           if (jj >= b.N) continue;
-          __nv_bfloat16 *dst = pieceB + (b.rowB + jj) * Kpitch + k;
+          // slice q of column jj at row rowB + (q + rs - 1) N + jj; the rs - 1 slices
+          // before slice 0 and after slice S - 1 are zero
+          __nv_bfloat16 *dst = pieceB + (b.rowB + (int64_t)(b.rs - 1) * b.N + jj) * Kpitch + k;
+          const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+          for (int p = 1; p < b.rs; ++p) {
+            dst[-p * plane] = zero;
+            dst[(S - 1 + p) * plane] = zero;
+          }
           if (k >= K) {
-            const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
             for (int p = 0; p < S; ++p) dst[p * plane] = zero;
             continue;
           }
@@ -396,7 +422,8 @@ int check_batch(const mw_plan *p, const mw_batch *b) {
   const double bits = std::ceil(std::log2((double)S_min * (double)b->max_K)) + 2 * p->w - 2;
   if (bits > 62 || bits + (double)p->w * (p->group - 1) > 62)
     return fail(MW_EINVAL, "group %d too large for K = %lld", p->group, (long long)b->max_K);
-  if ((int64_t)p->S_A * b->sum_M > 0x7fffffffLL || (int64_t)p->S_B * b->sum_N > 0x7fffffffLL)
+  if ((int64_t)p->S_A * b->sum_M > 0x7fffffffLL ||
+      (int64_t)(p->S_B + 2 * (kMaxStack - 1)) * b->sum_N > 0x7fffffffLL)
     return fail(MW_EUNSUPPORTED, "batch too large for 32-bit piece rows");
   return MW_OK;
 }
@@ -431,7 +458,7 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
   BHeader *hdr = reinterpret_cast<BHeader *>(w8 + L.header);
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(BHeader), s);
   if (e != cudaSuccess) return cuda_fail(e, "batch header memset");
-  prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, n_groups(p.D, L.sched), L.planes, p.S_A,
+  prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, p.D, L.sched, L.bn, L.rmax, L.planes, p.S_A,
                                      p.S_B, L.Kpitch, L.items_max, b, info, hdr, status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch prologue launch");
   if (!exps_only) {
@@ -550,7 +577,7 @@ int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem
   phase(1, s);
   ProductLaunch P{};
   P.pieceA = w8 + L.pieceA; P.pieceB = w8 + L.pieceB;
-  P.rowsA = (int64_t)p.S_A * b.sum_M; P.rowsB = (int64_t)p.S_B * b.sum_N; P.Kpitch = L.Kpitch;
+  P.rowsA = (int64_t)p.S_A * b.sum_M; P.rowsB = L.rowsB; P.Kpitch = L.Kpitch;
   P.S_A = p.S_A; P.S_B = p.S_B; P.D = p.D; P.w = p.w; P.group = L.sched; P.chunk = p.chunk;
   P.info = w8 + L.info; P.hdr = w8 + L.header; P.count = b.count;
   P.item_problem = reinterpret_cast<const int32_t *>(w8 + L.items);

@@ -46,11 +46,11 @@ namespace {
 #define MW_WIDE_TILE 1   // 0: always 128 x 128 tiles (build knob for comparisons)
 #endif
 constexpr int BM = 128, BK = 64;
-constexpr int NBUF = 2;             // accumulators in tensor memory
 constexpr uint32_t STAGE_A = BM * BK * 2;
 constexpr uint32_t MAGIC_BITS = 0x4B400000u;  // bit pattern of 1.5 * 2^23
 // Kernel shapes.  Tile 128 x BN (BN = 128 or 256); NBUF accumulators of BN fp32
-// columns in tensor memory.  Two drain modes.  Narrow: every diagonal sum s_t
+// columns in tensor memory (all 512 columns: with 128-column tiles four, so that
+// the MMAs of short products run up to three drains ahead).  Two drain modes.  Narrow: every diagonal sum s_t
 // fits in int32 (checked by the host), each diagonal is accumulated in 32-bit
 // registers (arithmetic mod 2^32) and stored as int32.  Wide: a group of
 // diagonals is accumulated by Horner's rule in int64 (BN = 128 only).
@@ -61,6 +61,7 @@ template <int BN_, bool NARROW> struct Shape {
   static constexpr int WARPS = (NARROW && BN == 128) ? 16 : 8;  // drain warps
   static constexpr int COLS = BN * 4 / WARPS;                 // columns per drain thread
   static constexpr int THREADS = 64 + 32 * WARPS;
+  static constexpr int NBUF = 512 / BN;
   static constexpr int TMEM_COLS = NBUF * BN;
   static constexpr size_t SMEM = 1024 + STAGES * (STAGE_A + STAGE_B) + 512;
   static_assert(NARROW || BN == 128, "wide drain only with 128-column tiles");
@@ -84,16 +85,16 @@ struct PParams {
   BInfo single;
 };
 
-// Tensor maps over the two piece arrays with boxes of 16, 32, 64, 128 and 256
-// rows: a tile loads only the rows its problem has (rows past them would only
-// feed outputs that are never stored).
-constexpr int NBOX = 5;
+// Tensor maps over the two piece arrays with boxes of 16, 32, 48, ..., 256 rows:
+// a tile loads only the rows its problem has, rounded up to 16 (rows past them
+// would only feed outputs that are never stored).  4 KB of kernel parameters.
+constexpr int NBOX = 16;
 struct Maps {
   CUtensorMap a[NBOX], b[NBOX];
 };
-__host__ __device__ constexpr int box_rows(int i) { return 16 << i; }
+__host__ __device__ constexpr int box_rows(int i) { return 16 * (i + 1); }
 __device__ __forceinline__ int box_index(int64_t rows) {
-  return rows <= 16 ? 0 : rows <= 32 ? 1 : rows <= 64 ? 2 : rows <= 128 ? 3 : 4;
+  return rows <= 16 ? 0 : rows >= 256 ? NBOX - 1 : (int)((rows + 15) >> 4) - 1;
 }
 
 __device__ __forceinline__ const BInfo &problem(const PParams &P, int i) {
@@ -101,10 +102,13 @@ __device__ __forceinline__ const BInfo &problem(const PParams &P, int i) {
 }
 
 struct Item {
-  int i, g, t0, t1, tm, tn, KB;
+  int i, g, t0, t1, tm, tn, KB, rs;
   int64_t M, N, rowA, rowB, part;
 };
 
+// Work item u: problem, output tile, diagonals t0..t1.  Single products take
+// the diagonal groups most expensive first (gorder); a batch's problems carry
+// their own diagonals per item (nd) and items per tile (G).
 __device__ __forceinline__ Item decode_item(const PParams &P, int64_t u) {
   Item x;
   x.i = P.item_problem ? P.item_problem[u]
@@ -112,30 +116,40 @@ __device__ __forceinline__ Item decode_item(const PParams &P, int64_t u) {
   const BInfo &b = problem(P, x.i);
   const int64_t local = u - b.work;
   const int tiles = b.tiles_m * b.tiles_n;
-  x.g = P.gorder[(int)(local / tiles)];
   const int tile = (int)(local % tiles);
   x.tm = tile % b.tiles_m;
   x.tn = tile / b.tiles_m;
-  x.t0 = x.g * P.group;
-  x.t1 = min(P.D, x.t0 + P.group) - 1;
+  const int nd = P.info ? b.nd : P.group;
+  x.g = P.info ? (int)(local / tiles) : P.gorder[(int)(local / tiles)];
+  x.t0 = x.g * nd;
+  x.t1 = min(P.D, x.t0 + nd) - 1;
+  x.rs = P.info ? b.rs : 1;
   x.KB = b.KB;
   x.M = b.M; x.N = b.N; x.rowA = b.rowA; x.rowB = b.rowB; x.part = b.part;
   return x;
 }
+// A block of rs diagonals t..t+rs-1 sweeps the A slices p = plo..phi against
+// the rs B slices t-p .. t-p+rs-1 (zero slices outside 0..S_B-1): column block
+// j collects exactly the pairs of diagonal t + j.
 __device__ __forceinline__ int plo(const PParams &P, int t) { return max(0, t - P.S_B + 1); }
-__device__ __forceinline__ int phi(const PParams &P, int t) { return min(t, P.S_A - 1); }
-__device__ __forceinline__ int nsteps(const PParams &P, int t, int KB) {
-  const int n = phi(P, t) - plo(P, t) + 1;
+__device__ __forceinline__ int phi(const PParams &P, int t, int rs) {
+  return min(t + rs - 1, P.S_A - 1);
+}
+__device__ __forceinline__ int nsteps(const PParams &P, int t, int rs, int KB) {
+  const int n = phi(P, t, rs) - plo(P, t) + 1;
   return n > 0 ? n * KB : 0;
 }
 
-template <int BN_, bool NARROW>
+// STACK: B slices side by side (batches of small products); otherwise one
+// slice per MMA and the drain stores one diagonal per tile column.
+template <int BN_, bool NARROW, bool STACK>
 __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
     ozaki_kernel(const __grid_constant__ Maps maps, const PParams P) {
   using SH = Shape<BN_, NARROW>;
   constexpr int BN = SH::BN, STAGES = SH::STAGES, TMEM_COLS = SH::TMEM_COLS;
   constexpr uint32_t STAGE_B = SH::STAGE_B;
   constexpr int NUM_DRAIN_WARPS = SH::WARPS;
+  constexpr int NBUF = SH::NBUF;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -200,15 +214,17 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         ring[slot] = u;
         mbar_arrive(&uf[slot]);
         if (u < 0) break;
-        const Item x = decode_item(P, u);
+        Item x = decode_item(P, u);
+        if constexpr (!STACK) x.rs = 1;
         const int ia = box_index(min((int64_t)BM, x.M - (int64_t)x.tm * BM));
-        const int ib = box_index(min((int64_t)BN, x.N - (int64_t)x.tn * BN));
-        const uint32_t bytes = (uint32_t)(box_rows(ia) + box_rows(ib)) * BK * 2;
-        for (int t = x.t0; t <= x.t1 && !*abort; ++t) {
-          for (int p = plo(P, t); p <= phi(P, t) && !*abort; ++p) {
-            const int q = t - p;
+        const int ib = box_index(min((int64_t)BN, x.rs * x.N - (int64_t)x.tn * BN));
+        // the boxes of maps.a are at most BM rows and of maps.b at most BN rows
+        const uint32_t bytes = (uint32_t)(min(box_rows(ia), BM) + min(box_rows(ib), BN)) * BK * 2;
+        for (int t = x.t0; t <= x.t1 && !*abort; t += x.rs) {
+          for (int p = plo(P, t); p <= phi(P, t, x.rs) && !*abort; ++p) {
+            const int q = t - p;                  // first of the rs B slices
             const int ra = (int)(x.rowA + (int64_t)p * x.M + (int64_t)x.tm * BM);
-            const int rb = (int)(x.rowB + (int64_t)q * x.N + (int64_t)x.tn * BN);
+            const int rb = (int)(x.rowB + (int64_t)(q + x.rs - 1) * x.N + (int64_t)x.tn * BN);
             for (int kb = 0; kb < x.KB; ++kb, ++it) {
               const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
               if (!mbar_wait(&empty[s], ph ^ 1, P.status, abort)) break;
@@ -230,12 +246,13 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         const int64_t u = ring[slot];
         mbar_arrive(&ue[slot]);
         if (u < 0) break;
-        const Item x = decode_item(P, u);
+        Item x = decode_item(P, u);
+        if constexpr (!STACK) x.rs = 1;
         // N of the MMA: the tile's valid columns rounded up to 16
-        const int ncols = (int)min((int64_t)BN, x.N - (int64_t)x.tn * BN);
+        const int ncols = (int)min((int64_t)BN, x.rs * x.N - (int64_t)x.tn * BN);
         const uint32_t idesc = idesc_bf16(BM, (ncols + 15) & ~15);
-        for (int t = x.t0; t <= x.t1 && !*abort; ++t) {
-          const int tot = nsteps(P, t, x.KB);
+        for (int t = x.t0; t <= x.t1 && !*abort; t += x.rs) {
+          const int tot = nsteps(P, t, x.rs, x.KB);
           for (int j = 0; j < tot && !*abort; ++ch) {
             const int nk = min(P.chunk_kb, tot - j);
             const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
@@ -278,16 +295,18 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&ue[slot]);
       if (u < 0) break;
-      const Item x = decode_item(P, u);
+      Item x = decode_item(P, u);
+      if constexpr (!STACK) x.rs = 1;
       const int64_t r = (int64_t)x.tm * BM + row;
       const int64_t c0 = (int64_t)x.tn * BN + slice * COLS;
       if constexpr (NARROW) {
-        // one diagonal at a time in 32-bit accumulators, stored as int32 s_t
-        for (int t = x.t0; t <= x.t1 && ok; ++t) {
+        // one block of rs diagonals at a time in 32-bit accumulators, stored as
+        // int32 s_t; column c of the tile is column c mod N of diagonal t + c / N
+        for (int t = x.t0; t <= x.t1 && ok; t += x.rs) {
           uint32_t acc[COLS];
 #pragma unroll
           for (int i = 0; i < COLS; ++i) acc[i] = 0;
-          const int nch = (nsteps(P, t, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
+          const int nch = (nsteps(P, t, x.rs, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
           for (int c = 0; c < nch; ++c, ++ch) {
             const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
             if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], bph, P.status, abort))) {
@@ -312,12 +331,27 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
           }
           if (!ok) break;
           if (r < x.M) {
-            // plane t is column-major: lanes (consecutive rows) store consecutive words
+            // planes are column-major: lanes (consecutive rows) store consecutive words
             const uint32_t bias = (uint32_t)nch * MAGIC_BITS;
-            int32_t *dst = static_cast<int32_t *>(P.partials) + x.part + (int64_t)t * x.N * x.M + r;
+            if constexpr (STACK) {
+              const int nd = min(x.rs, x.t1 - t + 1);     // diagonals of this block to keep
+              int j = (int)(c0 / x.N);
+              int64_t col = c0 - (int64_t)j * x.N;
+              int32_t *base = static_cast<int32_t *>(P.partials) + x.part + r;
 #pragma unroll
-            for (int i = 0; i < COLS; ++i)
-              if (c0 + i < x.N) dst[(c0 + i) * x.M] = (int32_t)(acc[i] - bias);
+              for (int i = 0; i < COLS; ++i) {
+                if (j < nd) base[((int64_t)(t + j) * x.N + col) * x.M] = (int32_t)(acc[i] - bias);
+                if (++col == x.N) {
+                  col = 0;
+                  ++j;
+                }
+              }
+            } else {
+              int32_t *dst = static_cast<int32_t *>(P.partials) + x.part + (int64_t)t * x.N * x.M + r;
+#pragma unroll
+              for (int i = 0; i < COLS; ++i)
+                if (c0 + i < x.N) dst[(c0 + i) * x.M] = (int32_t)(acc[i] - bias);
+            }
           }
         }
       } else {
@@ -331,7 +365,7 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             for (int i = 0; i < 64; ++i) acc[i] <<= P.w;
             bias <<= P.w;
           }
-          const int nch = (nsteps(P, t, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
+          const int nch = (nsteps(P, t, 1, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
           bias += (uint64_t)nch * MAGIC_BITS;
           for (int c = 0; c < nch; ++c, ++ch) {
             const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
@@ -480,7 +514,8 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
     return fail(MW_EUNSUPPORTED, "more than 2^31 piece rows");
   // 128 x 256 tiles for a single wide product in narrow mode (half the A-operand
   // traffic per flop); batches of small products keep 128 x 128.
-  const int bn = (MW_WIDE_TILE && a.narrow && !a.info && a.N >= 256) ? 256 : 128;
+  const int bn = a.info ? (a.narrow ? 256 : 128)
+                        : ((MW_WIDE_TILE && a.narrow && a.N >= 256) ? 256 : 128);
   PParams P{};
   P.info = static_cast<const BInfo *>(a.info);
   P.hdr = static_cast<const BHeader *>(a.hdr);
@@ -497,6 +532,7 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
     b.tiles_m = (int)((a.M + BM - 1) / BM);
     b.tiles_n = (int)((a.N + bn - 1) / bn);
     b.KB = (int)((a.K + BK - 1) / BK);
+    b.rs = 1; b.nd = a.group; b.G = G;
     P.single_work = (int64_t)G * b.tiles_m * b.tiles_n;
   }
   // most expensive groups first: pairs on a diagonal grow, then shrink
@@ -519,14 +555,20 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   if (rc) return rc;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_kernel<128, true>,
+    cudaError_t e = cudaFuncSetAttribute(ozaki_kernel<128, true, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Shape<128, true>::SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ozaki_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(ozaki_kernel<128, false, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)Shape<128, false>::SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ozaki_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(ozaki_kernel<256, true, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Shape<256, true>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ozaki_kernel<256, true, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)Shape<256, true>::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "product kernel smem attribute");
     attr_set = true;
@@ -538,12 +580,17 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int grid = nsm;
   if (!a.info) grid = (int)std::min<int64_t>(P.single_work, nsm);
-  if (a.narrow && bn == 256)
-    ozaki_kernel<256, true><<<grid, Shape<256, true>::THREADS, Shape<256, true>::SMEM, s>>>(maps, P);
+  using S256 = Shape<256, true>;
+  using S128 = Shape<128, true>;
+  using W128 = Shape<128, false>;
+  if (a.narrow && bn == 256 && a.info)
+    ozaki_kernel<256, true, true><<<grid, S256::THREADS, S256::SMEM, s>>>(maps, P);
+  else if (a.narrow && bn == 256)
+    ozaki_kernel<256, true, false><<<grid, S256::THREADS, S256::SMEM, s>>>(maps, P);
   else if (a.narrow)
-    ozaki_kernel<128, true><<<grid, Shape<128, true>::THREADS, Shape<128, true>::SMEM, s>>>(maps, P);
+    ozaki_kernel<128, true, false><<<grid, S128::THREADS, S128::SMEM, s>>>(maps, P);
   else
-    ozaki_kernel<128, false><<<grid, Shape<128, false>::THREADS, Shape<128, false>::SMEM, s>>>(maps, P);
+    ozaki_kernel<128, false, false><<<grid, W128::THREADS, W128::SMEM, s>>>(maps, P);
   return cuda_fail(cudaGetLastError(), "product kernel launch");
 }
 

@@ -21,7 +21,12 @@ struct BInfo {            // one problem, filled by the prologue
   int64_t work;           // first work item
   int64_t outs;           // prefix sum of M*N: first output in the flat output order
   int64_t stripes;        // prefix sum of ceil(N/32): first 32-column stripe of B
-  int32_t tiles_m, tiles_n, KB, pad;
+  int32_t tiles_m, tiles_n, KB;
+  // rs: B slices side by side in one MMA (column block j of the accumulator is
+  // diagonal t + j); the piece rows of B then hold rs - 1 zero slices before
+  // slice 0 and after slice S_B - 1, slice q at rowB + (q + rs - 1) N.
+  // nd: diagonals per work item; G: work items per output tile.
+  int32_t rs, nd, G;
 };
 
 struct BHeader {          // written by the prologue
