@@ -195,9 +195,11 @@ __global__ void __launch_bounds__(256) item_table_kernel(const BInfo *info, cons
 
 // ---- 2. split ---------------------------------------------------------------------
 // Rows of the A_i: one warp per row (k contiguous, coalesced reads); the shared
-// exponent by a warp reduction, then the balanced pieces of the row.
-template <int MW, int NL>
-__global__ void __launch_bounds__(256) batch_split_rows_kernel(
+// exponent by a warp reduction, then the balanced pieces of the row.  W8: the
+// w = 8 digit cutter (compiled alone, so the kernel's code stays small).  Columns
+// from K up to K rounded to 64 are zero; the product never reads past them.
+template <int MW, int NL, bool W8>
+__global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
     const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
     __nv_bfloat16 *pieceA, int32_t *eA, int32_t *spA, int32_t *max_spread, int range,
     int exps_only, unsigned int *status) {
@@ -240,7 +242,8 @@ __global__ void __launch_bounds__(256) batch_split_rows_kernel(
     const int64_t plane = b.M * Kpitch;
     const int F = w * S - 2 - E;
     const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-    for (int64_t k = lane; k < Kpitch; k += 32) {
+    const int64_t Kp = (K + 63) & ~(int64_t)63;
+    for (int64_t k = lane; k < Kp; k += 32) {
       if (k >= K) {  // zero padding: no arithmetic
         for (int p = 0; p < S; ++p) dst[k + p * plane] = zero;
         continue;
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(256) batch_split_rows_kernel(
       double x[MW];
 #pragma unroll
       for (int j = 0; j < MW; ++j) x[j] = base[j * b.psa + k];
-      if (w == 8)
+      if constexpr (W8)
         cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst + k, plane, status);
       else
         cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst + k, plane, status);
@@ -260,8 +263,8 @@ __global__ void __launch_bounds__(256) batch_split_rows_kernel(
 // problem.  Pass 1 reads rows of the stripe (coalesced) and reduces the column
 // exponents in shared memory; pass 2 stages 32 x 32 tiles of the stripe in
 // shared memory and cuts them so that the pieces are written k-contiguous.
-template <int MW, int NL>
-__global__ void __launch_bounds__(256) batch_split_cols_kernel(
+template <int MW, int NL, bool W8>
+__global__ void __launch_bounds__(256, 3) batch_split_cols_kernel(
     const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
     __nv_bfloat16 *pieceB, int32_t *eB, int32_t *spB, int32_t *max_spread, int range,
     int exps_only, unsigned int *status) {
@@ -309,7 +312,8 @@ __global__ void __launch_bounds__(256) batch_split_cols_kernel(
     __syncthreads();
     if (!exps_only) {
       const int64_t plane = b.N * Kpitch;
-      for (int64_t k0 = 0; k0 < Kpitch; k0 += 32) {
+      const int64_t Kp = (K + 63) & ~(int64_t)63;
+      for (int64_t k0 = 0; k0 < Kp; k0 += 32) {
 #pragma unroll
         for (int q = 0; q < MW; ++q)
 #pragma unroll
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(256) batch_split_cols_kernel(
 #pragma unroll
           for (int q = 0; q < MW; ++q) x[q] = tile[(q * 32 + kl) * 33 + jl];
           const int F = w * S - 2 - sE[jl];
-          if (w == 8)
+          if constexpr (W8)
             cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst, plane, status);
           else
             cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst, plane, status);
@@ -428,27 +432,34 @@ int check_batch(const mw_plan *p, const mw_batch *b) {
   return MW_OK;
 }
 
-template <int MW, int NL>
-int launch_split_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
-                    uint8_t *w8, const Layout &L, int exps_only, cudaStream_t s) {
+template <int MW, int NL, bool W8>
+int launch_split_w(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
+                   uint8_t *w8, const Layout &L, int exps_only, cudaStream_t s) {
   BHeader *h = reinterpret_cast<BHeader *>(w8 + L.header);
-  batch_split_rows_kernel<MW, NL><<<grid_for(8), 256, 0, s>>>(
+  batch_split_rows_kernel<MW, NL, W8><<<grid_for(8), 256, 0, s>>>(
       info, hdr, b.count, p.w, p.S_A, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceA),
       reinterpret_cast<int32_t *>(w8 + L.eA), reinterpret_cast<int32_t *>(w8 + L.spA),
       h->max_spread, p.range_A, exps_only, status_ptr());
   const size_t sm = (size_t)MW * 32 * 33 * sizeof(double);
   static bool attr_set = false;  // once per instantiation
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(batch_split_cols_kernel<MW, NL>,
+    cudaError_t e = cudaFuncSetAttribute(batch_split_cols_kernel<MW, NL, W8>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_fail(e, "batched split smem attribute");
     attr_set = true;
   }
-  batch_split_cols_kernel<MW, NL><<<grid_for(4), 256, sm, s>>>(
+  batch_split_cols_kernel<MW, NL, W8><<<grid_for(4), 256, sm, s>>>(
       info, hdr, b.count, p.w, p.S_B, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceB),
       reinterpret_cast<int32_t *>(w8 + L.eB), reinterpret_cast<int32_t *>(w8 + L.spB),
       h->max_spread + 1, p.range_B, exps_only, status_ptr());
   return MW_OK;
+}
+
+template <int MW, int NL>
+int launch_split_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
+                    uint8_t *w8, const Layout &L, int exps_only, cudaStream_t s) {
+  return p.w == 8 ? launch_split_w<MW, NL, true>(info, hdr, b, p, w8, L, exps_only, s)
+                  : launch_split_w<MW, NL, false>(info, hdr, b, p, w8, L, exps_only, s);
 }
 
 int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void *ws,
