@@ -14,7 +14,146 @@
 namespace mw {
 namespace {
 
-// Fixed-point value of one entry in NL limbs (two's complement, little endian).
+// T += A and T -= A on NL 64-bit limbs, one carry chain of add.cc/addc
+// (sub.cc/subc) instructions.
+template <int NL>
+__device__ __forceinline__ void add_limbs(uint64_t (&T)[NL], const uint64_t (&A)[NL]);
+template <int NL>
+__device__ __forceinline__ void sub_limbs(uint64_t (&T)[NL], const uint64_t (&A)[NL]);
+template <>
+__device__ __forceinline__ void add_limbs<2>(uint64_t (&T)[2], const uint64_t (&A)[2]) {
+  asm("{\n"
+      "add.cc.u64 %0, %0, %2;\n"
+      "addc.u64 %1, %1, %3;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1])
+      : "l"(A[0]), "l"(A[1]));
+}
+template <>
+__device__ __forceinline__ void sub_limbs<2>(uint64_t (&T)[2], const uint64_t (&A)[2]) {
+  asm("{\n"
+      "sub.cc.u64 %0, %0, %2;\n"
+      "subc.u64 %1, %1, %3;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1])
+      : "l"(A[0]), "l"(A[1]));
+}
+template <>
+__device__ __forceinline__ void add_limbs<4>(uint64_t (&T)[4], const uint64_t (&A)[4]) {
+  asm("{\n"
+      "add.cc.u64 %0, %0, %4;\n"
+      "addc.cc.u64 %1, %1, %5;\n"
+      "addc.cc.u64 %2, %2, %6;\n"
+      "addc.u64 %3, %3, %7;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3])
+      : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]));
+}
+template <>
+__device__ __forceinline__ void sub_limbs<4>(uint64_t (&T)[4], const uint64_t (&A)[4]) {
+  asm("{\n"
+      "sub.cc.u64 %0, %0, %4;\n"
+      "subc.cc.u64 %1, %1, %5;\n"
+      "subc.cc.u64 %2, %2, %6;\n"
+      "subc.u64 %3, %3, %7;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3])
+      : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]));
+}
+template <>
+__device__ __forceinline__ void add_limbs<6>(uint64_t (&T)[6], const uint64_t (&A)[6]) {
+  asm("{\n"
+      "add.cc.u64 %0, %0, %6;\n"
+      "addc.cc.u64 %1, %1, %7;\n"
+      "addc.cc.u64 %2, %2, %8;\n"
+      "addc.cc.u64 %3, %3, %9;\n"
+      "addc.cc.u64 %4, %4, %10;\n"
+      "addc.u64 %5, %5, %11;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3]), "+l"(T[4]), "+l"(T[5])
+      : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]));
+}
+template <>
+__device__ __forceinline__ void sub_limbs<6>(uint64_t (&T)[6], const uint64_t (&A)[6]) {
+  asm("{\n"
+      "sub.cc.u64 %0, %0, %6;\n"
+      "subc.cc.u64 %1, %1, %7;\n"
+      "subc.cc.u64 %2, %2, %8;\n"
+      "subc.cc.u64 %3, %3, %9;\n"
+      "subc.cc.u64 %4, %4, %10;\n"
+      "subc.u64 %5, %5, %11;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3]), "+l"(T[4]), "+l"(T[5])
+      : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]));
+}
+template <>
+__device__ __forceinline__ void add_limbs<8>(uint64_t (&T)[8], const uint64_t (&A)[8]) {
+  asm("{\n"
+      "add.cc.u64 %0, %0, %8;\n"
+      "addc.cc.u64 %1, %1, %9;\n"
+      "addc.cc.u64 %2, %2, %10;\n"
+      "addc.cc.u64 %3, %3, %11;\n"
+      "addc.cc.u64 %4, %4, %12;\n"
+      "addc.cc.u64 %5, %5, %13;\n"
+      "addc.cc.u64 %6, %6, %14;\n"
+      "addc.u64 %7, %7, %15;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3]), "+l"(T[4]), "+l"(T[5]), "+l"(T[6]), "+l"(T[7])
+      : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]));
+}
+template <>
+__device__ __forceinline__ void sub_limbs<8>(uint64_t (&T)[8], const uint64_t (&A)[8]) {
+  asm("{\n"
+      "sub.cc.u64 %0, %0, %8;\n"
+      "subc.cc.u64 %1, %1, %9;\n"
+      "subc.cc.u64 %2, %2, %10;\n"
+      "subc.cc.u64 %3, %3, %11;\n"
+      "subc.cc.u64 %4, %4, %12;\n"
+      "subc.cc.u64 %5, %5, %13;\n"
+      "subc.cc.u64 %6, %6, %14;\n"
+      "subc.u64 %7, %7, %15;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3]), "+l"(T[4]), "+l"(T[5]), "+l"(T[6]), "+l"(T[7])
+      : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]));
+}
+template <>
+__device__ __forceinline__ void add_limbs<10>(uint64_t (&T)[10], const uint64_t (&A)[10]) {
+  asm("{\n"
+      "add.cc.u64 %0, %0, %10;\n"
+      "addc.cc.u64 %1, %1, %11;\n"
+      "addc.cc.u64 %2, %2, %12;\n"
+      "addc.cc.u64 %3, %3, %13;\n"
+      "addc.cc.u64 %4, %4, %14;\n"
+      "addc.cc.u64 %5, %5, %15;\n"
+      "addc.cc.u64 %6, %6, %16;\n"
+      "addc.cc.u64 %7, %7, %17;\n"
+      "addc.cc.u64 %8, %8, %18;\n"
+      "addc.u64 %9, %9, %19;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3]), "+l"(T[4]), "+l"(T[5]), "+l"(T[6]), "+l"(T[7]), "+l"(T[8]), "+l"(T[9])
+      : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(A[8]), "l"(A[9]));
+}
+template <>
+__device__ __forceinline__ void sub_limbs<10>(uint64_t (&T)[10], const uint64_t (&A)[10]) {
+  asm("{\n"
+      "sub.cc.u64 %0, %0, %10;\n"
+      "subc.cc.u64 %1, %1, %11;\n"
+      "subc.cc.u64 %2, %2, %12;\n"
+      "subc.cc.u64 %3, %3, %13;\n"
+      "subc.cc.u64 %4, %4, %14;\n"
+      "subc.cc.u64 %5, %5, %15;\n"
+      "subc.cc.u64 %6, %6, %16;\n"
+      "subc.cc.u64 %7, %7, %17;\n"
+      "subc.cc.u64 %8, %8, %18;\n"
+      "subc.u64 %9, %9, %19;\n"
+      "}"
+      : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3]), "+l"(T[4]), "+l"(T[5]), "+l"(T[6]), "+l"(T[7]), "+l"(T[8]), "+l"(T[9])
+      : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(A[8]), "l"(A[9]));
+}
+
+// Fixed-point value of one entry in NL limbs (two's complement, little endian):
+// T = sum_j trunc(x_j 2^F), every word's truncated magnitude (a 53-bit integer
+// shifted to limbs li, li+1) added or subtracted with one carry chain.
 template <int MW, int NL>
 __device__ __forceinline__ void fixed_point(const double (&w)[MW], int F, uint64_t (&T)[NL]) {
 #pragma unroll
@@ -37,19 +176,11 @@ __device__ __forceinline__ void fixed_point(const double (&w)[MW], int F, uint64
       lo = M << off;
       hi = off ? (M >> (64 - off)) : 0;
     }
-    // T += (neg ? -1 : 1) * (hi:lo << 64*li), as T + (~V) + 1 when negative
-    uint64_t carry = neg ? 1 : 0;
+    uint64_t A[NL];
 #pragma unroll
-    for (int i = 0; i < NL; ++i) {
-      uint64_t a = (i == li) ? lo : ((i == li + 1) ? hi : 0);
-      if (neg) a = ~a;
-      const uint64_t s1 = T[i] + a;
-      const uint64_t c1 = s1 < a;
-      const uint64_t s2 = s1 + carry;
-      const uint64_t c2 = s2 < carry;
-      T[i] = s2;
-      carry = c1 | c2;
-    }
+    for (int i = 0; i < NL; ++i) A[i] = (i == li) ? lo : ((i == li + 1) ? hi : 0);
+    if (neg) sub_limbs<NL>(T, A);
+    else add_limbs<NL>(T, A);
   }
 }
 
