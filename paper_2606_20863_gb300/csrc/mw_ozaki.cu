@@ -7,27 +7,33 @@
 // w <= 8, stored in bfloat16 (exact); a product of two pieces is at most
 // 2^(2w-2) and a sum of `chunk` of them is at most 2^22, so the fp32
 // accumulators of the tensor core hold exact integers.  After every chunk the
-// accumulator is drained from tensor memory into 64-bit integers:
+// accumulator is drained from tensor memory into integer registers:
 //   v + 1.5*2^23 (one fp32 add, exact for |v| <= 2^22) has bit pattern
 //   0x4B400000 + v, which is added as an unsigned 32-bit value; the constant
-//   is subtracted once per group (arithmetic mod 2^64, exact because the true
-//   group value fits in int64).
-// A group of `group` consecutive diagonals t0..t1 is fused by Horner's rule,
-// V = sum_t s_t 2^(w (t1 - t)), and written to the partial-sum buffer
-// ([group][M][N] per problem); the fusion adds the groups exactly,
-// X = sum_g V_g 2^(w (D-1-t1_g)), and rounds X 2^(E_i + E_j + 4 - w(D+1)) to
-// nearest into m words, one after the other (greedy), in integer arithmetic.
+//   times the number of chunks is subtracted at the end.
+// Narrow mode (every s_t fits in int32): each diagonal sum is accumulated mod
+// 2^32 and stored as an int32 plane.  Wide mode: a group of diagonals t0..t1
+// is accumulated by Horner's rule mod 2^64, V = sum_t s_t 2^(w (t1 - t)), and
+// stored as an int64 plane.  Planes are column-major per problem.  The fusion
+// adds the planes exactly into one integer X and rounds X 2^(E_i + E_j + 4 -
+// w(D+1)) to nearest into m words, one after the other (greedy).
 //
-// Product kernel (one 128 x 128 output tile of one diagonal group per work item,
-// one CTA per SM, persistent):
+// Product kernel (persistent, one CTA per SM; a work item is one output tile of
+// one diagonal group):
 //   warp 0      scheduler and TMA producer: takes work items from a global
-//               counter in index order (most expensive groups first) and hands
-//               them to the other roles through a small ring in shared memory;
-//               piece tiles 128 x 64 of A_p and B_q per pipeline stage
+//               counter in index order and hands them to the other roles
+//               through a small ring in shared memory; per pipeline stage a
+//               128 x 64 box of A_p and up to 256 x 64 of B_q (box heights in
+//               steps of 16 rows, as many as the tile has)
 //   warp 1      tensor-memory allocation and the single MMA-issuing thread
-//   warps 2..9  drain: warp w reads TMEM lanes 32 (w % 4).., columns 64 ((w-2)/4)..
-// The same kernel serves one product (problem given in the launch parameters)
-// and batches (device array of problems, mw_batched.cu).  Every wait is bounded.
+//   warps 2..   drain: warp w reads TMEM lanes 32 (w % 4).. and its share of columns
+// Tiles are 128 x 256 (single products with N >= 256, and batches) or 128 x 128.
+// Batches of small products (N <= 128) put rs = floor(256 / N) B slices of a
+// problem side by side in one MMA: column block j of the accumulator is then
+// diagonal t + j (zero slices before and after the B slices keep every block
+// exact).  The same kernel serves one product (problem given in the launch
+// parameters) and batches (device array of problems, mw_batched.cu).  Every wait
+// is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
