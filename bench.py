@@ -49,10 +49,12 @@ def parse():
                     help="end-to-end runs from host memory (-1 = steps/4, at least 3; 0 = leave out)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows in the CPU sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8],
+                    help="table2: words per m-double (2, 4 or 8)")
     ap.add_argument("--count", type=int, default=20000,
                     help="od_batch: number of products (20,000 is the benchmark; fewer for profiling)")
     ap.add_argument("--workload", default="qd1024",
-                    choices=["qd1024", "dd4096", "qd4096", "od_batch", "adjoint"],
+                    choices=["qd1024", "dd4096", "qd4096", "od_batch", "adjoint", "table2"],
                     help="qd1024 (default): the benchmark line; the others measure the other "
                          "configurations of the method")
     return ap.parse_args()
@@ -594,6 +596,97 @@ def run_adjoint(args, mw, torch, dist, rank, world, dev):
     return line
 
 
+# Table 2 of the paper: 1,024 inner products of length 6,144 on the Section 2 bit
+# pattern, one thread of a Xeon 5318Y (milliseconds: ordinary, vectorized).
+PAPER_TABLE2_MS = {2: (158.0, 69.0), 4: (1977.0, 318.0), 8: (6428.0, 1520.0)}
+# integer multiply-adds d_a d_b -> int64 per clock and SM assumed for the
+# inner-product kernel's roofline (half the 128 int32 lanes of an SM)
+IMAD_WIDE_PER_CLK_SM = 64
+
+
+def run_table2(args, mw, torch, dist, rank, world, dev):
+    """Table 2's workload on the GPU: 1,024 m-double inner products of length
+    6,144, both vectors on the Section 2 bit pattern (seed 5), mw_dot_batched."""
+    import synthetic
+    m = args.m
+    A, B = synthetic.table2_operands(m)
+    _, count, K = A.shape
+    tA, tB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    plan = mw.plan_dot(tA, tB)
+    C = torch.empty((m, count), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flops = 2.0 * K * count
+
+    def step():
+        mw.mw_dot_batched(tA, tB, plan, C=C, check=False)
+
+    for _ in range(args.warmup):
+        step()
+    mw.check_status()
+    torch.cuda.synchronize()
+    step_ms, _, clk = timed(step, args.steps, flush, mw, dist, dev, phase=False)
+    value, t_step = aggregate(sum(step_ms) / 1e3, flops, args.steps, dist, dev)
+    pairs = sum(1 for p in range(plan.S_A) for q in range(plan.S_B) if p + q < plan.D)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = nsm * IMAD_WIDE_PER_CLK_SM * (clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    kern_s = statistics.mean(step_ms) / 1e3
+    achieved = pairs * K * count / kern_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T multiply-adds/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "dot_kernel (24-bit digits, int64 diagonal sums on the integer units)",
+            "peak_source": f"{nsm} SMs x {IMAD_WIDE_PER_CLK_SM} int32 x int32 -> int64 "
+                           "multiply-adds per clock x max SM clock (assumed rate)",
+            "algorithmic": f"{pairs} digit pairs per entry x {K} x {count} per launch"}
+
+    e2e_steps = args.e2e_steps if args.e2e_steps >= 0 else max(3, args.steps // 4)
+    e2e = None
+    if e2e_steps > 0:
+        hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+        hC = torch.empty((m, count), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps + 1):          # the first run is an untimed warm-up
+            if i == 1:
+                t0 = time.perf_counter()
+            eA = hA.to(dev, non_blocking=True)
+            eB = hB.to(dev, non_blocking=True)
+            out = mw.mw_dot_batched(eA, eB, check=False)   # plans from the data (synchronizes)
+            hC.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
+               "d2h_bytes_per_step": int(hC.numel() * 8)}
+        mw.check_status()
+    ordinary, vectorized = PAPER_TABLE2_MS[m]
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"Table 2: {count} m-double inner products of length {K}, "
+                                   "vectors on the Section 2 bit pattern, seed 5",
+                       "m": m, "count": count, "K": K, "plan": plan.as_dict(),
+                       "form": "MW_DOT: 24-bit digits, int64 diagonal sums, exact fusion",
+                       "paper_table2_ms": {"ordinary": ordinary, "vectorized": vectorized,
+                                           "hardware": "Xeon 5318Y, one thread"},
+                       "speedup_vs_paper_vectorized": vectorized / (t_step * 1e3 / args.steps),
+                       "l2": "flushed (256 MiB write) before every timed step"},
+            "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": 1 * args.steps}
+    if rank == 0 and not args.no_cpu:
+        from oracle import textbook
+        tc = textbook.TextbookC()
+        t0 = time.perf_counter()
+        for i in range(count):
+            tc.gemm(np.ascontiguousarray(A[:, i:i + 1, :]),
+                    np.ascontiguousarray(B[:, i:i + 1, :].transpose(0, 2, 1)), threads=1)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"all {count} inner products, one thread as in Table 2, "
+                                          f"{dt:.2f} s"}
+    return line
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -608,6 +701,8 @@ def main():
         line = run_batch(args, mw, torch, dist, rank, world, dev)
     elif args.workload == "adjoint":
         line = run_adjoint(args, mw, torch, dist, rank, world, dev)
+    elif args.workload == "table2":
+        line = run_table2(args, mw, torch, dist, rank, world, dev)
     else:
         line = run_single(args, args.workload, mw, torch, dist, rank, world, dev)
     if rank == 0:

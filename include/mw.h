@@ -26,6 +26,10 @@
  *             before that), the "stepping stone to the Ozaki scheme" of
  *             Section 1; step 4 is exact integer fusion and rounding to nearest
  *             of each word in turn.
+ * Inner products (mw_dot_batched, the workload of Table 2) use a third form:
+ *   MW_DOT    pieces are 24-bit integers, products summed in int64 on the
+ *             integer units (no operand reuse, so no tensor cores); exact
+ *             integer fusion and rounding as for MW_OZAKI.
  *
  * Conventions for every entry point:
  *  - Device pointers unless the name says otherwise; the caller owns all memory.
@@ -65,14 +69,14 @@ enum {
 };
 
 /* forms of the product */
-enum { MW_PLAIN = 0, MW_OZAKI = 1 };
+enum { MW_PLAIN = 0, MW_OZAKI = 1, MW_DOT = 2 };
 
 /* digit formats written by mw_split */
 enum { MW_DIGITS_BF16 = 0, MW_DIGITS_F64 = 1 };
 
 /* A plan fixes the slicing of a product.  mw_plan_gemm fills it from the error
  * analysis (see there); a caller may also set the fields directly.
- *   w      piece width in bits (MW_OZAKI: 7 or 8; MW_PLAIN: 1..26)
+ *   w      piece width in bits (MW_OZAKI: 7 or 8; MW_PLAIN: 1..26; MW_DOT: 24)
  *   S_A    pieces per entry of op(A); S_B pieces per entry of op(B)
  *   D      diagonals kept: pairs (p, q) with p < S_A, q < S_B, p + q < D
  *   group  diagonals fused into one 64-bit partial sum (MW_OZAKI)
@@ -89,8 +93,11 @@ typedef struct mw_plan {
  * most range_A (range_B) binary orders of magnitude, measured as max minus min
  * of ilogb+1 over the nonzero entries.  Host only, no GPU work.
  * plan->w on input: 0 lets the planner choose (MW_OZAKI 8, MW_PLAIN the widest
- * width whose sums stay exact); a width in range (2..8 for MW_OZAKI, 4..26 for
- * MW_PLAIN) is used as given.  Zero the struct before the call.
+ * width whose sums stay exact, MW_DOT 24); a width in range (2..8 for MW_OZAKI,
+ * 4..26 for MW_PLAIN, 24 for MW_DOT) is used as given.  Zero the struct before
+ * the call.  MW_DOT plans one inner product of length K (M = N = 1) with
+ * S_A = S_B = the smallest compiled piece count that covers the analysis
+ * (2: 4..8, 4: 8..12, 8: 17..21) and D <= S + 4.
  * Returns MW_EINVAL for bad arguments, MW_EUNSUPPORTED if no plan fits the
  * exactness thresholds (e.g. K too long for MW_PLAIN). */
 int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, int range_B,
@@ -167,6 +174,22 @@ int mw_gemm_noalloc(const mw_plan *plan, int transA, int transB, int64_t M, int6
                     const double *A, int64_t lda, int64_t plane_stride_a,
                     const double *B, int64_t ldb, int64_t plane_stride_b,
                     double *C, int64_t ldc, int64_t plane_stride_c, mw_stream_t stream);
+
+/* ---- inner products (Section 2: the s_i of an inner product; Table 2 times
+ * 1,024 inner products of length 6,144) ------------------------------------ */
+
+/* c_i = sum_k a_ik b_ik for i < count, every product error-free summed as in
+ * Section 2 with the plan's pieces (mw_plan_gemm(m, MW_DOT, 1, 1, K, ...)):
+ * |c_i - exact| <= 2K 2^(-52m) sum_k |a_ik||b_ik| for operands within the
+ * plan's exponent spreads.  a_i is row i of A (count x K, m planes, row stride
+ * lda, plane stride plane_stride_a), b_i row i of B (likewise); c_i is entry i
+ * of every plane of C (plane stride plane_stride_c).  One CTA per inner product;
+ * no workspace, asynchronous.  MW_EINVAL for a plan of another form or bad
+ * arguments, MW_EUNSUPPORTED for piece counts the kernel is not compiled for;
+ * device status bits as for mw_gemm. */
+int mw_dot_batched(const mw_plan *plan, int64_t count, int64_t K, const double *A, int64_t lda,
+                   int64_t plane_stride_a, const double *B, int64_t ldb, int64_t plane_stride_b,
+                   double *C, int64_t plane_stride_c, mw_stream_t stream);
 
 /* ---- batches of independent products (power-series coefficient convolutions,
  * Section 1, come as many small products of uneven sizes) -------------------- */

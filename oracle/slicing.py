@@ -153,17 +153,22 @@ def diagonal_sums(dA: np.ndarray, dB: np.ndarray, D: int) -> np.ndarray:
     """s[t, i, j] = sum_{p+q=t} sum_k dA[p, i, k] dB[q, j, k]  (Section 2 s_i).
 
     Products of digit matrices use numpy's int64 matmul (an exact integer
-    library primitive); the magnitude bound below rules out overflow."""
+    library primitive) while the magnitude bound rules out overflow, and
+    Python integers (numpy object arrays, exact at any size) otherwise."""
     S_A, M, K = dA.shape
     S_B, N, K2 = dB.shape
     assert K == K2
     amax = int(np.abs(dA).max()) if dA.size else 0
     bmax = int(np.abs(dB).max()) if dB.size else 0
-    if amax * bmax * K * min(S_A, S_B) >= (1 << 62):
-        raise OverflowError("diagonal sum may exceed int64")
-    s = np.zeros((D, M, N), dtype=np.int64)
+    if amax * bmax * K * min(S_A, S_B) < (1 << 62):
+        s = np.zeros((D, M, N), dtype=np.int64)
+        for p, q in pairs(S_A, S_B, D):
+            s[p + q] += dA[p] @ dB[q].T
+        return s
+    oA, oB = dA.astype(object), dB.astype(object)
+    s = np.zeros((D, M, N), dtype=object)
     for p, q in pairs(S_A, S_B, D):
-        s[p + q] += dA[p] @ dB[q].T
+        s[p + q] = s[p + q] + oA[p].dot(oB[q].T)
     return s
 
 

@@ -26,9 +26,9 @@ _LIB_PATH = os.path.join(_HERE, "libmw.so")
 
 MW_OK, MW_EINVAL, MW_ERANGE, MW_ENONFINITE, MW_ECUDA, MW_ETIMEOUT, MW_ENOSPC, MW_WRANGE = (
     0, 1, 2, 4, 8, 16, 32, 64)
-MW_PLAIN, MW_OZAKI = 0, 1
+MW_PLAIN, MW_OZAKI, MW_DOT = 0, 1, 2
 MW_DIGITS_BF16, MW_DIGITS_F64 = 0, 1
-_MODES = {"plain": MW_PLAIN, "ozaki": MW_OZAKI}
+_MODES = {"plain": MW_PLAIN, "ozaki": MW_OZAKI, "dot": MW_DOT}
 STATUS_NAMES = {MW_ERANGE: "ERANGE", MW_ENONFINITE: "ENONFINITE", MW_ETIMEOUT: "ETIMEOUT",
                 MW_WRANGE: "WRANGE"}
 
@@ -88,6 +88,7 @@ def _load():
         "mw_measure_spread_batched": [i32, ctypes.POINTER(mw_batch), vp, vp, ctypes.c_size_t,
                                       ip, ip, vp],
         "mw_gemm_batched": [pp, ctypes.POINTER(mw_batch), vp, vp, ctypes.c_size_t, vp],
+        "mw_dot_batched": [pp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, vp],
         "mw_set_phase_events": [ctypes.POINTER(ctypes.c_void_p), i32],
     }
     for name, args in sig.items():
@@ -105,7 +106,8 @@ EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_works
             "mw_gemm",
             "mw_measure_spread", "mw_gemm_backward", "mw_get_status", "mw_last_error",
             "mw_version", "mw_set_phase_events", "mw_gemm_noalloc", "mw_batch_describe",
-            "mw_gemm_batched_workspace_size", "mw_measure_spread_batched", "mw_gemm_batched")
+            "mw_gemm_batched_workspace_size", "mw_measure_spread_batched", "mw_gemm_batched",
+            "mw_dot_batched")
 
 
 def _check(rc: int, what: str):
@@ -452,3 +454,34 @@ class MWGemm(torch.autograd.Function):
         dA, dB = mw_gemm_backward(A, B, G, mode=ctx.mode, need_dA=ctx.needs_input_grad[0],
                                   need_dB=ctx.needs_input_grad[1])
         return dA, dB, None
+
+
+def plan_dot(A: torch.Tensor, B: torch.Tensor) -> mw_plan:
+    """MW_DOT plan for the inner products of the rows of A and B, both
+    (m, count, K), with the exponent spreads measured on them (synchronizes)."""
+    m, count, K = A.shape
+    ra, rb = mw_measure_spread(A, B, False, True)
+    return mw_plan_gemm(m, "dot", 1, 1, K, ra, rb)
+
+
+def mw_dot_batched(A: torch.Tensor, B: torch.Tensor, plan: mw_plan | None = None,
+                   C: torch.Tensor | None = None, check: bool = True) -> torch.Tensor:
+    """c_i = sum_k A[:, i, k] B[:, i, k] in m-double precision for every row i;
+    A and B are (m, count, K), the result (m, count)."""
+    if A.dim() != 3 or B.shape != A.shape:
+        raise MWError("A and B must be (m, count, K) tensors of one shape")
+    m, count, K = A.shape
+    if plan is None:
+        plan = plan_dot(A, B)
+    if C is None:
+        C = torch.empty((m, count), dtype=torch.float64, device=A.device)
+    pa, lda, psa = _mat(A, "A")
+    pb, ldb, psb = _mat(B, "B")
+    if C.dtype != torch.float64 or not C.is_cuda or C.shape != (m, count) or C.stride(1) != 1:
+        raise MWError("C must be a CUDA float64 (m, count) tensor with unit column stride")
+    _check(_lib.mw_dot_batched(ctypes.byref(plan), count, K, pa, lda, psa, pb, ldb, psb,
+                               ctypes.c_void_p(C.data_ptr()), C.stride(0), _stream()),
+           "mw_dot_batched")
+    if check:
+        check_status()
+    return C

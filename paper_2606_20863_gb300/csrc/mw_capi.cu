@@ -213,8 +213,25 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
     if (w < 4) return fail(MW_EUNSUPPORTED, "K = %lld too long for exact FP64 sums", (long long)K);
     p.group = 1;
     p.chunk = 0;
+  } else if (mode == MW_DOT) {
+    if (want_w != 0 && want_w != 24) return fail(MW_EINVAL, "MW_DOT pieces are 24 bits");
+    if (M != 1 || N != 1) return fail(MW_EINVAL, "MW_DOT plans one inner product: M = N = 1");
+    finish(24);
+    int lo = 0, hi = 0;
+    dot_pieces_range(m, &lo, &hi);
+    const int S = std::max(std::max(p.S_A, p.S_B), lo);
+    if (S > hi) return fail(MW_EUNSUPPORTED, "inner products need %d pieces, at most %d", S, hi);
+    p.S_A = p.S_B = S;
+    const double bitsD = 52.0 * m + range_A + range_B + std::log2((double)S) + 6.0 - lgK;
+    p.D = std::min(ceil_div_bits(bitsD, 24), 2 * S - 1);
+    if (p.D > S + 4) return fail(MW_EUNSUPPORTED, "inner products keep at most S + 4 diagonals");
+    // a thread's int64 diagonal sums take ceil(K / 256) products below 2^46 each
+    if ((double)S * std::ceil((double)K / 256.0) > std::ldexp(1.0, 16))
+      return fail(MW_EUNSUPPORTED, "K = %lld too long for the inner-product kernel", (long long)K);
+    p.group = 1;
+    p.chunk = 0;
   } else {
-    return fail(MW_EINVAL, "mode must be MW_PLAIN or MW_OZAKI");
+    return fail(MW_EINVAL, "mode must be MW_PLAIN, MW_OZAKI or MW_DOT");
   }
   *plan = p;
   return MW_OK;

@@ -52,6 +52,9 @@ struct OzakiArgs {
 };
 // The product kernel for one problem (info == nullptr: M, N, K) or a batch
 // (info, hdr: device arrays written by the batched prologue, mw_work.cuh).
+// Pieces per entry the inner-product kernel is compiled for (w = 24).
+int dot_pieces_range(int m, int *lo, int *hi);
+
 // Profiling hook of mw_set_phase_events: records event i on s while set.
 void phase(int i, cudaStream_t s);
 

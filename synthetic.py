@@ -23,7 +23,8 @@ pattern is Section 2):
   [-20, 20]).
 * ``paper_pattern_mdouble``: every word a positive double whose 52 fraction
   bits follow the Section 2 pattern ``1 b^12`` four times, the words of one
-  entry placed 52 bits apart as in the paper's double doubles.
+  entry placed 52 bits apart as in the paper's double doubles (Table 2's
+  1,024 inner products of length 6,144: ``table2_operands``).
 """
 from __future__ import annotations
 
@@ -180,3 +181,10 @@ def adjoint_case(seed: int = 4, M: int = 2048, K: int = 1024, N: int = 2048):
     B = uniform_mdouble(rng, 2, K, N)
     W = rng.sym(M * N).reshape(M, N)
     return A, B, W
+
+
+def table2_operands(m: int, count: int = 1024, K: int = 6144, seed: int = 5):
+    """Table 2's workload: count inner products of length K, both vectors of
+    every product m-doubles on the Section 2 bit pattern; rows of A and B."""
+    rng = SplitMix64(seed)
+    return paper_pattern_mdouble(rng, m, count, K), paper_pattern_mdouble(rng, m, count, K)

@@ -121,6 +121,31 @@ def test_diagonal_sums_brute_force():
                 assert sp.s[t, i, j] == s
 
 
+def test_diagonal_sums_beyond_int64_brute_force():
+    """24-bit digits over a long K: diagonal sums past 2^63 are still exact
+    (checked by loops over p, q, k in Python integers)."""
+    rng = SplitMix64(34)
+    A = uniform_mdouble(rng, 8, 1, 6144)
+    B = uniform_mdouble(rng, 8, 6144, 1)
+    w, S, D = 24, 19, 20
+    sp = slicing.SlicedProduct(A, B, w, S, S, D)
+    assert sp.s.dtype == object                      # the int64 bound did not hold
+    dA = [[int(x) for x in sp.A.digits[p, 0]] for p in range(S)]
+    dB = [[int(x) for x in sp.B.digits[q, 0]] for q in range(S)]
+    big = 0
+    for t in range(D):
+        s = 0
+        for p in range(S):
+            q = t - p
+            if 0 <= q < S:
+                s += sum(a * b for a, b in zip(dA[p], dB[q]))
+        assert sp.s[t, 0, 0] == s
+        big = max(big, abs(s))
+    # and the whole method still reaches the rounded exact product
+    ex = exact.ExactProduct(A, B, [0], [0])
+    assert ex.error_ratio(sp.result()).max() <= 1.0
+
+
 @pytest.mark.parametrize("m,w", [(2, 8), (2, 7), (4, 8), (2, 20)])
 def test_all_pairs_full_coverage_equals_rounded_exact_product(m, w):
     """P3: keeping every pair with S covering every bit, the fused result is the
