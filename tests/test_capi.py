@@ -62,6 +62,47 @@ def test_plan_constraints(mw, m, mode):
                 assert S_min * K * 2 ** (2 * p.w - 2) <= 2 ** 53
 
 
+@pytest.mark.parametrize("m", [2, 4, 8])
+def test_dot_plan_constraints(mw, m):
+    """MW_DOT plans: 24-bit digits, S_A = S_B within the compiled range, the
+    same truncation budget as products, D <= S + 4, a thread's int64 sums
+    (ceil(K/256) products below 2^46) safe; too long or too wide is refused."""
+    lo, hi = {2: (4, 8), 4: (8, 12), 8: (17, 21)}[m]
+    for K in (1, 7, 700, 6144, 100000):
+        for ra, rb in ((0, 0), (16, 16), (40, 40), (3, 60)):
+            p = mw.mw_plan_gemm(m, "dot", 1, 1, K, ra, rb)
+            lgK = math.log2(K)
+            assert p.w == 24 and p.S_A == p.S_B and lo <= p.S_A <= hi
+            assert p.w * p.S_A >= 52 * m + max(ra, rb) + math.log2(m) + 5 - lgK - 1e-9
+            if p.D < 2 * p.S_A - 1:
+                assert p.w * p.D >= 52 * m + ra + rb + math.log2(p.S_A) + 6 - lgK - 1e-9
+            assert p.D <= p.S_A + 4
+            assert p.S_A * math.ceil(K / 256) * 2 ** 46 < 2 ** 63
+    with pytest.raises(mw.MWError):
+        mw.mw_plan_gemm(m, "dot", 1, 1, 10 ** 8, 0, 0)        # K too long for int64 sums
+    with pytest.raises(mw.MWError):
+        mw.mw_plan_gemm(m, "dot", 1, 1, 100, 300, 300)        # spreads need too many pieces
+    with pytest.raises(mw.MWError):
+        mw.mw_plan_gemm(m, "dot", 4, 1, 100, 0, 0)            # one inner product per plan
+
+
+@pytest.mark.parametrize("m,lo,hi", [(2, -6, 6), (4, -20, 20), (8, -3, 3)])
+def test_dot_planner_meets_bound_on_the_oracle(mw, m, lo, hi):
+    """The MW_DOT plan from the measured spreads keeps the oracle's summation
+    with 24-bit digits within the bound (one inner product of length 500)."""
+    from oracle import exact, slicing
+    from synthetic import SplitMix64, loguniform_mdouble
+    rng = SplitMix64(95 + m)
+    a = loguniform_mdouble(rng, m, 1, 500, lo, hi)
+    b = loguniform_mdouble(rng, m, 500, 1, lo, hi)
+    ra = int(slicing.row_exponents(a)[1].max())
+    rb = int(slicing.row_exponents(slicing.logical(b, True))[1].max())
+    p = mw.mw_plan_gemm(m, "dot", 1, 1, 500, ra, rb)
+    sp = slicing.SlicedProduct(a, b, p.w, p.S_A, p.S_B, p.D)
+    assert sp.A.in_range and sp.B.in_range
+    assert exact.exact_product_full(a, b).error_ratio(sp.result()).max() <= 1.0
+
+
 def test_host_side_errors(mw):
     with pytest.raises(mw.MWError):
         mw.mw_plan_gemm(3, "ozaki", 10, 10, 10, 0, 0)
