@@ -507,8 +507,11 @@ int combine_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const m
                uint8_t *w8, const Layout &L, cudaStream_t s) {
   const int bits = 64 + p.w * (p.D - 1) + 1;
   if (bits <= 256) launch_combine_b<MW, 4>(info, hdr, b, p, w8, L, s);
+  else if (bits <= 320) launch_combine_b<MW, 5>(info, hdr, b, p, w8, L, s);
   else if (bits <= 384) launch_combine_b<MW, 6>(info, hdr, b, p, w8, L, s);
+  else if (bits <= 448) launch_combine_b<MW, 7>(info, hdr, b, p, w8, L, s);
   else if (bits <= 512) launch_combine_b<MW, 8>(info, hdr, b, p, w8, L, s);
+  else if (bits <= 576) launch_combine_b<MW, 9>(info, hdr, b, p, w8, L, s);
   else if (bits <= 640) launch_combine_b<MW, 10>(info, hdr, b, p, w8, L, s);
   else return fail(MW_EUNSUPPORTED, "too many diagonals for the fusion");
   return cuda_fail(cudaGetLastError(), "batch combine launch");

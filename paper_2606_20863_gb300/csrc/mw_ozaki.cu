@@ -472,9 +472,13 @@ template <int MW>
 int launch_combine_nl(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
   // |X| < 2^(63 + w (D-1)) plus a sign bit
   const int bits = 64 + a.w * (a.D - 1) + 1;
+  // as few 64-bit limbs as hold the fused integer (the rounding walks every limb)
   if (bits <= 256) return launch_combine<MW, 4>(a, G, narrow, s);
+  if (bits <= 320) return launch_combine<MW, 5>(a, G, narrow, s);
   if (bits <= 384) return launch_combine<MW, 6>(a, G, narrow, s);
+  if (bits <= 448) return launch_combine<MW, 7>(a, G, narrow, s);
   if (bits <= 512) return launch_combine<MW, 8>(a, G, narrow, s);
+  if (bits <= 576) return launch_combine<MW, 9>(a, G, narrow, s);
   if (bits <= 640) return launch_combine<MW, 10>(a, G, narrow, s);
   return fail(MW_EUNSUPPORTED, "D = %d diagonals of %d bits too many for the fusion", a.D, a.w);
 }

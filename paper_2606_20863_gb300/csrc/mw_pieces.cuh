@@ -17,9 +17,28 @@ namespace {
 // T += A and T -= A on NL 64-bit limbs, one carry chain of add.cc/addc
 // (sub.cc/subc) instructions.
 template <int NL>
-__device__ __forceinline__ void add_limbs(uint64_t (&T)[NL], const uint64_t (&A)[NL]);
+__device__ __forceinline__ void add_limbs(uint64_t (&T)[NL], const uint64_t (&A)[NL]) {
+  uint64_t c = 0;   // the same arithmetic for other compilers
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const uint64_t s1 = T[i] + A[i], c1 = s1 < A[i];
+    const uint64_t s2 = s1 + c;
+    c = c1 | (s2 < c);
+    T[i] = s2;
+  }
+}
 template <int NL>
-__device__ __forceinline__ void sub_limbs(uint64_t (&T)[NL], const uint64_t (&A)[NL]);
+__device__ __forceinline__ void sub_limbs(uint64_t (&T)[NL], const uint64_t (&A)[NL]) {
+  uint64_t b = 0;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const uint64_t d1 = T[i] - A[i], b1 = T[i] < A[i];
+    const uint64_t d2 = d1 - b;
+    b = b1 | (d1 < b);
+    T[i] = d2;
+  }
+}
+#if defined(__CUDA_ARCH__)
 template <>
 __device__ __forceinline__ void add_limbs<2>(uint64_t (&T)[2], const uint64_t (&A)[2]) {
   asm("{\n"
@@ -150,6 +169,7 @@ __device__ __forceinline__ void sub_limbs<10>(uint64_t (&T)[10], const uint64_t 
       : "+l"(T[0]), "+l"(T[1]), "+l"(T[2]), "+l"(T[3]), "+l"(T[4]), "+l"(T[5]), "+l"(T[6]), "+l"(T[7]), "+l"(T[8]), "+l"(T[9])
       : "l"(A[0]), "l"(A[1]), "l"(A[2]), "l"(A[3]), "l"(A[4]), "l"(A[5]), "l"(A[6]), "l"(A[7]), "l"(A[8]), "l"(A[9]));
 }
+#endif
 
 // Fixed-point value of one entry in NL limbs (two's complement, little endian):
 // T = sum_j trunc(x_j 2^F), every word's truncated magnitude (a 53-bit integer
