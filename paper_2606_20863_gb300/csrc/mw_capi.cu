@@ -297,9 +297,31 @@ Operands ops_in(void *ws, int64_t M, int64_t N) {
   return o;
 }
 
+// A second stream per device: op(B) is cut there while op(A) is cut on the
+// caller's stream (the two splits share nothing); events fork and join the two,
+// which also holds inside a stream capture.
+cudaStream_t side_stream() {
+  static cudaStream_t st[kMaxDevices] = {nullptr};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_status_mu);
+  if (!st[dev] && cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking) != cudaSuccess)
+    st[dev] = nullptr;
+  return st[dev];
+}
+
 int split_both(const mw_plan &p, int transA, int transB, int64_t M, int64_t N, int64_t K,
                const double *A, int64_t lda, int64_t psa, const double *B, int64_t ldb,
                int64_t psb, void *ws, const Layout &L, bool exps_only, cudaStream_t s) {
+  cudaStream_t s2 = side_stream();
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool fork = s2 != nullptr &&
+              cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) == cudaSuccess;
+  if (fork) fork = cudaEventRecord(ev[0], s) == cudaSuccess &&
+                   cudaStreamWaitEvent(s2, ev[0], 0) == cudaSuccess;
+  if (!fork) s2 = s;
   Operands o = ops_in(ws, M, N);
   uint8_t *w8 = static_cast<uint8_t *>(ws);
   SplitArgs a{};
@@ -315,7 +337,15 @@ int split_both(const mw_plan &p, int transA, int transB, int64_t M, int64_t N, i
   a.trans = !transB; a.R = N; a.ld = ldb; a.plane_stride = psb; a.X = B; a.S = p.S_B;
   a.digits = w8 + L.digB; a.exps = o.eB; a.spread = o.spB; a.max_spread = o.maxsp + 1;
   a.range = p.range_B;
-  return launch_split(a, exps_only, s);
+  rc = launch_split(a, exps_only, s2);
+  if (fork) {
+    cudaError_t e = cudaEventRecord(ev[1], s2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+    if (e != cudaSuccess && !rc) rc = cuda_fail(e, "split join");
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);   // released once the recorded work is done
+  return rc;
 }
 
 int check_gemm_mats(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,

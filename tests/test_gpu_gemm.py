@@ -258,3 +258,32 @@ def test_ozaki_4096(mw, cuda, m):
     r2, c2 = [0, 4095], [7, 4000]
     sp = slicing.SlicedProduct(A, B, plan.w, plan.S_A, plan.S_B, plan.D, rows=r2, cols=c2)
     assert np.array_equal(C[:, r2][:, :, c2], sp.result())
+
+
+def test_gemm_replays_in_a_cuda_graph(mw, cuda):
+    """mw_gemm (its two operand splits forked onto a second stream and joined)
+    captured in a CUDA graph: replays give the eager words, and follow new
+    operand values at the same addresses."""
+    rng = SplitMix64(360)
+    A, B = uniform_mdouble(rng, 2, 300, 200), uniform_mdouble(rng, 2, 200, 270)
+    tA, tB = to_dev(A, cuda), to_dev(B, cuda)
+    plan = mw.plan_for(tA, tB, "ozaki")
+    ws = torch.empty(mw.workspace_size(plan, 300, 270, 200), dtype=torch.uint8, device=cuda)
+    C = torch.empty((2, 300, 270), dtype=torch.float64, device=cuda)
+    mw.mw_gemm(tA, tB, plan, C=C, ws=ws)
+    torch.cuda.synchronize()
+    expect = C.clone()
+    C.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            mw.mw_gemm(tA, tB, plan, C=C, ws=ws, check=False)
+    g.replay()
+    torch.cuda.synchronize()
+    mw.check_status()
+    assert torch.equal(C, expect)
+    tA.mul_(0.5)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(C, 0.5 * expect)
