@@ -134,3 +134,24 @@ def test_octo_double_batch_20000(mw, cuda):
         worst = max(worst, exact.ExactProduct(An, Bn, rows, cols).error_ratio(C).max())
     record_worst("20,000 od products, 200 sampled problems x 2 entries", worst)
     assert worst <= 1.0
+
+
+def test_batch_wide_partial_sums(mw, cuda):
+    """A batch whose longest K makes diagonal sums pass 2^31: 64-bit Horner
+    groups on 128 x 128 tiles, one B slice per MMA; every problem equals the
+    single product bit for bit, two entries the oracle."""
+    rng = SplitMix64(640)
+    shapes = [(20, 30, 9000), (5, 7, 100), (130, 9, 2500)]
+    As = [to_dev(uniform_mdouble(rng, 2, M, K), cuda) for M, N, K in shapes]
+    Bs = [to_dev(uniform_mdouble(rng, 2, K, N), cuda) for M, N, K in shapes]
+    batch = mw.Batch(As, Bs)
+    plan = batch.plan_
+    Kp = -(-9000 // 64) * 64
+    assert min(plan.S_A, plan.S_B) * Kp * 2 ** (2 * plan.w - 2) >= 2 ** 31   # wide
+    Cs = batch.run()
+    mw.check_status()
+    for A, B, C in zip(As, Bs, Cs):
+        assert torch.equal(C, mw.mw_gemm(A, B, plan))
+    An, Bn = As[0].cpu().numpy(), Bs[0].cpu().numpy()
+    sp = slicing.SlicedProduct(An, Bn, plan.w, plan.S_A, plan.S_B, plan.D, rows=[0, 19], cols=[29])
+    assert np.array_equal(Cs[0].cpu().numpy()[:, [0, 19]][:, :, [29]], sp.result())

@@ -109,3 +109,23 @@ def test_dot_rejects_bad_plans(mw, cuda):
     plan.S_A = plan.S_B = 40                          # not compiled
     with pytest.raises(mw.MWError):
         mw.mw_dot_batched(tA, tB, plan)
+
+
+def test_dot_status_bits(mw, cuda):
+    """Non-finite input raises MW_ENONFINITE, a spread beyond the plan's raises
+    the MW_WRANGE warning, a clean call raises nothing."""
+    mw.get_status(clear=True)
+    rng = SplitMix64(750)
+    A, B = operands("uniform", rng, 2, 3, 40)
+    tA, tB = to_dev(A, cuda), to_dev(B, cuda)
+    plan = mw.plan_dot(tA, tB)
+    mw.mw_dot_batched(tA, tB, plan, check=False)
+    assert mw.get_status(clear=True) == 0
+    A2 = A.copy()
+    A2[0, 1, 7] = np.nan
+    mw.mw_dot_batched(to_dev(A2, cuda), tB, plan, check=False)
+    assert mw.get_status(clear=True) & mw.MW_ENONFINITE
+    A3 = A.copy()
+    A3[:, 2, 5] *= 2.0 ** -40                       # spread of row 2 beyond the plan's
+    mw.mw_dot_batched(to_dev(A3, cuda), tB, plan, check=False)
+    assert mw.get_status(clear=True) & mw.MW_WRANGE
