@@ -49,6 +49,8 @@ def parse():
                     help="end-to-end runs from host memory (-1 = steps/4, at least 3; 0 = leave out)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows in the CPU sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="single products: launch each step directly instead of replaying a graph")
     ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8],
                     help="table2: words per m-double (2, 4 or 8)")
     ap.add_argument("--count", type=int, default=20000,
@@ -321,15 +323,33 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     pairs = count_pairs(plan)
 
-    def step():
+    def call():
         mw.mw_gemm(tA, tB, plan, C=C, ws=ws, check=False)
 
+    # one product call captured in a CUDA graph and replayed per step (the
+    # launches of the splits, product and fusion without host gaps)
+    call()
+    torch.cuda.synchronize()
+    mw.check_status()
+    graph = None
+    # short steps (1024^3) lose a few percent to launch gaps; at 4096^3 direct calls
+    # measured about 2 % faster than a replayed graph
+    if not args.no_graph and n <= 1024:
+        graph = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream()
+        with torch.cuda.stream(gs):
+            with torch.cuda.graph(graph, stream=gs):
+                call()
+    step = graph.replay if graph is not None else call
     for _ in range(args.warmup):
         step()
     mw.check_status()
     torch.cuda.synchronize()
-    step_ms, kern_ms, clk = timed(step, args.steps, flush, mw, dist, dev)
+    step_ms, _, clk = timed(step, args.steps, flush, mw, dist, dev, phase=False)
     value, t_step = aggregate(sum(step_ms) / 1e3, flops, args.steps, dist, dev)
+    # product-kernel time: phase events around direct calls (events are not
+    # recorded inside a graph), as many runs as timed steps
+    _, kern_ms, _ = timed(call, args.steps, flush, mw, None, dev)
 
     # plain FP64 form on the same operands and bound (the comparison of the metric)
     pplan = mw.plan_for(tA, tB, "plain")
@@ -384,6 +404,8 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
                        "form": "Ozaki: bf16 integer slices on tcgen05, fp32 drained to integers",
                        "plan": plan.as_dict(), "slice_pairs": pairs,
                        "l2": "flushed (256 MiB write) before every timed step",
+                       "launch": "direct calls" if graph is None else
+                                 "one mw_gemm call captured in a CUDA graph, replayed per step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "plain_fp64_gflops": plain_gflops, "plain_plan": pplan.as_dict(),
                        "speedup_vs_plain": (value / world / plain_gflops) if plain_gflops else None,
