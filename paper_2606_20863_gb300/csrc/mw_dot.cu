@@ -83,6 +83,19 @@ __device__ __forceinline__ void dot_digits(uint64_t (&T)[NL], int32_t (&d)[S],
   }
 }
 
+// 8-byte asynchronous copy global -> shared (completion by commit groups)
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // 128-bit (hi, lo) add
 __device__ __forceinline__ void add128(uint64_t &lo, int64_t &hi, uint64_t lo2, int64_t hi2) {
   const uint64_t s = lo + lo2;
@@ -115,6 +128,7 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
   __shared__ uint64_t red_lo[kDotThreads / 32][DC];
   __shared__ int64_t red_hi[kDotThreads / 32][DC];
   __shared__ int exps[2];
+  extern __shared__ double stage[];   // [2 buffers][2 MW words][kDotThreads]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int D = a.D;
   for (int64_t i = blockIdx.x; i < a.count; i += gridDim.x) {
@@ -164,12 +178,28 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
     int64_t s[DC];
 #pragma unroll
     for (int t = 0; t < DC; ++t) s[t] = 0;
-    for (int64_t k = tid; k < a.K; k += kDotThreads) {
+    // the words of the next entry are copied into this thread's shared slots
+    // while the current one is cut (each thread reads only what it copied)
+    auto slot = [&](int buf, int j) { return stage + ((buf * 2 * MW + j) * kDotThreads + tid); };
+    auto fetch = [&](int64_t k, int buf) {
+#pragma unroll
+      for (int j = 0; j < MW; ++j) {
+        cp_async8(slot(buf, j), pa + j * a.psa + k);
+        cp_async8(slot(buf, MW + j), pb + j * a.psb + k);
+      }
+    };
+    int buf = 0;
+    if (tid < a.K) fetch(tid, 0);
+    cp_async_commit();
+    for (int64_t k = tid; k < a.K; k += kDotThreads, buf ^= 1) {
+      if (k + kDotThreads < a.K) fetch(k + kDotThreads, buf ^ 1);
+      cp_async_commit();
+      cp_async_wait<1>();
       double xa[MW], xb[MW];
 #pragma unroll
       for (int j = 0; j < MW; ++j) {
-        xa[j] = pa[j * a.psa + k];
-        xb[j] = pb[j * a.psb + k];
+        xa[j] = *slot(buf, j);
+        xb[j] = *slot(buf, MW + j);
       }
       int32_t da[S], db[S];
       {
@@ -188,6 +218,7 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
         for (int q = 0; q < S; ++q)
           if (p + q < DC && p + q < D) s[p + q] += (int64_t)da[p] * (int64_t)db[q];
     }
+    cp_async_wait<0>();
     // block sums in 128 bits
 #pragma unroll
     for (int t = 0; t < DC; ++t) {
@@ -243,7 +274,15 @@ int launch_dot_s(const DotArgs &a, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::min<int64_t>(a.count, (int64_t)nsm * 8);
-  dot_kernel<MW, S, NL, NLF><<<grid, kDotThreads, 0, st>>>(a);
+  constexpr size_t smem = 2 * 2 * MW * kDotThreads * sizeof(double);
+  static bool attr_set = false;   // once per instance
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(dot_kernel<MW, S, NL, NLF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "dot kernel smem attribute");
+    attr_set = true;
+  }
+  dot_kernel<MW, S, NL, NLF><<<grid, kDotThreads, smem, st>>>(a);
   return cuda_fail(cudaGetLastError(), "dot kernel launch");
 }
 
