@@ -272,6 +272,13 @@ int mw_get_status(int *bits, int clear);
 /* Message for the last host-side error of the calling thread ("" if none). */
 const char *mw_last_error(void);
 
+/* Diagnostic with no counterpart in the paper: one CTA waits on a shared-memory
+ * barrier that nothing completes, with the bounded wait the pipeline kernels
+ * use but a limit of limit_us microseconds (1 .. 10^7); the wait gives up,
+ * raises MW_ETIMEOUT in the status word and the kernel returns, leaving the
+ * context usable.  Asynchronous on `stream`; read the bit with mw_get_status. */
+int mw_selftest_timeout(unsigned int limit_us, mw_stream_t stream);
+
 /* Library version string. */
 const char *mw_version(void);
 

@@ -89,6 +89,7 @@ def _load():
                                       ip, ip, vp],
         "mw_gemm_batched": [pp, ctypes.POINTER(mw_batch), vp, vp, ctypes.c_size_t, vp],
         "mw_dot_batched": [pp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, vp],
+        "mw_selftest_timeout": [ctypes.c_uint, vp],
         "mw_set_phase_events": [ctypes.POINTER(ctypes.c_void_p), i32],
     }
     for name, args in sig.items():
@@ -107,7 +108,7 @@ EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_works
             "mw_measure_spread", "mw_gemm_backward", "mw_get_status", "mw_last_error",
             "mw_version", "mw_set_phase_events", "mw_gemm_noalloc", "mw_batch_describe",
             "mw_gemm_batched_workspace_size", "mw_measure_spread_batched", "mw_gemm_batched",
-            "mw_dot_batched")
+            "mw_dot_batched", "mw_selftest_timeout")
 
 
 def _check(rc: int, what: str):
@@ -485,3 +486,11 @@ def mw_dot_batched(A: torch.Tensor, B: torch.Tensor, plan: mw_plan | None = None
     if check:
         check_status()
     return C
+
+
+def selftest_timeout(limit_us: int = 50000) -> int:
+    """Let one bounded wait run out on the GPU (a barrier nothing completes) and
+    return the status bits it left (MW_ETIMEOUT expected); synchronizes."""
+    get_status(clear=True)
+    _check(_lib.mw_selftest_timeout(limit_us, _stream()), "mw_selftest_timeout")
+    return get_status(clear=True)

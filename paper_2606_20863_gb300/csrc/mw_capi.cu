@@ -7,6 +7,7 @@
 #include <mutex>
 #include <string>
 
+#include "mw_device.cuh"
 #include "mw_internal.h"
 
 namespace mw {
@@ -135,9 +136,37 @@ int check_mat(const double *X, int64_t rows, int64_t cols, int64_t ld, int64_t p
 
 using namespace mw;
 
+namespace mw {
+namespace {
+
+// One CTA waits on a barrier that nothing completes: the bounded wait of the
+// pipeline kernels runs out after limit_ns, raises MW_ETIMEOUT and returns.
+__global__ void selftest_wait_kernel(uint64_t limit_ns, unsigned int *status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_for(&bar, 0, status, (volatile int *)&abort_flag, limit_ns);
+  __syncthreads();
+}
+
+}  // namespace
+}  // namespace mw
+
 extern "C" {
 
 const char *mw_last_error(void) { return g_msg.c_str(); }
+
+int mw_selftest_timeout(unsigned int limit_us, mw_stream_t stream) {
+  if (limit_us < 1 || limit_us > 10000000u) return fail(MW_EINVAL, "limit must be 1 us .. 10 s");
+  selftest_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)limit_us * 1000ull,
+                                                           status_ptr());
+  return cuda_fail(cudaGetLastError(), "self-test launch");
+}
 
 const char *mw_version(void) { return "mw 0.1 (sm_103a, tcgen05 bf16 slices, fp64 pieces)"; }
 

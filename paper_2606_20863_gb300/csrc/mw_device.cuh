@@ -72,23 +72,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Wait until the phase of `bar` with parity `parity` has completed.  Returns
-// false (after raising MW_ETIMEOUT) if that takes longer than the limit or if
+// false (after raising MW_ETIMEOUT) if that takes longer than limit_ns or if
 // *abort became nonzero meanwhile.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned int *status,
-                                          volatile int *abort) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity,
+                                              unsigned int *status, volatile int *abort,
+                                              uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t spin = 1;; ++spin) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((spin & 255u) == 0) {
       if (*abort) return false;
-      if (global_ns() - t0 > kWaitLimitNs) {
+      if (global_ns() - t0 > limit_ns) {
         raise_status(status, MW_ETIMEOUT);
         *abort = 1;
         return false;
       }
     }
   }
+}
+
+// The pipeline kernels' wait: limit kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned int *status,
+                                          volatile int *abort) {
+  return mbar_wait_for(bar, parity, status, abort, kWaitLimitNs);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
