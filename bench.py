@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-graph", action="store_true",
                     help="single products: launch each step directly instead of replaying a graph")
-    ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8],
-                    help="table2: words per m-double (2, 4 or 8)")
+    ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8, 16],
+                    help="table2: words per m-double (2, 4, 8 or 16)")
     ap.add_argument("--count", type=int, default=20000,
                     help="od_batch: number of products (20,000 is the benchmark; fewer for profiling)")
     ap.add_argument("--workload", default="qd1024",
@@ -620,7 +620,8 @@ def run_adjoint(args, mw, torch, dist, rank, world, dev):
 
 # Table 2 of the paper: 1,024 inner products of length 6,144 on the Section 2 bit
 # pattern, one thread of a Xeon 5318Y (milliseconds: ordinary, vectorized).
-PAPER_TABLE2_MS = {2: (158.0, 69.0), 4: (1977.0, 318.0), 8: (6428.0, 1520.0)}
+PAPER_TABLE2_MS = {2: (158.0, 69.0), 4: (1977.0, 318.0), 8: (6428.0, 1520.0),
+                   16: (40780.0, 9491.0)}
 # integer multiply-adds d_a d_b -> int64 per clock and SM assumed for the
 # inner-product kernel's roofline (half the 128 int32 lanes of an SM)
 IMAD_WIDE_PER_CLK_SM = 64

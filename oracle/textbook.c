@@ -25,8 +25,8 @@
 #include <stdint.h>
 #include <string.h>
 
-#define MAXM 8
-#define MAXT 160
+#define MAXM 16
+#define MAXT 320
 
 static inline double two_sum(double a, double b, double *e) {
   double s = a + b;

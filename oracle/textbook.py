@@ -66,7 +66,7 @@ class TextbookC:
         B = np.ascontiguousarray(B, dtype=np.float64)
         m, M, K = A.shape
         _, K2, N = B.shape
-        assert K == K2 and B.shape[0] == m and m in (2, 4, 8)
+        assert K == K2 and B.shape[0] == m and m in (2, 4, 8, 16)
         C = np.zeros((m, M, N))
         r = np.arange(M, dtype=np.int64) if rows is None else np.asarray(rows, dtype=np.int64)
         self.lib.tb_gemm_rows(m, M, N, K, self._p(A), self._p(B), self._p(C),

@@ -416,7 +416,7 @@ int grid_for(int per_sm) {
 int check_batch(const mw_plan *p, const mw_batch *b) {
   if (!p || !b) return fail(MW_EINVAL, "plan/batch is NULL");
   if (p->mode != MW_OZAKI) return fail(MW_EUNSUPPORTED, "batches run in the Ozaki form");
-  if (p->m != 2 && p->m != 4 && p->m != 8) return fail(MW_EINVAL, "m must be 2, 4 or 8");
+  if (p->m != 2 && p->m != 4 && p->m != 8) return fail(MW_EINVAL, "batches take m = 2, 4 or 8");
   if (b->count < 1 || b->sum_M < 1 || b->sum_N < 1 || b->max_K < 1)
     return fail(MW_EINVAL, "empty batch");
   if (p->w < 2 || p->w > 8 || (int64_t)p->chunk << (2 * p->w - 2) > (1 << 22) || p->chunk % 64)

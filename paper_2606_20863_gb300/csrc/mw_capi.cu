@@ -59,7 +59,8 @@ unsigned int *status_ptr() {
 
 namespace {
 
-bool valid_m(int m) { return m == 2 || m == 4 || m == 8; }
+// m = 16 (hexa doubles) runs the tensor-core form and inner products only
+bool valid_m(int m) { return m == 2 || m == 4 || m == 8 || m == 16; }
 
 int ceil_div_bits(double bits, int w) {
   const int n = (int)std::ceil(bits / w - 1e-9);
@@ -100,7 +101,7 @@ Layout layout(const mw_plan &p, int64_t M, int64_t N, int64_t K) {
 
 int check_plan(const mw_plan *p, int64_t M, int64_t N, int64_t K) {
   if (!p) return fail(MW_EINVAL, "plan is NULL");
-  if (!valid_m(p->m)) return fail(MW_EINVAL, "m = %d, must be 2, 4 or 8", p->m);
+  if (!valid_m(p->m)) return fail(MW_EINVAL, "m = %d, must be 2, 4, 8 or 16", p->m);
   if (M <= 0 || N <= 0 || K <= 0) return fail(MW_EINVAL, "dimensions must be positive");
   if (p->S_A < 1 || p->S_B < 1 || p->D < 1) return fail(MW_EINVAL, "S_A, S_B, D must be >= 1");
   if (p->mode == MW_OZAKI) {
@@ -111,6 +112,7 @@ int check_plan(const mw_plan *p, int64_t M, int64_t N, int64_t K) {
     if (gmax < 1 || p->group > gmax)
       return fail(MW_EINVAL, "group %d exceeds the int64 limit %d", p->group, gmax);
   } else if (p->mode == MW_PLAIN) {
+    if (p->m == 16) return fail(MW_EUNSUPPORTED, "m = 16 runs in the MW_OZAKI form only");
     if (p->w < 1 || p->w > 26) return fail(MW_EINVAL, "plain piece width w must be 1..26");
     const int S_min = p->S_A < p->S_B ? p->S_A : p->S_B;
     const double bits = std::log2((double)S_min * (double)K) + 2.0 * p->w - 2.0;
@@ -199,7 +201,7 @@ int mw_get_status(int *bits, int clear) {
 int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, int range_B,
                  mw_plan *plan) {
   if (!plan) return fail(MW_EINVAL, "plan is NULL");
-  if (!valid_m(m)) return fail(MW_EINVAL, "m = %d, must be 2, 4 or 8", m);
+  if (!valid_m(m)) return fail(MW_EINVAL, "m = %d, must be 2, 4, 8 or 16", m);
   if (M <= 0 || N <= 0 || K <= 0) return fail(MW_EINVAL, "dimensions must be positive");
   if (range_A < 0 || range_B < 0) return fail(MW_EINVAL, "ranges must be >= 0");
   const int want_w = plan->w;
@@ -232,6 +234,7 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
     p.group = group_size(S_min, K, p.w);
     if (p.group < 1) return fail(MW_EUNSUPPORTED, "K = %lld too long for 64-bit partial sums", (long long)K);
   } else if (mode == MW_PLAIN) {
+    if (m == 16) return fail(MW_EUNSUPPORTED, "m = 16 runs in the MW_OZAKI form only");
     if (want_w != 0 && (want_w < 4 || want_w > 26)) return fail(MW_EINVAL, "plain w must be 4..26");
     int w = want_w ? want_w : 26;
     for (; w >= 4; --w) {
@@ -269,7 +272,7 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
 int mw_split(int m, int trans, int64_t R, int64_t K, const double *X, int64_t ld,
              int64_t plane_stride, int w, int S, int format, void *digits, int64_t digit_ld,
              int32_t *exps, int32_t *spread, int32_t *max_spread, int range, mw_stream_t stream) {
-  if (!valid_m(m)) return fail(MW_EINVAL, "m = %d, must be 2, 4 or 8", m);
+  if (!valid_m(m)) return fail(MW_EINVAL, "m = %d, must be 2, 4, 8 or 16", m);
   if (R <= 0 || K <= 0) return fail(MW_EINVAL, "dimensions must be positive");
   int rc = trans ? check_mat(X, K, R, ld, plane_stride, m, "X") : check_mat(X, R, K, ld, plane_stride, m, "X");
   if (rc) return rc;
@@ -434,7 +437,7 @@ int mw_measure_spread(int m, int transA, int transB, int64_t M, int64_t N, int64
                       const double *A, int64_t lda, int64_t psa, const double *B, int64_t ldb,
                       int64_t psb, void *ws, size_t ws_bytes, int *range_A, int *range_B,
                       mw_stream_t stream) {
-  if (!valid_m(m)) return fail(MW_EINVAL, "m = %d, must be 2, 4 or 8", m);
+  if (!valid_m(m)) return fail(MW_EINVAL, "m = %d, must be 2, 4, 8 or 16", m);
   if (M <= 0 || N <= 0 || K <= 0) return fail(MW_EINVAL, "dimensions must be positive");
   if (!range_A || !range_B) return fail(MW_EINVAL, "range outputs are NULL");
   int rc = check_gemm_mats(m, transA, transB, M, N, K, A, lda, psa, B, ldb, psb);

@@ -264,6 +264,7 @@ template <int MW> struct DotS;
 template <> struct DotS<2> { static constexpr int lo = 4, hi = 8; };
 template <> struct DotS<4> { static constexpr int lo = 8, hi = 12; };
 template <> struct DotS<8> { static constexpr int lo = 17, hi = 21; };
+template <> struct DotS<16> { static constexpr int lo = 35, hi = 36; };
 
 template <int MW, int S>
 int launch_dot_s(const DotArgs &a, cudaStream_t st) {
@@ -304,7 +305,8 @@ int dot_pieces_range(int m, int *lo, int *hi) {
     case 2: *lo = DotS<2>::lo; *hi = DotS<2>::hi; return MW_OK;
     case 4: *lo = DotS<4>::lo; *hi = DotS<4>::hi; return MW_OK;
     case 8: *lo = DotS<8>::lo; *hi = DotS<8>::hi; return MW_OK;
-    default: return fail(MW_EINVAL, "m = %d, must be 2, 4 or 8", m);
+    case 16: *lo = DotS<16>::lo; *hi = DotS<16>::hi; return MW_OK;
+    default: return fail(MW_EINVAL, "m = %d, must be 2, 4, 8 or 16", m);
   }
 }
 
@@ -320,7 +322,8 @@ int mw_dot_batched(const mw_plan *plan, int64_t count, int64_t K, const double *
   if (!plan) return fail(MW_EINVAL, "plan is NULL");
   const mw_plan &p = *plan;
   if (p.mode != MW_DOT) return fail(MW_EINVAL, "plan mode must be MW_DOT");
-  if (p.m != 2 && p.m != 4 && p.m != 8) return fail(MW_EINVAL, "m must be 2, 4 or 8");
+  if (p.m != 2 && p.m != 4 && p.m != 8 && p.m != 16)
+    return fail(MW_EINVAL, "m must be 2, 4, 8 or 16");
   if (count < 1 || K < 1) return fail(MW_EINVAL, "count and K must be positive");
   if (!A || !B || !C) return fail(MW_EINVAL, "NULL operand");
   if (lda < K || ldb < K) return fail(MW_EINVAL, "lda and ldb must be >= K");
@@ -341,7 +344,8 @@ int mw_dot_batched(const mw_plan *plan, int64_t count, int64_t K, const double *
   switch (p.m) {
     case 2: return launch_dot_range<2, DotS<2>::lo>(a, p.S_A, st);
     case 4: return launch_dot_range<4, DotS<4>::lo>(a, p.S_A, st);
-    default: return launch_dot_range<8, DotS<8>::lo>(a, p.S_A, st);
+    case 8: return launch_dot_range<8, DotS<8>::lo>(a, p.S_A, st);
+    default: return launch_dot_range<16, DotS<16>::lo>(a, p.S_A, st);
   }
 }
 

@@ -470,16 +470,25 @@ int launch_combine(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
 
 template <int MW>
 int launch_combine_nl(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
-  // |X| < 2^(63 + w (D-1)) plus a sign bit
+  // |X| < 2^(63 + w (D-1)) plus a sign bit; as few 64-bit limbs as hold it (the
+  // rounding walks every limb)
   const int bits = 64 + a.w * (a.D - 1) + 1;
-  // as few 64-bit limbs as hold the fused integer (the rounding walks every limb)
-  if (bits <= 256) return launch_combine<MW, 4>(a, G, narrow, s);
-  if (bits <= 320) return launch_combine<MW, 5>(a, G, narrow, s);
-  if (bits <= 384) return launch_combine<MW, 6>(a, G, narrow, s);
-  if (bits <= 448) return launch_combine<MW, 7>(a, G, narrow, s);
-  if (bits <= 512) return launch_combine<MW, 8>(a, G, narrow, s);
-  if (bits <= 576) return launch_combine<MW, 9>(a, G, narrow, s);
-  if (bits <= 640) return launch_combine<MW, 10>(a, G, narrow, s);
+  if constexpr (MW == 16) {
+    if (bits <= 768) return launch_combine<MW, 12>(a, G, narrow, s);
+    if (bits <= 832) return launch_combine<MW, 13>(a, G, narrow, s);
+    if (bits <= 896) return launch_combine<MW, 14>(a, G, narrow, s);
+    if (bits <= 960) return launch_combine<MW, 15>(a, G, narrow, s);
+    if (bits <= 1024) return launch_combine<MW, 16>(a, G, narrow, s);
+    if (bits <= 1088) return launch_combine<MW, 17>(a, G, narrow, s);
+  } else {
+    if (bits <= 256) return launch_combine<MW, 4>(a, G, narrow, s);
+    if (bits <= 320) return launch_combine<MW, 5>(a, G, narrow, s);
+    if (bits <= 384) return launch_combine<MW, 6>(a, G, narrow, s);
+    if (bits <= 448) return launch_combine<MW, 7>(a, G, narrow, s);
+    if (bits <= 512) return launch_combine<MW, 8>(a, G, narrow, s);
+    if (bits <= 576) return launch_combine<MW, 9>(a, G, narrow, s);
+    if (bits <= 640) return launch_combine<MW, 10>(a, G, narrow, s);
+  }
   return fail(MW_EUNSUPPORTED, "D = %d diagonals of %d bits too many for the fusion", a.D, a.w);
 }
 
@@ -642,6 +651,7 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
     case 2: return launch_combine_nl<2>(a, G, narrow, s);
     case 4: return launch_combine_nl<4>(a, G, narrow, s);
     case 8: return launch_combine_nl<8>(a, G, narrow, s);
+    case 16: return launch_combine_nl<16>(a, G, narrow, s);
   }
   return fail(MW_EINVAL, "m must be 2, 4 or 8");
 }

@@ -15,6 +15,7 @@
 //   end with a carry, written as bfloat16 or double.
 #include <cuda_bf16.h>
 #include <cstdio>
+#include <type_traits>
 
 #include "mw_device.cuh"
 #include "mw_pieces.cuh"
@@ -223,8 +224,19 @@ int launch_pieces_m(const SplitArgs &a, cudaStream_t s) {
     case 2: return launch_pieces_nl<2, Out>(a, s);
     case 4: return launch_pieces_nl<4, Out>(a, s);
     case 8: return launch_pieces_nl<8, Out>(a, s);
+    case 16:
+      // hexa doubles: bfloat16 pieces (MW_OZAKI) only
+      if constexpr (std::is_same<Out, __nv_bfloat16>::value) {
+        const int bits = a.w * a.S + 3;
+        if (bits <= 768) return launch_pieces<16, Out, 12>(a, s);
+        if (bits <= 896) return launch_pieces<16, Out, 14>(a, s);
+        if (bits <= 1024) return launch_pieces<16, Out, 16>(a, s);
+        return fail(MW_EUNSUPPORTED, "w*S = %d too large (at most 1021 bits)", a.w * a.S);
+      } else {
+        return fail(MW_EUNSUPPORTED, "m = 16 is cut into bfloat16 pieces only");
+      }
   }
-  return fail(MW_EINVAL, "m must be 2, 4 or 8");
+  return fail(MW_EINVAL, "m must be 2, 4, 8 or 16");
 }
 
 }  // namespace

@@ -41,8 +41,8 @@ def test_version(mw):
     assert "sm_103a" in mw.version()
 
 
-@pytest.mark.parametrize("m", [2, 4, 8])
-@pytest.mark.parametrize("mode", ["ozaki", "plain"])
+@pytest.mark.parametrize("m,mode", [(2, "ozaki"), (4, "ozaki"), (8, "ozaki"), (16, "ozaki"),
+                                    (2, "plain"), (4, "plain"), (8, "plain")])
 def test_plan_constraints(mw, m, mode):
     for K in (1, 7, 64, 1024, 4096, 65536):
         for ra, rb in ((0, 0), (16, 16), (40, 40), (3, 60)):
@@ -62,14 +62,15 @@ def test_plan_constraints(mw, m, mode):
                 assert S_min * K * 2 ** (2 * p.w - 2) <= 2 ** 53
 
 
-@pytest.mark.parametrize("m", [2, 4, 8])
+@pytest.mark.parametrize("m", [2, 4, 8, 16])
 def test_dot_plan_constraints(mw, m):
     """MW_DOT plans: 24-bit digits, S_A = S_B within the compiled range, the
     same truncation budget as products, D <= S + 4, a thread's int64 sums
     (ceil(K/256) products below 2^46) safe; too long or too wide is refused."""
-    lo, hi = {2: (4, 8), 4: (8, 12), 8: (17, 21)}[m]
+    lo, hi = {2: (4, 8), 4: (8, 12), 8: (17, 21), 16: (35, 36)}[m]
+    spreads = ((0, 0), (16, 16)) if m == 16 else ((0, 0), (16, 16), (40, 40), (3, 60))
     for K in (1, 7, 700, 6144, 100000):
-        for ra, rb in ((0, 0), (16, 16), (40, 40), (3, 60)):
+        for ra, rb in spreads:
             p = mw.mw_plan_gemm(m, "dot", 1, 1, K, ra, rb)
             lgK = math.log2(K)
             assert p.w == 24 and p.S_A == p.S_B and lo <= p.S_A <= hi
@@ -101,6 +102,14 @@ def test_dot_planner_meets_bound_on_the_oracle(mw, m, lo, hi):
     sp = slicing.SlicedProduct(a, b, p.w, p.S_A, p.S_B, p.D)
     assert sp.A.in_range and sp.B.in_range
     assert exact.exact_product_full(a, b).error_ratio(sp.result()).max() <= 1.0
+
+
+def test_hexa_double_forms(mw):
+    """m = 16 plans in the tensor-core form and for inner products, not in the
+    FP64 form."""
+    assert mw.mw_plan_gemm(16, "ozaki", 100, 100, 1024, 0, 0).S_A >= 104
+    with pytest.raises(mw.MWError):
+        mw.mw_plan_gemm(16, "plain", 100, 100, 1024, 0, 0)
 
 
 def test_host_side_errors(mw):

@@ -55,6 +55,14 @@ def test_dot_bit_exact(mw, cuda, m, count, K, kind):
     check_dots(mw, cuda, A, B)
 
 
+@pytest.mark.parametrize("count,K,kind", [(4, 1, "uniform"), (3, 40, "pattern"), (2, 700, "pattern")])
+def test_dot_hexa_double(mw, cuda, count, K, kind):
+    """m = 16 inner products (35 or 36 digits of 24 bits a term)."""
+    rng = SplitMix64(760 + K)
+    A, B = operands(kind, rng, 16, count, K)
+    check_dots(mw, cuda, A, B)
+
+
 def test_dot_edge_cases(mw, cuda):
     """Zero vectors, one nonzero entry, exact cancellation, a tie."""
     m, K = 4, 5
@@ -88,7 +96,7 @@ def test_dot_strided_rows(mw, cuda):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("m", [2, 4, 8])
+@pytest.mark.parametrize("m", [2, 4, 8, 16])
 def test_table2_workload(mw, cuda, m):
     """1,024 inner products of length 6,144 on the Section 2 bit pattern
     (Table 2's workload), 16 sampled products against the oracle."""

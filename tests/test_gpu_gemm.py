@@ -93,6 +93,8 @@ def check_ozaki(mw, cuda, A, B, plan, transA=False, transB=False, rows=None, col
     (4, 129, 257, 65, -20, 20),
     (2, 300, 520, 100, -6, 6),      # odd number of tile rows: the last CTA pair has an empty tile
     (2, 520, 1000, 64, None, None),
+    (16, 20, 24, 30, None, None),   # hexa doubles (Table 2's 16d precision)
+    (16, 130, 70, 100, -3, 3),
 ])
 def test_ozaki_bit_exact(mw, cuda, m, M, N, K, lo, hi):
     rng = SplitMix64(300 + m + M)

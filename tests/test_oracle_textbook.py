@@ -60,7 +60,7 @@ def test_table2_speedup_column():
         assert round(int(ordinary) / int(vectorized), 1) == float(speedup)
 
 
-@pytest.mark.parametrize("m", [2, 4, 8])
+@pytest.mark.parametrize("m", [2, 4, 8, 16])
 def test_c_and_python_agree_bitwise(tc, m):
     rng = SplitMix64(61 + m)
     A = loguniform_mdouble(rng, m, 5, 6, -10, 10)
@@ -87,6 +87,19 @@ def test_textbook_within_bound(tc, m, gen):
     C = tc.gemm(A, B)
     ex = exact.exact_product_full(A, B)
     assert ex.error_ratio(C).max() <= 1.0
+
+
+@pytest.mark.parametrize("gen", ["uniform", "pattern"])
+def test_textbook_hexa_double_within_bound(tc, gen):
+    """m = 16 (Table 2's 16d column) through the same generic renormalisation."""
+    rng = SplitMix64(86)
+    n = 6
+    if gen == "uniform":
+        A, B = uniform_mdouble(rng, 16, n, n), uniform_mdouble(rng, 16, n, n)
+    else:
+        A, B = paper_pattern_mdouble(rng, 16, n, n), paper_pattern_mdouble(rng, 16, n, n)
+    ex = exact.exact_product_full(A, B)
+    assert ex.error_ratio(tc.gemm(A, B)).max() <= 1.0
 
 
 def test_single_products_are_accurate():
