@@ -2,7 +2,9 @@
  *
  * An m-double is an unevaluated sum of m nonoverlapping doubles (Section 1 of
  * J. Verschelde, "Multiword Arithmetic and Parallel Computing"); m is 2
- * (double double), 4 (quad double) or 8 (octo double).  A matrix of
+ * (double double), 4 (quad double), 8 (octo double) or 16 (hexa double,
+ * Table 2's 16d precision; MW_OZAKI single products and mw_dot_batched only,
+ * not MW_PLAIN nor batches).  A matrix of
  * m-doubles is stored as m planes of doubles ("structure of arrays", the
  * register-friendly layout the abstract argues for): entry (r, c) of word
  * plane j is at  base[j * plane_stride + r * ld + c]  (row major, ld >= cols,
@@ -57,7 +59,8 @@ typedef struct CUstream_st *mw_stream_t; /* same type as cudaStream_t */
 /* return codes (host) and status bits (device, see mw_get_status) */
 enum {
   MW_OK = 0,
-  MW_EINVAL = 1,      /* bad argument: m not in {2,4,8}, dims <= 0, ld too small, NULL */
+  MW_EINVAL = 1,      /* bad argument: m not in {2,4,8,16} (or 16 where the form takes
+                         only {2,4,8}), dims <= 0, ld too small, NULL */
   MW_ERANGE = 2,      /* status bit: fixed-point value outside [-2^(wS-1), 2^(wS-1)) (input not normalised) */
   MW_ENONFINITE = 4,  /* status bit: an input word is inf or nan */
   MW_ECUDA = 8,       /* a CUDA call failed */
@@ -97,9 +100,10 @@ typedef struct mw_plan {
  * 4..26 for MW_PLAIN, 24 for MW_DOT) is used as given.  Zero the struct before
  * the call.  MW_DOT plans one inner product of length K (M = N = 1) with
  * S_A = S_B = the smallest compiled piece count that covers the analysis
- * (2: 4..8, 4: 8..12, 8: 17..21) and D <= S + 4.
+ * (2: 4..8, 4: 8..12, 8: 17..21, 16: 35..36) and D <= S + 4.
  * Returns MW_EINVAL for bad arguments, MW_EUNSUPPORTED if no plan fits the
- * exactness thresholds (e.g. K too long for MW_PLAIN). */
+ * exactness thresholds (e.g. K too long for MW_PLAIN) or for m = 16 with
+ * MW_PLAIN. */
 int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, int range_B,
                  mw_plan *plan);
 

@@ -112,7 +112,7 @@ int check_plan(const mw_plan *p, int64_t M, int64_t N, int64_t K) {
     if (gmax < 1 || p->group > gmax)
       return fail(MW_EINVAL, "group %d exceeds the int64 limit %d", p->group, gmax);
   } else if (p->mode == MW_PLAIN) {
-    if (p->m == 16) return fail(MW_EUNSUPPORTED, "m = 16 runs in the MW_OZAKI form only");
+    if (p->m == 16) return fail(MW_EUNSUPPORTED, "m = 16 has no MW_PLAIN form (MW_OZAKI and MW_DOT take it)");
     if (p->w < 1 || p->w > 26) return fail(MW_EINVAL, "plain piece width w must be 1..26");
     const int S_min = p->S_A < p->S_B ? p->S_A : p->S_B;
     const double bits = std::log2((double)S_min * (double)K) + 2.0 * p->w - 2.0;
@@ -234,7 +234,7 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
     p.group = group_size(S_min, K, p.w);
     if (p.group < 1) return fail(MW_EUNSUPPORTED, "K = %lld too long for 64-bit partial sums", (long long)K);
   } else if (mode == MW_PLAIN) {
-    if (m == 16) return fail(MW_EUNSUPPORTED, "m = 16 runs in the MW_OZAKI form only");
+    if (m == 16) return fail(MW_EUNSUPPORTED, "m = 16 has no MW_PLAIN form (MW_OZAKI and MW_DOT take it)");
     if (want_w != 0 && (want_w < 4 || want_w > 26)) return fail(MW_EINVAL, "plain w must be 4..26");
     int w = want_w ? want_w : 26;
     for (; w >= 4; --w) {
