@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "mw_device.cuh"
+#include "mw_column.cuh"
 #include "mw_fuse.cuh"
 #include "mw_pieces.cuh"
 #include "mw_work.cuh"
@@ -204,6 +205,11 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
     __nv_bfloat16 *pieceA, int32_t *eA, int32_t *spA, int32_t *max_spread, int range,
     int exps_only, unsigned int *status) {
   if (hdr->bad) return;
+  // m >= 8, w = 8: each word adds its fields into this thread's column of slots
+  // (cut_column) instead of a carry chain over every limb
+  constexpr bool kColumn = W8 && MW >= 8;
+  constexpr int kSlots = kColumn ? (64 * NL - 8) / 24 + 4 : 1;   // S <= 8 NL
+  __shared__ uint32_t slots[kSlots][256];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -251,10 +257,16 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
       double x[MW];
 #pragma unroll
       for (int j = 0; j < MW; ++j) x[j] = base[j * b.psa + k];
-      if constexpr (W8)
+      if constexpr (kColumn) {
+        __nv_bfloat16 *q = dst + k + (int64_t)(S - 1) * plane;
+        if (!cut_column<MW, 8>(x, F, S, &slots[0][threadIdx.x], 256,
+                               [&](int kk, int32_t d) { q[-kk * plane] = to_out<__nv_bfloat16>(d); }))
+          raise_status(status, MW_ERANGE);
+      } else if constexpr (W8) {
         cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst + k, plane, status);
-      else
+      } else {
         cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst + k, plane, status);
+      }
     }
   }
 }
@@ -268,8 +280,11 @@ __global__ void __launch_bounds__(256, 3) batch_split_cols_kernel(
     const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
     __nv_bfloat16 *pieceB, int32_t *eB, int32_t *spB, int32_t *max_spread, int range,
     int exps_only, unsigned int *status) {
-  extern __shared__ double tile[];              // [MW][32 k][33]
+  extern __shared__ double tile[];              // [MW][32 k][33], then for the column
+                                                // cut the threads' slots
   __shared__ int smax[8][32], smin[8][32], sE[32];
+  constexpr bool kColumn = W8 && MW >= 8;     // as in the row kernel
+  uint32_t *slots = reinterpret_cast<uint32_t *>(tile + MW * 32 * 33) + threadIdx.x;
   if (hdr->bad) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int64_t task = blockIdx.x; task < hdr->sum_stripes; task += gridDim.x) {
@@ -344,10 +359,16 @@ __global__ void __launch_bounds__(256, 3) batch_split_cols_kernel(
 #pragma unroll
           for (int q = 0; q < MW; ++q) x[q] = tile[(q * 32 + kl) * 33 + jl];
           const int F = w * S - 2 - sE[jl];
-          if constexpr (W8)
+          if constexpr (kColumn) {
+            __nv_bfloat16 *q = dst + (int64_t)(S - 1) * plane;
+            if (!cut_column<MW, 8>(x, F, S, slots, 256,
+                                   [&](int kk, int32_t d) { q[-kk * plane] = to_out<__nv_bfloat16>(d); }))
+              raise_status(status, MW_ERANGE);
+          } else if constexpr (W8) {
             cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst, plane, status);
-          else
+          } else {
             cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst, plane, status);
+          }
         }
         __syncthreads();
       }
@@ -367,6 +388,7 @@ __global__ void __launch_bounds__(256, 3) batch_combine_kernel(const BInfo *info
                                                             int G, int group, int D, int w) {
   if (hdr->bad) return;
   __shared__ int first;
+  __shared__ uint32_t limbs[2 * NL][256];          // this thread's column: limbs[*][threadIdx.x]
   const int64_t total = hdr->sum_MN;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total;
        base += (int64_t)gridDim.x * blockDim.x) {
@@ -401,8 +423,9 @@ __global__ void __launch_bounds__(256, 3) batch_combine_kernel(const BInfo *info
     }
     double *c = b.C + r * b.ldc + j;
     const int64_t psc = b.psc;
-    round_words32<MW, 2 * NL>(U, eA[b.eA + r] + eB[b.eB + j] + 4 - w * (D + 1),
-                              [&](int k, double v) { c[k * psc] = v; });
+    round_column<MW, 2 * NL>(U, &limbs[0][threadIdx.x], 256,
+                             eA[b.eA + r] + eB[b.eB + j] + 4 - w * (D + 1),
+                             [&](int k, double v) { c[k * psc] = v; });
   }
 }
 
@@ -440,7 +463,9 @@ int launch_split_w(const BInfo *info, const BHeader *hdr, const mw_batch &b, con
       info, hdr, b.count, p.w, p.S_A, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceA),
       reinterpret_cast<int32_t *>(w8 + L.eA), reinterpret_cast<int32_t *>(w8 + L.spA),
       h->max_spread, p.range_A, exps_only, status_ptr());
-  const size_t sm = (size_t)MW * 32 * 33 * sizeof(double);
+  // the tile, then (w = 8, m >= 8) 256 columns of (64 NL - 8) / 24 + 4 slots
+  const size_t sm = (size_t)MW * 32 * 33 * sizeof(double) +
+                    (W8 && MW >= 8 ? (size_t)((64 * NL - 8) / 24 + 4) * 256 * sizeof(uint32_t) : 0);
   static bool attr_set = false;  // once per instantiation
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(batch_split_cols_kernel<MW, NL, W8>,

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 
+#include "mw_column.cuh"
 #include "mw_device.cuh"
 #include "mw_fuse.cuh"
 #include "mw_internal.h"
@@ -128,7 +129,13 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
   __shared__ uint64_t red_lo[kDotThreads / 32][DC];
   __shared__ int64_t red_hi[kDotThreads / 32][DC];
   __shared__ int exps[2];
-  extern __shared__ double stage[];   // [2 buffers][2 MW words][kDotThreads]
+  __shared__ uint32_t rcol[2 * NLF];   // the fusing thread's limbs
+  extern __shared__ double stage[];   // [2 buffers][2 MW words][kDotThreads], then for
+                                      // m >= 8 the threads' digit columns
+  // m >= 8: each word adds its fields into this thread's column of slots
+  // (cut_column) instead of a carry chain over every limb
+  constexpr bool kColumn = MW >= 8;
+  uint32_t *dcol = reinterpret_cast<uint32_t *>(stage + 2 * 2 * MW * kDotThreads) + threadIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int D = a.D;
   for (int64_t i = blockIdx.x; i < a.count; i += gridDim.x) {
@@ -202,15 +209,23 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
         xb[j] = *slot(buf, MW + j);
       }
       int32_t da[S], db[S];
-      {
-        uint64_t T[NL];
-        fixed_point<MW, NL>(xa, Fa, T);
-        dot_digits<S, NL>(T, da, a.status);
-      }
-      {
-        uint64_t T[NL];
-        fixed_point<MW, NL>(xb, Fb, T);
-        dot_digits<S, NL>(T, db, a.status);
+      if constexpr (kColumn) {
+        bool ok = cut_column<MW, kDotW>(xa, Fa, S, dcol, kDotThreads,
+                                        [&](int k, int32_t d) { da[S - 1 - k] = d; });
+        ok &= cut_column<MW, kDotW>(xb, Fb, S, dcol, kDotThreads,
+                                    [&](int k, int32_t d) { db[S - 1 - k] = d; });
+        if (!ok) raise_status(a.status, MW_ERANGE);
+      } else {
+        {
+          uint64_t T[NL];
+          fixed_point<MW, NL>(xa, Fa, T);
+          dot_digits<S, NL>(T, da, a.status);
+        }
+        {
+          uint64_t T[NL];
+          fixed_point<MW, NL>(xb, Fb, T);
+          dot_digits<S, NL>(T, db, a.status);
+        }
       }
 #pragma unroll
       for (int p = 0; p < S; ++p)
@@ -252,8 +267,8 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
       to_limbs32<NLF>(X, U);
       double *c = a.C + i;
       const int64_t psc = a.psc;
-      round_words32<MW, 2 * NLF>(U, Ea + Eb + 4 - kDotW * (D + 1),
-                                 [&](int k, double v) { c[k * psc] = v; });
+      round_column<MW, 2 * NLF>(U, rcol, 1, Ea + Eb + 4 - kDotW * (D + 1),
+                                [&](int k, double v) { c[k * psc] = v; });
     }
     __syncthreads();
   }
@@ -275,7 +290,8 @@ int launch_dot_s(const DotArgs &a, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::min<int64_t>(a.count, (int64_t)nsm * 8);
-  constexpr size_t smem = 2 * 2 * MW * kDotThreads * sizeof(double);
+  constexpr size_t smem = 2 * 2 * MW * kDotThreads * sizeof(double) +
+                         (MW >= 8 ? (size_t)(S + 3) * kDotThreads * sizeof(uint32_t) : 0);
   static bool attr_set = false;   // once per instance
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(dot_kernel<MW, S, NL, NLF>,

@@ -41,6 +41,7 @@
 #include <cmath>
 
 #include "mw_device.cuh"
+#include "mw_column.cuh"
 #include "mw_fuse.cuh"
 #include "mw_tc.cuh"
 #include "mw_work.cuh"
@@ -431,6 +432,7 @@ template <int MW, int NL, bool NARROW>
 __global__ void combine_kernel(const void *__restrict__ partials, const int32_t *eA,
                                const int32_t *eB, int64_t M, int64_t N, int G, int group, int D,
                                int w, double *C, int64_t ldc, int64_t psc) {
+  __shared__ uint32_t limbs[2 * NL][128];          // this thread's column: limbs[*][threadIdx.x]
   const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
   if (i >= M || j >= N) return;
   uint32_t U[2 * NL];
@@ -452,8 +454,8 @@ __global__ void combine_kernel(const void *__restrict__ partials, const int32_t 
     to_limbs32<NL>(X, U);
   }
   double *c = C + i * ldc + j;
-  round_words32<MW, 2 * NL>(U, eA[i] + eB[j] + 4 - w * (D + 1),
-                            [&](int k, double v) { c[k * psc] = v; });
+  round_column<MW, 2 * NL>(U, &limbs[0][threadIdx.x], 128, eA[i] + eB[j] + 4 - w * (D + 1),
+                           [&](int k, double v) { c[k * psc] = v; });
 }
 
 template <int MW, int NL>
@@ -471,7 +473,7 @@ int launch_combine(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
 template <int MW>
 int launch_combine_nl(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
   // |X| < 2^(63 + w (D-1)) plus a sign bit; as few 64-bit limbs as hold it (the
-  // rounding walks every limb)
+  // fusion touches every limb)
   const int bits = 64 + a.w * (a.D - 1) + 1;
   if constexpr (MW == 16) {
     if (bits <= 768) return launch_combine<MW, 12>(a, G, narrow, s);
