@@ -223,7 +223,9 @@ int mw_batch_describe(int count, const int64_t *shapes, mw_batch *batch);
 int mw_gemm_batched_workspace_size(const mw_plan *plan, const mw_batch *batch, size_t *bytes);
 
 /* Exponent spreads over all rows of the A_i and all columns of the B_i
- * (synchronizes); input to mw_plan_gemm for the batch. */
+ * (synchronizes); input to mw_plan_gemm for the batch.  ws: device workspace
+ * of at least 8192 + 256 count + 16 (sum_M + sum_N) + sum_MN / 32 bytes
+ * (MW_ENOSPC otherwise). */
 int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *problems,
                               void *ws, size_t ws_bytes, int *range_A, int *range_B,
                               mw_stream_t stream);

@@ -400,7 +400,7 @@ class Batch:
     def measure_spread(self):
         """Largest exponent spreads over the batch (synchronizes)."""
         b = self.batch
-        need = 4096 + 200 * b.count + 16 * (b.sum_M + b.sum_N) + 4096
+        need = 8192 + 256 * b.count + 16 * (b.sum_M + b.sum_N) + b.sum_MN // 32
         ws = _workspace(need, self.d_problems.device)
         ra, rb = ctypes.c_int(0), ctypes.c_int(0)
         _check(_lib.mw_measure_spread_batched(self.m, ctypes.byref(b),

@@ -41,7 +41,8 @@ constexpr double kL2Budget = 48.0 * (1 << 20);  // bytes of pieces in flight
 constexpr int kMaxStack = 8;
 
 struct Layout {
-  size_t header, info, eA, spA, eB, spB, pieceA, pieceB, items, partials, total;
+  size_t header, info, eA, spA, eB, spB, rowtab, stripetab, outtab, pieceA, pieceB, items,
+      partials, total;
   int64_t Kpitch;
   int64_t items_max;  // bound on the work items, from the batch sums
   int64_t rowsB;      // piece rows of B (bound: every problem with the most zero slices)
@@ -67,6 +68,11 @@ Layout layout_of(const mw_plan &p, const mw_batch &b) {
   L.spA = off;    off = a256(off + 4 * (size_t)b.sum_M);
   L.eB = off;     off = a256(off + 4 * (size_t)b.sum_N);
   L.spB = off;    off = a256(off + 4 * (size_t)b.sum_N);
+  // problem of every row of the A_i, every 32-column stripe of the B_i and every
+  // block of 256 outputs (lookup_tables_kernel)
+  L.rowtab = off;    off = a256(off + 4 * (size_t)b.sum_M);
+  L.stripetab = off; off = a256(off + 4 * (size_t)(b.sum_N / 32 + b.count + 1));
+  L.outtab = off;    off = a256(off + 4 * (size_t)(b.sum_MN / 256 + 2));
   L.pieceA = off; off = a256(off + 2 * (size_t)p.S_A * b.sum_M * L.Kpitch);
   L.pieceB = off; off = a256(off + 2 * (size_t)L.rowsB * L.Kpitch);
   L.planes = L.narrow ? p.D : n_groups(p.D, p.group);
@@ -194,6 +200,25 @@ __global__ void __launch_bounds__(256) item_table_kernel(const BInfo *info, cons
     table[u] = find_problem(info, count, u, [](const BInfo &b) { return b.work; });
 }
 
+// The problem of every row of the A_i (rows numbered problem by problem), of
+// every 32-column stripe of the B_i and of every block of 256 outputs (the
+// block's first output), one warp per problem: the split and fusion kernels
+// read it with one load instead of a binary search over the descriptors.
+__global__ void __launch_bounds__(256) lookup_tables_kernel(const BInfo *info, const BHeader *hdr,
+                                                            int count, int32_t *rowtab,
+                                                            int32_t *stripetab, int32_t *outtab) {
+  if (hdr->bad) return;
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const BInfo &b = info[i];
+    for (int64_t r = lane; r < b.M; r += 32) rowtab[b.eA + r] = (int32_t)i;
+    for (int64_t t = lane; t < (b.N + 31) / 32; t += 32) stripetab[b.stripes + t] = (int32_t)i;
+    const int64_t first = (b.outs + 255) >> 8, last = (b.outs + b.M * b.N - 1) >> 8;
+    for (int64_t blk = first + lane; blk <= last; blk += 32) outtab[blk] = (int32_t)i;
+  }
+}
+
 // ---- 2. split ---------------------------------------------------------------------
 // Rows of the A_i: one warp per row (k contiguous, coalesced reads); the shared
 // exponent by a warp reduction, then the balanced pieces of the row.  W8: the
@@ -203,18 +228,20 @@ template <int MW, int NL, bool W8>
 __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
     const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
     __nv_bfloat16 *pieceA, int32_t *eA, int32_t *spA, int32_t *max_spread, int range,
-    int exps_only, unsigned int *status) {
+    int exps_only, const int32_t *rowtab, unsigned int *status) {
   if (hdr->bad) return;
   // m >= 8, w = 8: each word adds its fields into this thread's column of slots
   // (cut_column) instead of a carry chain over every limb
   constexpr bool kColumn = W8 && MW >= 8;
   constexpr int kSlots = kColumn ? (64 * NL - 8) / 24 + 4 : 1;   // S <= 8 NL
   __shared__ uint32_t slots[kSlots][256];
+  if constexpr (kColumn)
+    for (int c = 0; c < kSlots; ++c) slots[c][threadIdx.x] = 0u;   // cut_column leaves it zero
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
        task < hdr->sum_M; task += nwarps) {
-    const int i = find_problem(info, count, task, [](const BInfo &b) { return b.eA; });
+    const int i = rowtab[task];
     const BInfo &b = info[i];
     const int64_t r = task - b.eA, K = b.K;
     const double *base = b.A + r * b.lda;
@@ -251,16 +278,20 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
     const int64_t Kp = (K + 63) & ~(int64_t)63;
     for (int64_t k = lane; k < Kp; k += 32) {
       if (k >= K) {  // zero padding: no arithmetic
-        for (int p = 0; p < S; ++p) dst[k + p * plane] = zero;
+        __nv_bfloat16 *q = dst + k;
+        for (int p = 0; p < S; ++p, q += plane) *q = zero;
         continue;
       }
       double x[MW];
 #pragma unroll
       for (int j = 0; j < MW; ++j) x[j] = base[j * b.psa + k];
       if constexpr (kColumn) {
-        __nv_bfloat16 *q = dst + k + (int64_t)(S - 1) * plane;
-        if (!cut_column<MW, 8>(x, F, S, &slots[0][threadIdx.x], 256,
-                               [&](int kk, int32_t d) { q[-kk * plane] = to_out<__nv_bfloat16>(d); }))
+        // digits from the least significant (piece S-1) up
+        uint16_t *q = reinterpret_cast<uint16_t *>(dst + k) + (int64_t)(S - 1) * plane;
+        if (!cut_column<MW, 8>(x, F, S, &slots[0][threadIdx.x], 256, [&](int, int32_t d) {
+              *q = small_int_bf16(d);
+              q -= plane;
+            }))
           raise_status(status, MW_ERANGE);
       } else if constexpr (W8) {
         cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst + k, plane, status);
@@ -273,28 +304,31 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
 
 // Columns of the B_i: one CTA (32 x 8 threads) per 32-column stripe of one
 // problem.  Pass 1 reads rows of the stripe (coalesced) and reduces the column
-// exponents in shared memory; pass 2 stages 32 x 32 tiles of the stripe in
+// exponents in shared memory; pass 2 stages 16 x 32 tiles of the stripe in
 // shared memory and cuts them so that the pieces are written k-contiguous.
 template <int MW, int NL, bool W8>
-__global__ void __launch_bounds__(256, 3) batch_split_cols_kernel(
+__global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
     const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
     __nv_bfloat16 *pieceB, int32_t *eB, int32_t *spB, int32_t *max_spread, int range,
-    int exps_only, unsigned int *status) {
-  extern __shared__ double tile[];              // [MW][32 k][33], then for the column
+    int exps_only, const int32_t *stripetab, unsigned int *status) {
+  extern __shared__ double tile[];              // [MW][16 k][33], then for the column
                                                 // cut the threads' slots
   __shared__ int smax[8][32], smin[8][32], sE[32];
   constexpr bool kColumn = W8 && MW >= 8;     // as in the row kernel
-  uint32_t *slots = reinterpret_cast<uint32_t *>(tile + MW * 32 * 33) + threadIdx.x;
+  uint32_t *slots = reinterpret_cast<uint32_t *>(tile + MW * 16 * 33) + threadIdx.x;
+  if constexpr (kColumn)
+    for (int c = 0; c < (64 * NL - 8) / 24 + 4; ++c) slots[c * 256] = 0u;   // left zero by cut_column
   if (hdr->bad) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int64_t task = blockIdx.x; task < hdr->sum_stripes; task += gridDim.x) {
-    const int i = find_problem(info, count, task, [](const BInfo &b) { return b.stripes; });
+    const int i = stripetab[task];
     const BInfo &b = info[i];
     const int64_t j0 = (task - b.stripes) * 32, K = b.K;
     const int64_t j = j0 + tx;
     int emax = kExpZero, emin = -kExpZero;
     bool nonfinite = false;
     if (j < b.N)
+#pragma unroll 4
       for (int64_t k = ty; k < K; k += 8) {
         int e = kExpZero;
 #pragma unroll
@@ -328,19 +362,29 @@ __global__ void __launch_bounds__(256, 3) batch_split_cols_kernel(
     if (!exps_only) {
       const int64_t plane = b.N * Kpitch;
       const int64_t Kp = (K + 63) & ~(int64_t)63;
-      for (int64_t k0 = 0; k0 < Kp; k0 += 32) {
+      // this thread's share of the next tile (rows ty, ty + 8), loaded while the
+      // current one is cut
+      double nxt[MW][2];
+      auto fetch = [&](int64_t k0) {
 #pragma unroll
         for (int q = 0; q < MW; ++q)
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int kl = ty + 8 * u;
-            const int64_t k = k0 + kl;
-            tile[(q * 32 + kl) * 33 + tx] = (k < K && j < b.N) ? b.B[q * b.psb + k * b.ldb + j] : 0.0;
+          for (int u = 0; u < 2; ++u) {
+            const int64_t k = k0 + ty + 8 * u;
+            nxt[q][u] = (k < K && j < b.N) ? b.B[q * b.psb + k * b.ldb + j] : 0.0;
           }
+      };
+      fetch(0);
+      for (int64_t k0 = 0; k0 < Kp; k0 += 16) {
+#pragma unroll
+        for (int q = 0; q < MW; ++q)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) tile[(q * 16 + ty + 8 * u) * 33 + tx] = nxt[q][u];
         __syncthreads();
-        for (int it = 0; it < 4; ++it) {
-          const int e = threadIdx.x + 256 * it;   // 1024 entries per tile, k fastest
-          const int jl = e >> 5, kl = e & 31;
+        if (k0 + 16 < Kp) fetch(k0 + 16);
+        for (int it = 0; it < 2; ++it) {
+          const int e = threadIdx.x + 256 * it;   // 512 entries per tile, k fastest
+          const int jl = e >> 4, kl = e & 15;
           const int64_t jj = j0 + jl, k = k0 + kl;
           if (jj >= b.N) continue;
           // slice q of column jj at row rowB + (q + rs - 1) N + jj; the rs - 1 slices
@@ -352,17 +396,21 @@ __global__ void __launch_bounds__(256, 3) batch_split_cols_kernel(
             dst[(S - 1 + p) * plane] = zero;
           }
           if (k >= K) {
-            for (int p = 0; p < S; ++p) dst[p * plane] = zero;
+            __nv_bfloat16 *q = dst;
+            for (int p = 0; p < S; ++p, q += plane) *q = zero;
             continue;
           }
           double x[MW];
 #pragma unroll
-          for (int q = 0; q < MW; ++q) x[q] = tile[(q * 32 + kl) * 33 + jl];
+          for (int q = 0; q < MW; ++q) x[q] = tile[(q * 16 + kl) * 33 + jl];
           const int F = w * S - 2 - sE[jl];
           if constexpr (kColumn) {
-            __nv_bfloat16 *q = dst + (int64_t)(S - 1) * plane;
-            if (!cut_column<MW, 8>(x, F, S, slots, 256,
-                                   [&](int kk, int32_t d) { q[-kk * plane] = to_out<__nv_bfloat16>(d); }))
+            // digits from the least significant (piece S-1) up
+            uint16_t *q = reinterpret_cast<uint16_t *>(dst) + (int64_t)(S - 1) * plane;
+            if (!cut_column<MW, 8>(x, F, S, slots, 256, [&](int, int32_t d) {
+                  *q = small_int_bf16(d);
+                  q -= plane;
+                }))
               raise_status(status, MW_ERANGE);
           } else if constexpr (W8) {
             cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst, plane, status);
@@ -385,23 +433,27 @@ template <int MW, int NL, bool NARROW>
 __global__ void __launch_bounds__(256, 3) batch_combine_kernel(const BInfo *info, const BHeader *hdr,
                                                             int count, const void *partials,
                                                             const int32_t *eA, const int32_t *eB,
-                                                            int G, int group, int D, int w) {
+                                                            int G, int group, int D, int w,
+                                                            const int32_t *outtab) {
   if (hdr->bad) return;
-  __shared__ int first;
   __shared__ uint32_t limbs[2 * NL][256];          // this thread's column: limbs[*][threadIdx.x]
   const int64_t total = hdr->sum_MN;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total;
        base += (int64_t)gridDim.x * blockDim.x) {
-    __syncthreads();
-    if (threadIdx.x == 0) first = find_problem(info, count, base, [](const BInfo &b) { return b.outs; });
-    __syncthreads();
     const int64_t f = base + threadIdx.x;
     if (f >= total) continue;
-    int i = first;
+    int i = outtab[base >> 8];                              // problem of the block's first output
     while (i + 1 < count && info[i + 1].outs <= f) ++i;   // at most a few steps
     const BInfo &b = info[i];
     const int64_t o = f - b.outs;                           // = j * M + r
-    const int64_t j = o / b.M, r = o - j * b.M;
+    int64_t j, r;
+    if (o <= 0xFFFFFFFFll && b.M <= 0xFFFFFFFFll) {         // 32-bit division when it fits
+      j = (uint32_t)o / (uint32_t)b.M;
+      r = o - j * b.M;
+    } else {
+      j = o / b.M;
+      r = o - j * b.M;
+    }
     uint32_t U[2 * NL];
     if (NARROW && w == 8) {
       fuse_w8<2 * NL>(U, static_cast<const int32_t *>(partials) + b.part + o, b.N * b.M, D);
@@ -462,9 +514,10 @@ int launch_split_w(const BInfo *info, const BHeader *hdr, const mw_batch &b, con
   batch_split_rows_kernel<MW, NL, W8><<<grid_for(8), 256, 0, s>>>(
       info, hdr, b.count, p.w, p.S_A, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceA),
       reinterpret_cast<int32_t *>(w8 + L.eA), reinterpret_cast<int32_t *>(w8 + L.spA),
-      h->max_spread, p.range_A, exps_only, status_ptr());
-  // the tile, then (w = 8, m >= 8) 256 columns of (64 NL - 8) / 24 + 4 slots
-  const size_t sm = (size_t)MW * 32 * 33 * sizeof(double) +
+      h->max_spread, p.range_A, exps_only, reinterpret_cast<const int32_t *>(w8 + L.rowtab),
+      status_ptr());
+  // the 16-row tile, then (w = 8, m >= 8) 256 columns of (64 NL - 8) / 24 + 4 slots
+  const size_t sm = (size_t)MW * 16 * 33 * sizeof(double) +
                     (W8 && MW >= 8 ? (size_t)((64 * NL - 8) / 24 + 4) * 256 * sizeof(uint32_t) : 0);
   static bool attr_set = false;  // once per instantiation
   if (!attr_set) {
@@ -473,10 +526,11 @@ int launch_split_w(const BInfo *info, const BHeader *hdr, const mw_batch &b, con
     if (e != cudaSuccess) return cuda_fail(e, "batched split smem attribute");
     attr_set = true;
   }
-  batch_split_cols_kernel<MW, NL, W8><<<grid_for(4), 256, sm, s>>>(
+  batch_split_cols_kernel<MW, NL, W8><<<grid_for(2), 256, sm, s>>>(
       info, hdr, b.count, p.w, p.S_B, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceB),
       reinterpret_cast<int32_t *>(w8 + L.eB), reinterpret_cast<int32_t *>(w8 + L.spB),
-      h->max_spread + 1, p.range_B, exps_only, status_ptr());
+      h->max_spread + 1, p.range_B, exps_only,
+      reinterpret_cast<const int32_t *>(w8 + L.stripetab), status_ptr());
   return MW_OK;
 }
 
@@ -497,6 +551,10 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
   prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, p.D, L.sched, L.bn, L.rmax, L.planes, p.S_A,
                                      p.S_B, L.Kpitch, L.items_max, b, info, hdr, status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch prologue launch");
+  lookup_tables_kernel<<<(unsigned)std::min<int64_t>((b.count + 7) / 8, grid_for(4)), 256, 0, s>>>(
+      info, hdr, b.count, reinterpret_cast<int32_t *>(w8 + L.rowtab),
+      reinterpret_cast<int32_t *>(w8 + L.stripetab), reinterpret_cast<int32_t *>(w8 + L.outtab));
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch lookup tables launch");
   if (!exps_only) {
     item_table_kernel<<<grid_for(4), 256, 0, s>>>(info, hdr, b.count,
                                                   reinterpret_cast<int32_t *>(w8 + L.items));
@@ -520,11 +578,13 @@ void launch_combine_b(const BInfo *info, const BHeader *hdr, const mw_batch &b,
   const int32_t *eA = reinterpret_cast<const int32_t *>(w8 + L.eA);
   const int32_t *eB = reinterpret_cast<const int32_t *>(w8 + L.eB);
   if (L.narrow)
-    batch_combine_kernel<MW, NL, true><<<grid_for(8), 256, 0, s>>>(
-        info, hdr, b.count, w8 + L.partials, eA, eB, n_groups(p.D, p.group), p.group, p.D, p.w);
+    batch_combine_kernel<MW, NL, true><<<grid_for(3), 256, 0, s>>>(
+        info, hdr, b.count, w8 + L.partials, eA, eB, n_groups(p.D, p.group), p.group, p.D, p.w,
+        reinterpret_cast<const int32_t *>(w8 + L.outtab));
   else
-    batch_combine_kernel<MW, NL, false><<<grid_for(8), 256, 0, s>>>(
-        info, hdr, b.count, w8 + L.partials, eA, eB, n_groups(p.D, p.group), p.group, p.D, p.w);
+    batch_combine_kernel<MW, NL, false><<<grid_for(3), 256, 0, s>>>(
+        info, hdr, b.count, w8 + L.partials, eA, eB, n_groups(p.D, p.group), p.group, p.D, p.w,
+        reinterpret_cast<const int32_t *>(w8 + L.outtab));
 }
 
 template <int MW>

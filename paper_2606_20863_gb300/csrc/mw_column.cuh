@@ -58,6 +58,46 @@ MW_HD int col_ctz(uint32_t x) {  // x != 0
 #endif
 }
 
+MW_HD uint32_t col_fshl(uint32_t lo, uint32_t hi, int n) {  // high word of (hi:lo) << n, n < 32
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_l(lo, hi, n);
+#else
+  return (uint32_t)(((((uint64_t)hi << 32) | lo) << n) >> 32);
+#endif
+}
+MW_HD uint32_t col_fshr(uint32_t lo, uint32_t hi, int n) {  // low word of (hi:lo) >> n, n < 32
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_r(lo, hi, n);
+#else
+  return (uint32_t)((((uint64_t)hi << 32) | lo) >> n);
+#endif
+}
+MW_HD float col_float(uint32_t b) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(b);
+#else
+  float f;
+  std::memcpy(&f, &b, sizeof f);
+  return f;
+#endif
+}
+MW_HD uint32_t col_fbits(float f) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_uint(f);
+#else
+  uint32_t b;
+  std::memcpy(&b, &f, sizeof b);
+  return b;
+#endif
+}
+
+// bfloat16 bits of an integer |d| <= 2^8 (exact): 1.5 2^23 + d has the float
+// bit pattern 0x4B400000 + d, less 1.5 2^23 it is d; a float of at most 8
+// significant bits is its top 16 bits.
+MW_HD uint16_t small_int_bf16(int32_t d) {
+  return (uint16_t)(col_fbits(col_float(0x4B400000u + (uint32_t)d) - 12582912.0f) >> 16);
+}
+
 // Slots of the column for S digits of w bits: the 24-bit chunk holding the top
 // digit, Ct = w (S-1) / 24, the ones below it and three above it (the highest
 // a word's four fields can reach; they stay zero for in-range input).
@@ -65,63 +105,65 @@ MW_HD int cut_column_slots(int w, int S) { return w * (S - 1) / 24 + 4; }
 
 // Balanced digits d_k (k = 0 least significant) of T = sum_j trunc(x_j 2^F):
 // d_k in [-2^(w-1), 2^(w-1)) for k < S-1, the top digit d_(S-1) the rest (in
-// [-2^(w-1), 2^(w-1)] when T lies in [-2^(wS-1), 2^(wS-1))).  emit(k, d) gets
-// them from k = 0 up.  Returns false when T lies outside that range.
+// [-2^(w-1), 2^(w-1)] when T lies in [-2^(wS-1), 2^(wS-1))).  emit(k, d) is
+// called once per digit in the order k = 0, 1, ..., S-1.  Returns false when T
+// lies outside that range.
 // col: this thread's column, slot c at col[c * stride], cut_column_slots(w, S)
-// of them.  Slot c holds bits 24c .. 24c+23 plus a signed excess; the slots
-// start at the bias H = 2^(w-1) (1 + 2^w + ... + 2^(w(S-2))) so that every digit
-// below the top one comes out as a plain w-bit field minus 2^(w-1).
+// of them, all zero on entry and left zero.  Slot c collects bits 24c .. 24c+23
+// of every word plus a signed excess; the carry pass adds the bias
+// H = 2^(w-1) (1 + 2^w + ... + 2^(w(S-2))), after which every digit below the
+// top one is a plain w-bit field minus 2^(w-1).
 template <int MW, int W, class Emit>
 MW_HD bool cut_column(const double (&x)[MW], int F, int S, uint32_t *col, int stride, Emit emit) {
   static_assert(W == 8 || W == 24, "digit widths 8 and 24");
   constexpr int32_t kHalf = 1 << (W - 1);
+  constexpr int32_t kBias = W == 24 ? kHalf : 0x808080;   // H restricted to a full chunk
   const int Ct = W * (S - 1) / 24;
-  for (int c = 0; c < Ct + 4; ++c) {
-    uint32_t h;
-    if (W == 24) {
-      h = c < S - 1 ? (uint32_t)kHalf : 0u;
-    } else {
-      const int nb = S - 1 - 3 * c;                  // biased bytes in this chunk
-      h = nb >= 3 ? 0x808080u : (nb <= 0 ? 0u : (0x808080u & ((1u << (8 * nb)) - 1u)));
-    }
-    col[c * stride] = h;
-  }
 #pragma unroll
   for (int j = 0; j < MW; ++j) {
     const uint64_t b = col_bits(x[j]);
-    const int be = (int)((b >> 52) & 0x7ff);
-    uint64_t M = b & ((1ull << 52) - 1);
-    if (be) M |= 1ull << 52;
+    const uint32_t bh = (uint32_t)(b >> 32);
+    const int be = (int)((bh >> 20) & 0x7ff);
+    const uint32_t mlo = (uint32_t)b;
+    const uint32_t mhi = (bh & 0xFFFFFu) | (be ? 0x100000u : 0u);   // M = mhi:mlo < 2^53
     const int sh = (be ? be : 1) - 1075 + F;      // weight of M's last bit on the grid
-    uint64_t y = M;
+    // y = trunc(M 2^min(sh, 0)) at bit pos = max(sh, 0)
+    uint32_t ylo = mlo, yhi = mhi;
     int pos = sh;
-    if (sh < 0) {                                   // truncated toward zero
-      y = -sh < 64 ? M >> -sh : 0;
+    if (sh < 0) {
+      const int r = -sh;
+      ylo = r < 32 ? col_fshr(mlo, mhi, r) : (r < 64 ? mhi >> (r - 32) : 0u);
+      yhi = r < 32 ? mhi >> r : 0u;
       pos = 0;
     }
     if (pos >= 24 * (Ct + 1)) {                     // only words the exponent does not cover
-      y = 0;                                        // (non-finite input, flagged elsewhere)
+      ylo = yhi = 0;                                // (non-finite input, flagged elsewhere)
       pos = 0;
     }
     const int c = pos / 24, o = pos - 24 * c;
-    const uint64_t lo = y << o;
-    const uint64_t hi = o ? (y >> (64 - o)) : 0;   // bits 64 .. 76
-    const int32_t f0 = (int32_t)(lo & 0xFFFFFF);
-    const int32_t f1 = (int32_t)((lo >> 24) & 0xFFFFFF);
-    const int32_t f2 = (int32_t)(((lo >> 48) | (hi << 16)) & 0xFFFFFF);
-    const int32_t f3 = (int32_t)(hi >> 8);
-    const int32_t s = (b >> 63) ? -1 : 1;
+    const uint32_t w0 = ylo << o, w1 = col_fshl(ylo, yhi, o), w2 = col_fshl(yhi, 0u, o);
+    const int32_t f0 = (int32_t)(w0 & 0xFFFFFFu);
+    const int32_t f1 = (int32_t)(col_fshr(w0, w1, 24) & 0xFFFFFFu);
+    const int32_t f2 = (int32_t)(col_fshr(w1, w2, 16) & 0xFFFFFFu);
+    const int32_t f3 = (int32_t)(w2 >> 8);
+    const int32_t s = (bh >> 31) ? -1 : 1;
     uint32_t *p = col + c * stride;
     p[0] = (uint32_t)((int32_t)p[0] + s * f0);
     p[stride] = (uint32_t)((int32_t)p[stride] + s * f1);
     p[2 * stride] = (uint32_t)((int32_t)p[2 * stride] + s * f2);
     p[3 * stride] = (uint32_t)((int32_t)p[3 * stride] + s * f3);
   }
+  // carry pass; lsign: sign of the digits below the current chunk's, read off
+  // the most significant nonzero digit (balanced digits), one compare a chunk
   int32_t carry = 0;
+  int lsign = 0;
+#pragma unroll
   for (int c = 0; c < Ct; ++c) {
-    const int32_t v = (int32_t)col[c * stride] + carry;
-    const int32_t u = v & 0xFFFFFF;
+    const int32_t v = (int32_t)col[c * stride] + carry + kBias;
+    col[c * stride] = 0u;
     carry = v >> 24;
+    const int32_t u = v & 0xFFFFFF;
+    if (u != kBias) lsign = u > kBias ? 1 : -1;
     if (W == 24) {
       emit(c, u - kHalf);
     } else {
@@ -130,30 +172,24 @@ MW_HD bool cut_column(const double (&x)[MW], int F, int S, uint32_t *col, int st
       emit(3 * c + 2, (u >> 16) - 128);
     }
   }
-  const int32_t v = (int32_t)col[Ct * stride] + carry;
   const int nb = W == 24 ? 0 : S - 1 - 3 * Ct;     // digits of chunk Ct below the top one
-  for (int i = 0; i < nb; ++i) emit(3 * Ct + i, ((v >> (8 * i)) & 0xFF) - 128);
+  const int32_t v = (int32_t)col[Ct * stride] + carry + (W == 24 ? 0 : (0x808080 & ((1 << (8 * nb)) - 1)));
+  for (int i = 0; i < nb; ++i) {
+    const int32_t d = ((v >> (8 * i)) & 0xFF) - 128;
+    emit(3 * Ct + i, d);
+    if (d != 0) lsign = d > 0 ? 1 : -1;
+  }
   const int32_t top = v >> (W == 24 ? 0 : 8 * nb);
   emit(S - 1, top);
-  bool ok = (col[(Ct + 1) * stride] | col[(Ct + 2) * stride] | col[(Ct + 3) * stride]) == 0u;
-  if (top <= -kHalf || top >= kHalf) {
-    // T = top 2^(w(S-1)) + L with |L| < 2^(w(S-1)) and L of the sign of its most
-    // significant nonzero digit: in range only for top = -2^(w-1), L >= 0 or
-    // top = 2^(w-1), L < 0.  Rare; the digits are recomputed for it.
-    int lsign = 0;
-    int32_t cy = 0;
-    for (int c = 0; c <= Ct; ++c) {
-      const int32_t vv = (int32_t)col[c * stride] + cy;
-      cy = vv >> 24;
-      const int nd = W == 24 ? (c < Ct ? 1 : 0) : (c < Ct ? 3 : nb);
-      for (int i = 0; i < nd; ++i) {
-        const int32_t d = W == 24 ? (vv & 0xFFFFFF) - kHalf : ((vv >> (8 * i)) & 0xFF) - 128;
-        if (d != 0) lsign = d > 0 ? 1 : -1;
-      }
-    }
-    ok = ok && ((top == -kHalf && lsign >= 0) || (top == kHalf && lsign < 0));
-  }
-  return ok;
+  const uint32_t above = col[(Ct + 1) * stride] | col[(Ct + 2) * stride] | col[(Ct + 3) * stride];
+  col[Ct * stride] = 0u;
+  col[(Ct + 1) * stride] = 0u;
+  col[(Ct + 2) * stride] = 0u;
+  col[(Ct + 3) * stride] = 0u;
+  // T = top 2^(w(S-1)) + L, |L| < 2^(w(S-1)), L of sign lsign: in range for
+  // |top| < 2^(w-1), for top = -2^(w-1) with L >= 0 and top = 2^(w-1) with L < 0
+  return above == 0u && ((top > -kHalf && top < kHalf) || (top == -kHalf && lsign >= 0) ||
+                         (top == kHalf && lsign < 0));
 }
 
 // X 2^ex into MW words by greedy rounding to nearest, ties to even: word k is

@@ -6,7 +6,8 @@
 // integer units instead of the tensor cores: one CTA per inner product,
 //   1. the shared exponents E_a, E_b of the two vectors (block reduction);
 //   2. every entry cut into S balanced digits of w = 24 bits (|d| <= 2^23) on
-//      the fixed-point grid below 2^E, as for the matrix product;
+//      the fixed-point grid below 2^E, as for the matrix product (m >= 8:
+//      through a shared-memory column of 24-bit slots, cut_column);
 //   3. each thread sums d^a_p d^b_q into int64 diagonal sums s_t, t = p + q < D
 //      (|d^a d^b| <= 2^46, so a thread's share of K stays far below 2^63); the
 //      block adds them up in 128 bits;
@@ -136,6 +137,8 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
   // (cut_column) instead of a carry chain over every limb
   constexpr bool kColumn = MW >= 8;
   uint32_t *dcol = reinterpret_cast<uint32_t *>(stage + 2 * 2 * MW * kDotThreads) + threadIdx.x;
+  if constexpr (kColumn)
+    for (int c = 0; c < S + 3; ++c) dcol[c * kDotThreads] = 0u;   // cut_column leaves it zero
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int D = a.D;
   for (int64_t i = blockIdx.x; i < a.count; i += gridDim.x) {
