@@ -211,7 +211,9 @@ def single_inputs(name):
 
 def timed(step, steps, flush, mw, dist, dev, phase=True):
     """Run `steps` steps with an untimed L2 flush before each; CUDA events on the
-    current stream; returns (per-step ms, product-kernel ms, clocks)."""
+    current stream; returns (per-step ms, product-kernel ms, clocks) and, with
+    phase events, leaves the mean ms of the split, product and fusion phases in
+    timed.phases."""
     import torch
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     clocks = Clocks(dev.index)
@@ -236,6 +238,10 @@ def timed(step, steps, flush, mw, dist, dev, phase=True):
     mw.check_status()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     kern_ms = [e[1].elapsed_time(e[2]) for e in ev] if phase else []
+    timed.phases = ({"split_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                     "product_ms": statistics.mean(kern_ms),
+                     "fusion_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in ev)}
+                    if phase else None)
     return step_ms, kern_ms, clk
 
 
@@ -456,6 +462,7 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
     # product-kernel time: the same call launched directly (phase events are not
     # recorded inside a graph), as many runs as timed steps
     _, kern_ms, _ = timed(batch.run, max(3, args.steps), flush, mw, None, dev)
+    phases = timed.phases
     roof = roofline_of(pairs, flops, kern_ms, "od_batch" if args.count == 20000 else None)
     roof["algorithmic"] = (f"{pairs} slice pairs x sum of 2 n^3 = {pairs * flops:.3e} flop per "
                            "launch; kernel time from direct calls of the batch")
@@ -495,8 +502,10 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
                                    "batched call replayed from a CUDA graph",
                        "m": 8, "count": args.count, "plan": plan.as_dict(), "slice_pairs": pairs,
                        "useful_flop_per_step": flops,
+                       "phases_ms_direct_calls": phases,
                        "l2": "flushed (256 MiB write) before every timed step"},
-            "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": 6 * args.steps}
+            # prologue, lookup tables, item table, two splits, product, fusion
+            "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": 7 * args.steps}
     if rank == 0 and not args.no_cpu:
         from oracle import textbook
         tc = textbook.TextbookC()
