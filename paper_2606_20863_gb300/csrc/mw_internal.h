@@ -72,6 +72,8 @@ struct ProductLaunch {
 };
 int launch_product(const ProductLaunch &a, cudaStream_t s);
 
+// Exact fusion and rounding of one product's partial sums (mw_combine.cu).
+int launch_combine(const OzakiArgs &a, int G, bool narrow, cudaStream_t s);
 // between_kernels runs after the product kernel is launched, before the combine.
 int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels);
 // Every diagonal sum s_t fits in int32: S_min * K * 2^(2w-2) < 2^31.  Then the

@@ -16,7 +16,8 @@
 // is accumulated by Horner's rule mod 2^64, V = sum_t s_t 2^(w (t1 - t)), and
 // stored as an int64 plane.  Planes are column-major per problem.  The fusion
 // adds the planes exactly into one integer X and rounds X 2^(E_i + E_j + 4 -
-// w(D+1)) to nearest into m words, one after the other (greedy).
+// w(D+1)) to nearest into m words, one after the other (greedy); that fusion
+// kernel is in mw_combine.cu.
 //
 // Product kernel (persistent, one CTA per SM; a work item is one output tile of
 // one diagonal group):
@@ -41,8 +42,6 @@
 #include <cmath>
 
 #include "mw_device.cuh"
-#include "mw_column.cuh"
-#include "mw_fuse.cuh"
 #include "mw_tc.cuh"
 #include "mw_work.cuh"
 
@@ -424,76 +423,6 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
   }
 }
 
-// ---- fusion of one product: thread per output ---------------------------------
-// Narrow: D planes of int32 diagonal sums s_t, weight 2^(w (D-1-t)).
-// Wide:   G planes of int64 group sums, weight 2^(w (D-1-t1_g)).
-// Planes are column-major (entry (i, j) at j M + i): threads run along i.
-template <int MW, int NL, bool NARROW>
-__global__ void combine_kernel(const void *__restrict__ partials, const int32_t *eA,
-                               const int32_t *eB, int64_t M, int64_t N, int G, int group, int D,
-                               int w, double *C, int64_t ldc, int64_t psc) {
-  __shared__ uint32_t limbs[2 * NL][128];          // this thread's column: limbs[*][threadIdx.x]
-  const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
-  if (i >= M || j >= N) return;
-  uint32_t U[2 * NL];
-  if (NARROW && w == 8) {
-    fuse_w8<2 * NL>(U, static_cast<const int32_t *>(partials) + j * M + i, N * M, D);
-  } else {
-    uint64_t X[NL];
-#pragma unroll
-    for (int k = 0; k < NL; ++k) X[k] = 0;
-    if constexpr (NARROW) {
-      fuse_diagonals<NL>(X, static_cast<const int32_t *>(partials) + j * M + i, N * M, D, group, w);
-    } else {
-      const int64_t *p = static_cast<const int64_t *>(partials);
-      for (int g = 0; g < G; ++g) {
-        const int t1 = min(D, (g + 1) * group) - 1;
-        add_shifted<NL>(X, p[((int64_t)g * N + j) * M + i], w * (D - 1 - t1));
-      }
-    }
-    to_limbs32<NL>(X, U);
-  }
-  double *c = C + i * ldc + j;
-  round_column<MW, 2 * NL>(U, &limbs[0][threadIdx.x], 128, eA[i] + eB[j] + 4 - w * (D + 1),
-                           [&](int k, double v) { c[k * psc] = v; });
-}
-
-template <int MW, int NL>
-int launch_combine(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
-  dim3 grid((unsigned)((a.M + 127) / 128), (unsigned)a.N);
-  if (narrow)
-    combine_kernel<MW, NL, true><<<grid, 128, 0, s>>>(a.partials, a.eA, a.eB, a.M, a.N, G, a.group,
-                                                      a.D, a.w, a.C, a.ldc, a.psc);
-  else
-    combine_kernel<MW, NL, false><<<grid, 128, 0, s>>>(a.partials, a.eA, a.eB, a.M, a.N, G,
-                                                       a.group, a.D, a.w, a.C, a.ldc, a.psc);
-  return cuda_fail(cudaGetLastError(), "combine launch");
-}
-
-template <int MW>
-int launch_combine_nl(const OzakiArgs &a, int G, bool narrow, cudaStream_t s) {
-  // |X| < 2^(63 + w (D-1)) plus a sign bit; as few 64-bit limbs as hold it (the
-  // fusion touches every limb)
-  const int bits = 64 + a.w * (a.D - 1) + 1;
-  if constexpr (MW == 16) {
-    if (bits <= 768) return launch_combine<MW, 12>(a, G, narrow, s);
-    if (bits <= 832) return launch_combine<MW, 13>(a, G, narrow, s);
-    if (bits <= 896) return launch_combine<MW, 14>(a, G, narrow, s);
-    if (bits <= 960) return launch_combine<MW, 15>(a, G, narrow, s);
-    if (bits <= 1024) return launch_combine<MW, 16>(a, G, narrow, s);
-    if (bits <= 1088) return launch_combine<MW, 17>(a, G, narrow, s);
-  } else {
-    if (bits <= 256) return launch_combine<MW, 4>(a, G, narrow, s);
-    if (bits <= 320) return launch_combine<MW, 5>(a, G, narrow, s);
-    if (bits <= 384) return launch_combine<MW, 6>(a, G, narrow, s);
-    if (bits <= 448) return launch_combine<MW, 7>(a, G, narrow, s);
-    if (bits <= 512) return launch_combine<MW, 8>(a, G, narrow, s);
-    if (bits <= 576) return launch_combine<MW, 9>(a, G, narrow, s);
-    if (bits <= 640) return launch_combine<MW, 10>(a, G, narrow, s);
-  }
-  return fail(MW_EUNSUPPORTED, "D = %d diagonals of %d bits too many for the fusion", a.D, a.w);
-}
-
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -649,13 +578,7 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
   int rc = launch_product(L, s);
   if (rc) return rc;
   if (between_kernels) between_kernels();
-  switch (a.m) {
-    case 2: return launch_combine_nl<2>(a, G, narrow, s);
-    case 4: return launch_combine_nl<4>(a, G, narrow, s);
-    case 8: return launch_combine_nl<8>(a, G, narrow, s);
-    case 16: return launch_combine_nl<16>(a, G, narrow, s);
-  }
-  return fail(MW_EINVAL, "m must be 2, 4 or 8");
+  return launch_combine(a, G, narrow, s);
 }
 
 }  // namespace mw
