@@ -251,11 +251,11 @@ def timed(step, steps, flush, mw, dist, dev, phase=True):
 # no traffic until it is captured again.
 KERNEL_SOURCES = ("mw_ozaki.cu", "mw_tc.cuh", "mw_device.cuh", "mw_work.cuh")
 TRAFFIC = {   # profiles/dram_traffic_ozaki_kernel.md
-    "qd1024": {"bytes": 397631744 + 90837248, "digest": "6e87600d786be671"},
-    "dd4096": {"bytes": 46380924416 + 1610370560, "digest": "6e87600d786be671"},
-    "qd4096": {"bytes": 138709625088 + 2540237568, "digest": "6e87600d786be671"},
-    # captured on 2,000 of the 20,000 products (same size distribution), times 10
-    "od_batch": {"bytes": 10 * (4058468096 + 2792812544), "digest": "6e87600d786be671"},
+    "qd1024": {"bytes": 395363328 + 91096832, "digest": "c15848e119b2e400"},
+    "dd4096": {"bytes": 47455044352 + 1611938048, "digest": "c15848e119b2e400"},
+    "qd4096": {"bytes": 181198118656 + 2540828672, "digest": "c15848e119b2e400"},
+    # 2,000 of the 20,000 products captured (the whole batch holds ~100 GB), x10
+    "od_batch": {"bytes": 10 * (4056931840 + 2792728320), "digest": "c15848e119b2e400"},
 }
 
 
