@@ -356,6 +356,7 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
     # product-kernel time: phase events around direct calls (events are not
     # recorded inside a graph), as many runs as timed steps
     _, kern_ms, _ = timed(call, args.steps, flush, mw, None, dev)
+    phases = timed.phases
 
     # plain FP64 form on the same operands and bound (the comparison of the metric)
     pplan = mw.plan_for(tA, tB, "plain")
@@ -416,6 +417,7 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
                        "plain_fp64_gflops": plain_gflops, "plain_plan": pplan.as_dict(),
                        "speedup_vs_plain": (value / world / plain_gflops) if plain_gflops else None,
                        "product_kernel_ms": kern_s * 1e3, "step_ms_min": min(step_ms),
+                       "phases_ms_direct_calls": phases,
                        "plain_roofline": plain_roof,
                        "int8_peak_tops_measured": int8_peak,
                        "slice_ops_per_s_over_int8_peak":
