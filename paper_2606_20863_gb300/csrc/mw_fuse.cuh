@@ -71,7 +71,8 @@ __device__ __forceinline__ void to_limbs32(const uint64_t (&X)[NL], uint32_t (&U
 // s_t = p[t * plane], as NL32 32-bit limbs (two's complement), built from the
 // least significant end: limb j takes the four sums of weights 2^(32j),
 // 2^(32j+8), 2^(32j+16), 2^(32j+24), joined by Horner in 64 bits (|.| < 2^56),
-// plus the signed carry out of limb j-1.
+// plus the signed carry out of limb j-1.  The sums are loaded sixteen at a time
+// (four limbs), so that more loads are in flight.
 template <int NL32>
 __device__ __forceinline__ void fuse_w8(uint32_t (&U)[NL32], const int32_t *p, int64_t plane,
                                         int D) {
@@ -79,15 +80,16 @@ __device__ __forceinline__ void fuse_w8(uint32_t (&U)[NL32], const int32_t *p, i
   const int32_t *last = p + (int64_t)(D - 1) * plane;   // s_{D-1}, weight 2^0
   int64_t R = 0;
 #pragma unroll
-  for (int j = 0; j < NL32; j += 2) {
-    int32_t s[8];
+  for (int j = 0; j < NL32; j += 4) {
+    int32_t s[16];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 16; ++k) {
       const int u = 4 * j + k;                            // s_{D-1-u}, weight 2^(8u)
-      s[k] = u < D ? last[-(int64_t)u * plane] : 0;
+      s[k] = (u < D && j + k / 4 < NL32) ? last[-(int64_t)u * plane] : 0;
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
+      if (j + h >= NL32) break;
       int64_t V = s[4 * h + 3];
       V = V * 256 + s[4 * h + 2];
       V = V * 256 + s[4 * h + 1];
