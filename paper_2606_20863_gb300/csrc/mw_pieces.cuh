@@ -9,6 +9,7 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include "mw_column.cuh"
 #include "mw_device.cuh"
 
 namespace mw {
@@ -216,7 +217,7 @@ template <typename Out>
 __device__ __forceinline__ Out to_out(int d);
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(int d) {
-  return __float2bfloat16_rn((float)d);  // |d| <= 2^(w-1) <= 256: exact
+  return __ushort_as_bfloat16(small_int_bf16(d));  // |d| <= 2^(w-1) <= 256: exact
 }
 template <>
 __device__ __forceinline__ double to_out<double>(int d) { return (double)d; }
@@ -225,10 +226,8 @@ template <typename Out>
 __device__ __forceinline__ void store2(Out *p, int d0, int d1);
 template <>
 __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16 *p, int d0, int d1) {
-  __nv_bfloat162 v;
-  v.x = to_out<__nv_bfloat16>(d0);
-  v.y = to_out<__nv_bfloat16>(d1);
-  *reinterpret_cast<__nv_bfloat162 *>(p) = v;
+  *reinterpret_cast<uint32_t *>(p) =
+      (uint32_t)small_int_bf16(d0) | ((uint32_t)small_int_bf16(d1) << 16);
 }
 template <>
 __device__ __forceinline__ void store2<double>(double *p, int d0, int d1) {
