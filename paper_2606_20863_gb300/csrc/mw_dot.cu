@@ -4,7 +4,9 @@
 //
 // An inner product has no operand reuse, so the products of pieces run on the
 // integer units instead of the tensor cores: one CTA per inner product,
-//   1. the shared exponents E_a, E_b of the two vectors (block reduction);
+//   1. the shared exponents E_a, E_b of the two vectors (block reduction over
+//      the leading words; the cut checks them against every word and cuts
+//      again in the rare case of input that is not normalised);
 //   2. every entry cut into S balanced digits of w = 24 bits (|d| <= 2^23) on
 //      the fixed-point grid below 2^E, as for the matrix product (m >= 8:
 //      through a shared-memory column of 24-bit slots, cut_column);
@@ -53,19 +55,17 @@ __host__ __device__ constexpr uint64_t dot_bias(int limb) {
 }
 
 // Balanced digits d[p] (p = 0 most significant) of the NL-limb fixed-point
-// value T in [-2^(wS-1), 2^(wS-1)) (checked: MW_ERANGE), w = 24: with 2^23 added
-// to every low digit the digits are 24-bit fields minus 2^23; the top digit is
-// the signed value above them.
+// value T, w = 24: with 2^23 added to every low digit the digits are 24-bit
+// fields minus 2^23; the top digit is the signed value above them.  Returns
+// false when T lies outside [-2^(wS-1), 2^(wS-1)).
 template <int S, int NL>
-__device__ __forceinline__ void dot_digits(uint64_t (&T)[NL], int32_t (&d)[S],
-                                           unsigned int *status) {
+__device__ __forceinline__ bool dot_digits(uint64_t (&T)[NL], int32_t (&d)[S]) {
   constexpr int b = kDotW * S - 1, lb = b >> 6, ob = b & 63;
   static_assert(lb < NL, "limbs cover the digits");
   const int64_t v = (int64_t)T[lb] >> ob;
   bool ok = v == 0 || v == -1;
 #pragma unroll
   for (int i = lb + 1; i < NL; ++i) ok &= T[i] == (uint64_t)v;
-  if (!ok) raise_status(status, MW_ERANGE);
   uint64_t H[NL];
 #pragma unroll
   for (int i = 0; i < NL; ++i) H[i] = dot_bias<S>(i);
@@ -83,6 +83,7 @@ __device__ __forceinline__ void dot_digits(uint64_t (&T)[NL], int32_t (&d)[S],
       d[0] = (int32_t)top;
     }
   }
+  return ok;
 }
 
 // 8-byte asynchronous copy global -> shared (completion by commit groups)
@@ -130,6 +131,9 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
   __shared__ uint64_t red_lo[kDotThreads / 32][DC];
   __shared__ int64_t red_hi[kDotThreads / 32][DC];
   __shared__ int exps[2];
+  // [0]: cut again with the exponents over all words; [1]: a non-finite word;
+  // [2]: an entry outside the range of its digits (raised after the last cut)
+  __shared__ int red_flag[3];
   __shared__ uint32_t rcol[2 * NLF];   // the fusing thread's limbs
   extern __shared__ double stage[];   // [2 buffers][2 MW words][kDotThreads], then for
                                       // m >= 8 the threads' digit columns
@@ -141,53 +145,39 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
     for (int c = 0; c < S + 3; ++c) dcol[c * kDotThreads] = 0u;   // cut_column leaves it zero
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int D = a.D;
+  if (tid == 0) red_flag[0] = red_flag[1] = red_flag[2] = 0;
+  __syncthreads();
   for (int64_t i = blockIdx.x; i < a.count; i += gridDim.x) {
     const double *pa = a.A + i * a.lda;
     const double *pb = a.B + i * a.ldb;
-    // 1. shared exponents (ilogb + 1 of the largest word) and spreads
-    int ea = kExpZero, eb = kExpZero, na = -kExpZero, nb = -kExpZero;
-    bool nonfinite = false;
+    // 1. shared exponents from the leading words (an m-double's largest word is
+    // its first), one read of 1/m of the data
+    int ea = kExpZero, eb = kExpZero;
     for (int64_t k = tid; k < a.K; k += kDotThreads) {
-      int xa = kExpZero, xb = kExpZero;
-#pragma unroll
-      for (int j = 0; j < MW; ++j) {
-        const int u = exp_plus1(pa[j * a.psa + k]), v = exp_plus1(pb[j * a.psb + k]);
-        if (u == kExpNonFinite || v == kExpNonFinite) nonfinite = true;
-        if (u != kExpNonFinite) xa = max(xa, u);
-        if (v != kExpNonFinite) xb = max(xb, v);
-      }
-      if (xa != kExpZero) { ea = max(ea, xa); na = min(na, xa); }
-      if (xb != kExpZero) { eb = max(eb, xb); nb = min(nb, xb); }
+      const int u = exp_plus1(pa[k]), v = exp_plus1(pb[k]);
+      if (u != kExpNonFinite) ea = max(ea, u);
+      if (v != kExpNonFinite) eb = max(eb, v);
     }
-    if (nonfinite) raise_status(a.status, MW_ENONFINITE);
     for (int o = 16; o; o >>= 1) {
       ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
       eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
-      na = min(na, __shfl_xor_sync(0xffffffffu, na, o));
-      nb = min(nb, __shfl_xor_sync(0xffffffffu, nb, o));
     }
-    if (lane == 0) {
-      red_i[0][warp] = ea; red_i[1][warp] = eb; red_i[2][warp] = na; red_i[3][warp] = nb;
-    }
+    if (lane == 0) { red_i[0][warp] = ea; red_i[1][warp] = eb; }
     __syncthreads();
     if (tid == 0) {
       for (int w = 1; w < kDotThreads / 32; ++w) {
-        ea = max(ea, red_i[0][w]); eb = max(eb, red_i[1][w]);
-        na = min(na, red_i[2][w]); nb = min(nb, red_i[3][w]);
+        ea = max(ea, red_i[0][w]);
+        eb = max(eb, red_i[1][w]);
       }
-      const int sa = ea == kExpZero ? 0 : ea - na, sb = eb == kExpZero ? 0 : eb - nb;
-      if ((a.range_A >= 0 && sa > a.range_A) || (a.range_B >= 0 && sb > a.range_B))
-        raise_status(a.status, MW_WRANGE);
       exps[0] = ea == kExpZero ? 0 : ea;
       exps[1] = eb == kExpZero ? 0 : eb;
     }
     __syncthreads();
-    const int Ea = exps[0], Eb = exps[1];
-    const int Fa = kDotW * S - 2 - Ea, Fb = kDotW * S - 2 - Eb;
-    // 2.-3. digits and this thread's diagonal sums
+    // 2.-3. digits and this thread's diagonal sums.  The cut reads every word
+    // and also finds the exponents over all words (ilogb + 1 of an entry's
+    // largest word, as defined); where a later word exceeds the leading words'
+    // exponent (input that is not normalised) the vectors are cut again with it.
     int64_t s[DC];
-#pragma unroll
-    for (int t = 0; t < DC; ++t) s[t] = 0;
     // the words of the next entry are copied into this thread's shared slots
     // while the current one is cut (each thread reads only what it copied)
     auto slot = [&](int buf, int j) { return stage + ((buf * 2 * MW + j) * kDotThreads + tid); };
@@ -198,45 +188,102 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
         cp_async8(slot(buf, MW + j), pb + j * a.psb + k);
       }
     };
-    int buf = 0;
-    if (tid < a.K) fetch(tid, 0);
-    cp_async_commit();
-    for (int64_t k = tid; k < a.K; k += kDotThreads, buf ^= 1) {
-      if (k + kDotThreads < a.K) fetch(k + kDotThreads, buf ^ 1);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const int Ea = exps[0], Eb = exps[1];
+      const int Fa = kDotW * S - 2 - Ea, Fb = kDotW * S - 2 - Eb;
+      int xa_max = kExpZero, xb_max = kExpZero, na = -kExpZero, nb = -kExpZero;
+      bool nonfinite = false;
+#pragma unroll
+      for (int t = 0; t < DC; ++t) s[t] = 0;
+      int buf = 0;
+      if (tid < a.K) fetch(tid, 0);
       cp_async_commit();
-      cp_async_wait<1>();
-      double xa[MW], xb[MW];
+      for (int64_t k = tid; k < a.K; k += kDotThreads, buf ^= 1) {
+        if (k + kDotThreads < a.K) fetch(k + kDotThreads, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        double xa[MW], xb[MW];
+        // each entry's largest word: the largest bit pattern without the sign
+        // (the order of non-negative doubles), one exponent per entry
+        uint64_t ma = 0, mb = 0;
 #pragma unroll
-      for (int j = 0; j < MW; ++j) {
-        xa[j] = *slot(buf, j);
-        xb[j] = *slot(buf, MW + j);
-      }
-      int32_t da[S], db[S];
-      if constexpr (kColumn) {
-        bool ok = cut_column<MW, kDotW>(xa, Fa, S, dcol, kDotThreads,
-                                        [&](int k, int32_t d) { da[S - 1 - k] = d; });
-        ok &= cut_column<MW, kDotW>(xb, Fb, S, dcol, kDotThreads,
-                                    [&](int k, int32_t d) { db[S - 1 - k] = d; });
-        if (!ok) raise_status(a.status, MW_ERANGE);
-      } else {
-        {
-          uint64_t T[NL];
-          fixed_point<MW, NL>(xa, Fa, T);
-          dot_digits<S, NL>(T, da, a.status);
+        for (int j = 0; j < MW; ++j) {
+          xa[j] = *slot(buf, j);
+          xb[j] = *slot(buf, MW + j);
+          const uint64_t ua = (uint64_t)__double_as_longlong(xa[j]) & 0x7FFFFFFFFFFFFFFFull;
+          const uint64_t ub = (uint64_t)__double_as_longlong(xb[j]) & 0x7FFFFFFFFFFFFFFFull;
+          ma = ua > ma ? ua : ma;
+          mb = ub > mb ? ub : mb;
         }
-        {
-          uint64_t T[NL];
-          fixed_point<MW, NL>(xb, Fb, T);
-          dot_digits<S, NL>(T, db, a.status);
+        const int xa_e = exp_plus1(__longlong_as_double((long long)ma));
+        const int xb_e = exp_plus1(__longlong_as_double((long long)mb));
+        if (xa_e == kExpNonFinite || xb_e == kExpNonFinite) nonfinite = true;
+        if (xa_e != kExpZero && xa_e != kExpNonFinite) { xa_max = max(xa_max, xa_e); na = min(na, xa_e); }
+        if (xb_e != kExpZero && xb_e != kExpNonFinite) { xb_max = max(xb_max, xb_e); nb = min(nb, xb_e); }
+        int32_t da[S], db[S];
+        if constexpr (kColumn) {
+          bool ok = cut_column<MW, kDotW>(xa, Fa, S, dcol, kDotThreads,
+                                          [&](int k, int32_t d) { da[S - 1 - k] = d; });
+          ok &= cut_column<MW, kDotW>(xb, Fb, S, dcol, kDotThreads,
+                                      [&](int k, int32_t d) { db[S - 1 - k] = d; });
+          if (!ok) red_flag[2] = 1;
+        } else {
+          bool ok = true;
+          {
+            uint64_t T[NL];
+            fixed_point<MW, NL>(xa, Fa, T);
+            ok &= dot_digits<S, NL>(T, da);
+          }
+          {
+            uint64_t T[NL];
+            fixed_point<MW, NL>(xb, Fb, T);
+            ok &= dot_digits<S, NL>(T, db);
+          }
+          if (!ok) red_flag[2] = 1;
         }
+#pragma unroll
+        for (int p = 0; p < S; ++p)
+#pragma unroll
+          for (int q = 0; q < S; ++q)
+            if (p + q < DC && p + q < D) s[p + q] += (int64_t)da[p] * (int64_t)db[q];
       }
-#pragma unroll
-      for (int p = 0; p < S; ++p)
-#pragma unroll
-        for (int q = 0; q < S; ++q)
-          if (p + q < DC && p + q < D) s[p + q] += (int64_t)da[p] * (int64_t)db[q];
+      cp_async_wait<0>();
+      // exponents over all words: the same as the leading words' for normalised
+      // input; otherwise cut again (at most once: the second pass uses them)
+      for (int o = 16; o; o >>= 1) {
+        xa_max = max(xa_max, __shfl_xor_sync(0xffffffffu, xa_max, o));
+        xb_max = max(xb_max, __shfl_xor_sync(0xffffffffu, xb_max, o));
+        na = min(na, __shfl_xor_sync(0xffffffffu, na, o));
+        nb = min(nb, __shfl_xor_sync(0xffffffffu, nb, o));
+      }
+      if (lane == 0) {
+        red_i[0][warp] = xa_max; red_i[1][warp] = xb_max; red_i[2][warp] = na; red_i[3][warp] = nb;
+      }
+      if (nonfinite) red_flag[1] = 1;
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < kDotThreads / 32; ++w) {
+          xa_max = max(xa_max, red_i[0][w]); xb_max = max(xb_max, red_i[1][w]);
+          na = min(na, red_i[2][w]); nb = min(nb, red_i[3][w]);
+        }
+        const int Ta = xa_max == kExpZero ? 0 : xa_max, Tb = xb_max == kExpZero ? 0 : xb_max;
+        const bool again = attempt == 0 && (Ta != Ea || Tb != Eb);
+        red_flag[0] = again ? 1 : 0;
+        if (!again) {
+          const int sa = xa_max == kExpZero ? 0 : xa_max - na;
+          const int sb = xb_max == kExpZero ? 0 : xb_max - nb;
+          if ((a.range_A >= 0 && sa > a.range_A) || (a.range_B >= 0 && sb > a.range_B))
+            raise_status(a.status, MW_WRANGE);
+          if (red_flag[1]) raise_status(a.status, MW_ENONFINITE);
+          if (red_flag[2]) raise_status(a.status, MW_ERANGE);
+        }
+        red_flag[1] = red_flag[2] = 0;      // every thread set its flags before the barrier
+        exps[0] = Ta;
+        exps[1] = Tb;
+      }
+      __syncthreads();
+      if (red_flag[0] == 0) break;          // read by every thread before tid 0 writes it again
     }
-    cp_async_wait<0>();
     // block sums in 128 bits
 #pragma unroll
     for (int t = 0; t < DC; ++t) {
@@ -270,7 +317,9 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
       to_limbs32<NLF>(X, U);
       double *c = a.C + i;
       const int64_t psc = a.psc;
-      round_column<MW, 2 * NLF>(U, rcol, 1, Ea + Eb + 4 - kDotW * (D + 1),
+      // exps: the exponents of the last cut (the same on both cuts but for input
+      // that is not normalised)
+      round_column<MW, 2 * NLF>(U, rcol, 1, exps[0] + exps[1] + 4 - kDotW * (D + 1),
                                 [&](int k, double v) { c[k * psc] = v; });
     }
     __syncthreads();

@@ -63,6 +63,22 @@ def test_dot_hexa_double(mw, cuda, count, K, kind):
     check_dots(mw, cuda, A, B)
 
 
+@pytest.mark.parametrize("m", [2, 4, 8, 16])
+def test_dot_words_not_normalised(mw, cuda, m):
+    """Entries whose later word is larger than the first (input that is not
+    normalised): the shared exponent is still ilogb + 1 of the largest word of
+    any entry, so the vectors are cut again with it; bit-exact vs the oracle."""
+    rng = SplitMix64(770 + m)
+    A, B = operands("uniform", rng, m, 3, 50)
+    A[0, 1, 7] = 0.0
+    A[1, 1, 7] = 4.0                    # leading word zero, the second 4
+    A[0, 2, 3] = 1e-3
+    A[m - 1, 2, 3] = 8.0                # the last word far above the first
+    B[0, 0, 9] = 0.0
+    B[1, 0, 9] = -16.0
+    check_dots(mw, cuda, A, B)
+
+
 def test_dot_edge_cases(mw, cuda):
     """Zero vectors, one nonzero entry, exact cancellation, a tie."""
     m, K = 4, 5
