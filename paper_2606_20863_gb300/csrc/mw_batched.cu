@@ -245,12 +245,17 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
     const BInfo &b = info[i];
     const int64_t r = task - b.eA, K = b.K;
     const double *base = b.A + r * b.lda;
+    // 1. the shared exponent.  Column cuts (m >= 8) take it from the leading
+    //    words (1/m of the data) and the cut below checks it against every
+    //    word; the spread measurement and the other cutters read every word.
+    const bool lead = kColumn && !exps_only;
     int emax = kExpZero, emin = -kExpZero;
     bool nonfinite = false;
     for (int64_t k = lane; k < K; k += 32) {
       int e = kExpZero;
 #pragma unroll
       for (int j = 0; j < MW; ++j) {
+        if (lead && j > 0) break;
         const int x = exp_plus1(base[j * b.psa + k]);
         if (x == kExpNonFinite) nonfinite = true;
         else e = max(e, x);
@@ -261,43 +266,77 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
       emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
       emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
     }
-    if (nonfinite) raise_status(status, MW_ENONFINITE);
-    const int E = emax == kExpZero ? 0 : emax;
-    const int sp = emax == kExpZero ? 0 : emax - emin;
-    if (lane == 0) {
-      eA[task] = E;
-      spA[task] = sp;
-      atomicMax(max_spread, sp);
-      if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
-    }
+    int E = emax == kExpZero ? 0 : emax;
+    auto finish = [&](int Ef, int sp, bool nonfin) {   // exponent, spread and flags of the row
+      if (nonfin) raise_status(status, MW_ENONFINITE);
+      if (lane == 0) {
+        eA[task] = Ef;
+        spA[task] = sp;
+        atomicMax(max_spread, sp);
+        if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
+      }
+    };
+    if (!lead) finish(E, emax == kExpZero ? 0 : emax - emin, nonfinite);
     if (exps_only) continue;
     __nv_bfloat16 *dst = pieceA + (b.rowA + r) * Kpitch;
     const int64_t plane = b.M * Kpitch;
-    const int F = w * S - 2 - E;
     const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
     const int64_t Kp = (K + 63) & ~(int64_t)63;
-    for (int64_t k = lane; k < Kp; k += 32) {
-      if (k >= K) {  // zero padding: no arithmetic
-        __nv_bfloat16 *q = dst + k;
-        for (int p = 0; p < S; ++p, q += plane) *q = zero;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const int F = w * S - 2 - E;
+      int tmax = kExpZero, tmin = -kExpZero;       // entry exponents over every word
+      bool tnonfinite = false, out_of_range = false;
+      for (int64_t k = lane; k < Kp; k += 32) {
+        if (k >= K) {  // zero padding: no arithmetic
+          if (attempt == 0) {
+            __nv_bfloat16 *q = dst + k;
+            for (int p = 0; p < S; ++p, q += plane) *q = zero;
+          }
+          continue;
+        }
+        double x[MW];
+#pragma unroll
+        for (int j = 0; j < MW; ++j) x[j] = base[j * b.psa + k];
+        if constexpr (kColumn) {
+          // the entry's largest word: the largest bit pattern without the sign
+          uint64_t mx = 0;
+#pragma unroll
+          for (int j = 0; j < MW; ++j) {
+            const uint64_t u = (uint64_t)__double_as_longlong(x[j]) & 0x7FFFFFFFFFFFFFFFull;
+            mx = u > mx ? u : mx;
+          }
+          const int xe = exp_plus1(__longlong_as_double((long long)mx));
+          if (xe == kExpNonFinite) tnonfinite = true;
+          else if (xe != kExpZero) { tmax = max(tmax, xe); tmin = min(tmin, xe); }
+          // digits from the least significant (piece S-1) up
+          uint16_t *q = reinterpret_cast<uint16_t *>(dst + k) + (int64_t)(S - 1) * plane;
+          if (!cut_column<MW, 8>(x, F, S, &slots[0][threadIdx.x], 256, [&](int, int32_t d) {
+                *q = small_int_bf16(d);
+                q -= plane;
+              }))
+            out_of_range = true;
+        } else if constexpr (W8) {
+          cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst + k, plane, status);
+        } else {
+          cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst + k, plane, status);
+        }
+      }
+      if (!lead) break;
+      // the exponent over every word: the leading words' one for normalised
+      // input; otherwise the row is cut again with it
+      for (int o = 16; o; o >>= 1) {
+        tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+      }
+      const int Et = tmax == kExpZero ? 0 : tmax;
+      if (Et != E && attempt == 0) {
+        E = Et;
         continue;
       }
-      double x[MW];
-#pragma unroll
-      for (int j = 0; j < MW; ++j) x[j] = base[j * b.psa + k];
-      if constexpr (kColumn) {
-        // digits from the least significant (piece S-1) up
-        uint16_t *q = reinterpret_cast<uint16_t *>(dst + k) + (int64_t)(S - 1) * plane;
-        if (!cut_column<MW, 8>(x, F, S, &slots[0][threadIdx.x], 256, [&](int, int32_t d) {
-              *q = small_int_bf16(d);
-              q -= plane;
-            }))
-          raise_status(status, MW_ERANGE);
-      } else if constexpr (W8) {
-        cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst + k, plane, status);
-      } else {
-        cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst + k, plane, status);
-      }
+      if (out_of_range) raise_status(status, MW_ERANGE);
+      finish(Et, tmax == kExpZero ? 0 : tmax - tmin,
+             __any_sync(0xffffffffu, tnonfinite || nonfinite));
+      break;
     }
   }
 }
@@ -314,6 +353,7 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
   extern __shared__ double tile[];              // [MW][16 k][33], then for the column
                                                 // cut the threads' slots
   __shared__ int smax[8][32], smin[8][32], sE[32];
+  __shared__ int tmx[32], tmn[32], redo, rflag[2];   // exponents over every word, flags
   constexpr bool kColumn = W8 && MW >= 8;     // as in the row kernel
   uint32_t *slots = reinterpret_cast<uint32_t *>(tile + MW * 16 * 33) + threadIdx.x;
   if constexpr (kColumn)
@@ -325,6 +365,9 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
     const BInfo &b = info[i];
     const int64_t j0 = (task - b.stripes) * 32, K = b.K;
     const int64_t j = j0 + tx;
+    // pass 1: column cuts (m >= 8) take the exponents from the leading words and
+    // check them against every word in pass 2, as in the row kernel
+    const bool lead = kColumn && !exps_only;
     int emax = kExpZero, emin = -kExpZero;
     bool nonfinite = false;
     if (j < b.N)
@@ -333,6 +376,7 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
         int e = kExpZero;
 #pragma unroll
         for (int q = 0; q < MW; ++q) {
+          if (lead && q > 0) break;
           const int x = exp_plus1(b.B[q * b.psb + k * b.ldb + j]);
           if (x == kExpNonFinite) nonfinite = true;
           else e = max(e, x);
@@ -351,7 +395,7 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
       const int E = emax == kExpZero ? 0 : emax;
       const int sp = emax == kExpZero ? 0 : emax - emin;
       sE[tx] = E;
-      if (j < b.N) {
+      if (j < b.N && !lead) {
         eB[b.eB + j] = E;
         spB[b.eB + j] = sp;
         atomicMax(max_spread, sp);
@@ -359,9 +403,16 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
       }
     }
     __syncthreads();
-    if (!exps_only) {
+    if (!exps_only) for (int attempt = 0; attempt < 2; ++attempt) {
       const int64_t plane = b.N * Kpitch;
       const int64_t Kp = (K + 63) & ~(int64_t)63;
+      if (ty == 0) {
+        tmx[tx] = kExpZero;
+        tmn[tx] = -kExpZero;
+      }
+      if (threadIdx.x == 0) redo = rflag[0] = rflag[1] = 0;
+      // entry exponents over every word of this thread's two columns
+      int tmax[2] = {kExpZero, kExpZero}, tmin[2] = {-kExpZero, -kExpZero};
       // this thread's share of the next tile (rows ty, ty + 8), loaded while the
       // current one is cut
       double nxt[MW][2];
@@ -382,6 +433,7 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
           for (int u = 0; u < 2; ++u) tile[(q * 16 + ty + 8 * u) * 33 + tx] = nxt[q][u];
         __syncthreads();
         if (k0 + 16 < Kp) fetch(k0 + 16);
+#pragma unroll
         for (int it = 0; it < 2; ++it) {
           const int e = threadIdx.x + 256 * it;   // 512 entries per tile, k fastest
           const int jl = e >> 4, kl = e & 15;
@@ -391,27 +443,38 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
           // before slice 0 and after slice S - 1 are zero
           __nv_bfloat16 *dst = pieceB + (b.rowB + (int64_t)(b.rs - 1) * b.N + jj) * Kpitch + k;
           const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-          for (int p = 1; p < b.rs; ++p) {
-            dst[-p * plane] = zero;
-            dst[(S - 1 + p) * plane] = zero;
+          if (attempt == 0) {
+            for (int p = 1; p < b.rs; ++p) {
+              dst[-p * plane] = zero;
+              dst[(S - 1 + p) * plane] = zero;
+            }
+            if (k >= K) {
+              __nv_bfloat16 *q = dst;
+              for (int p = 0; p < S; ++p, q += plane) *q = zero;
+            }
           }
-          if (k >= K) {
-            __nv_bfloat16 *q = dst;
-            for (int p = 0; p < S; ++p, q += plane) *q = zero;
-            continue;
-          }
+          if (k >= K) continue;
           double x[MW];
 #pragma unroll
           for (int q = 0; q < MW; ++q) x[q] = tile[(q * 16 + kl) * 33 + jl];
           const int F = w * S - 2 - sE[jl];
           if constexpr (kColumn) {
+            uint64_t mx = 0;                        // the entry's largest word
+#pragma unroll
+            for (int q = 0; q < MW; ++q) {
+              const uint64_t u = (uint64_t)__double_as_longlong(x[q]) & 0x7FFFFFFFFFFFFFFFull;
+              mx = u > mx ? u : mx;
+            }
+            const int xe = exp_plus1(__longlong_as_double((long long)mx));
+            if (xe == kExpNonFinite) rflag[0] = 1;
+            else if (xe != kExpZero) { tmax[it] = max(tmax[it], xe); tmin[it] = min(tmin[it], xe); }
             // digits from the least significant (piece S-1) up
             uint16_t *q = reinterpret_cast<uint16_t *>(dst) + (int64_t)(S - 1) * plane;
             if (!cut_column<MW, 8>(x, F, S, slots, 256, [&](int, int32_t d) {
                   *q = small_int_bf16(d);
                   q -= plane;
                 }))
-              raise_status(status, MW_ERANGE);
+              rflag[1] = 1;
           } else if constexpr (W8) {
             cut_one_w8<MW, NL, __nv_bfloat16>(x, F, S, dst, plane, status);
           } else {
@@ -420,6 +483,39 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
         }
         __syncthreads();
       }
+      if (!lead) break;
+      // exponents over every word against the leading words' (normalised input:
+      // equal; otherwise the stripe is cut again with them)
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int jl = (threadIdx.x >> 4) + 16 * it;
+        atomicMax(&tmx[jl], tmax[it]);
+        atomicMin(&tmn[jl], tmin[it]);
+      }
+      __syncthreads();
+      if (ty == 0) {
+        const int Et = tmx[tx] == kExpZero ? 0 : tmx[tx];
+        if (j < b.N && Et != sE[tx]) redo = 1;
+      }
+      __syncthreads();
+      if (redo && attempt == 0) {
+        if (ty == 0) sE[tx] = tmx[tx] == kExpZero ? 0 : tmx[tx];
+        __syncthreads();
+        continue;
+      }
+      if (ty == 0 && j < b.N) {
+        const int Et = tmx[tx] == kExpZero ? 0 : tmx[tx];
+        const int sp = tmx[tx] == kExpZero ? 0 : tmx[tx] - tmn[tx];
+        eB[b.eB + j] = Et;
+        spB[b.eB + j] = sp;
+        atomicMax(max_spread, sp);
+        if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
+      }
+      if (threadIdx.x == 0) {
+        if (rflag[0]) raise_status(status, MW_ENONFINITE);
+        if (rflag[1]) raise_status(status, MW_ERANGE);
+      }
+      break;
     }
     __syncthreads();
   }

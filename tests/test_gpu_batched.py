@@ -41,6 +41,40 @@ def test_batch_of_uneven_products(mw, cuda, m):
         assert exact.ExactProduct(An, Bn, rows, cols).error_ratio(C).max() <= 1.0
 
 
+def test_batch_entries_not_normalised(mw, cuda):
+    """Octo doubles whose later word is larger than the first, in a row of A and
+    a column of B: the splits take the exponents from the leading words, find
+    the larger word while cutting and cut that row or stripe again; every
+    problem still equals the single product and the oracle bit for bit."""
+    m = 8
+    rng = SplitMix64(620)
+    shapes = [(40, 50, 30), (70, 9, 100), (9, 70, 64)]
+    As, Bs = [], []
+    for M, N, K in shapes:
+        A = uniform_mdouble(rng, m, M, K)
+        B = uniform_mdouble(rng, m, K, N)
+        A[0, 3, 5] = 0.0
+        A[1, 3, 5] = 2.0                  # row 3: leading word zero, second word 2
+        A[0, 1, 0] = 1e-3
+        A[m - 1, 1, 0] = 4.0              # row 1: the last word far above the first
+        B[0, 2, 4] = 0.0
+        B[2, 2, 4] = -8.0                 # column 4 of B
+        As.append(to_dev(A, cuda))
+        Bs.append(to_dev(B, cuda))
+    batch = mw.Batch(As, Bs)
+    Cs = batch.run()
+    mw.check_status()
+    plan = batch.plan_
+    for i, (A, B, C) in enumerate(zip(As, Bs, Cs)):
+        assert torch.equal(C, single(mw, A, B, plan)), i
+        An, Bn = A.cpu().numpy(), B.cpu().numpy()
+        M, N = An.shape[1], Bn.shape[2]
+        rows, cols = sorted({0, 1, 3, M - 1}), sorted({0, 4, N - 1})
+        sp = slicing.SlicedProduct(An, Bn, plan.w, plan.S_A, plan.S_B, plan.D, rows=rows, cols=cols)
+        assert sp.A.in_range and sp.B.in_range
+        assert np.array_equal(C.cpu().numpy()[:, rows][:, :, cols], sp.result()), i
+
+
 def test_packed_batch_equals_list_batch(mw, cuda):
     """Batch.packed (descriptors from flat tensors, no per-problem loop) gives
     the same words as the list form, with rectangular problems at offsets."""
