@@ -316,6 +316,54 @@ def count_pairs(plan):
     return sum(1 for t in range(plan.D) for p in range(plan.S_A) if 0 <= t - p < plan.S_B)
 
 
+def e2e_pipelined(torch, steps, h_in, compute):
+    """End to end through the public call, as a stream of steps would run:
+    step i's pinned host inputs are copied in on one stream and its results
+    copied out to pinned host buffers on another while the GPU computes the
+    step before or after it (two device buffers of each input, ordered by
+    events).  Every step's copies and its call lie inside the timed region.
+    compute(device inputs) -> list of device outputs.  Two untimed steps first
+    (one per buffer, so that no allocation falls in the timed steps); returns
+    seconds per timed step."""
+    cur = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    d_in = [[torch.empty(h.shape, dtype=h.dtype, device=cur.device) for h in h_in] for _ in range(2)]
+    ev_in, ev_comp, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+    h_out = [None, None]
+    used = [False, False]
+    t0 = None
+    for i in range(steps + 2):
+        if i == 2:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        k = i % 2
+        with torch.cuda.stream(s_in):
+            if used[k]:
+                s_in.wait_event(ev_comp[k])          # step i-2 has read this buffer
+            for d, h in zip(d_in[k], h_in):
+                d.copy_(h, non_blocking=True)
+            ev_in[k].record(s_in)
+        cur.wait_event(ev_in[k])
+        outs = compute(d_in[k])
+        ev_comp[k].record(cur)
+        if h_out[0] is None:                          # pinned buffers before the timed steps
+            h_out = [[torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+                     for _ in range(2)]
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_comp[k])
+            for h, o in zip(h_out[k], outs):
+                o.record_stream(s_out)
+                h.copy_(o, non_blocking=True)
+            ev_out[k].record(s_out)
+        used[k] = True
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / steps
+
+
+E2E_HOW = ("pinned host inputs copied in and results copied out every step, on two copy "
+           "streams overlapping the neighbouring steps' compute (two steps in flight)")
+
+
 def run_single(args, name, mw, torch, dist, rank, world, dev):
     m, n, _, desc = WORKLOADS[name]
     A, B = single_inputs(name)
@@ -376,21 +424,13 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
     if e2e_steps > 0:
         hA = torch.from_numpy(A).pin_memory()
         hB = torch.from_numpy(B).pin_memory()
-        hC = torch.empty((m, M, N), dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(e2e_steps + 1):          # the first run is an untimed warm-up
-            if i == 1:
-                t0 = time.perf_counter()
-            dA = hA.to(dev, non_blocking=True)
-            dB = hB.to(dev, non_blocking=True)
-            out = mw.mw_gemm(dA, dB, mode="ozaki", check=False)  # plans from the data (synchronizes)
-            hC.copy_(out, non_blocking=True)
-            torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        # mw_gemm plans from the data (exponent spreads measured on the device,
+        # synchronizing the compute stream only)
+        e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB],
+                              lambda d: [mw.mw_gemm(d[0], d[1], mode="ozaki", check=False)])
         e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
-               "d2h_bytes_per_step": int(hC.numel() * 8)}
+               "d2h_bytes_per_step": int(m * M * N * 8), "how": E2E_HOW}
 
     kern_s = statistics.mean(kern_ms) / 1e3
     fp64_peak, int8_peak = measure_pipes(torch, dev)
@@ -477,23 +517,15 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
         del batch, g, dC
         hA = torch.from_numpy(FA).pin_memory()
         hB = torch.from_numpy(FB).pin_memory()
-        hC = torch.empty((8, total), dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(e2e_steps + 1):          # the first run is an untimed warm-up
-            if i == 1:
-                t0 = time.perf_counter()
-            eA = hA.to(dev, non_blocking=True)
-            eB = hB.to(dev, non_blocking=True)
+
+        def batch_call(d):
             eC = torch.empty((8, total), dtype=torch.float64, device=dev)
-            eb = mw.Batch.packed(eA, eB, eC, shapes, offsets)
-            eb.run()
-            hC.copy_(eC, non_blocking=True)
-            torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+            mw.Batch.packed(d[0], d[1], eC, shapes, offsets).run()
+            return [eC]
+        e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB], batch_call)
         e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
-               "d2h_bytes_per_step": int(hC.numel() * 8)}
+               "d2h_bytes_per_step": int(8 * total * 8), "how": E2E_HOW}
         mw.check_status()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
@@ -577,28 +609,18 @@ def run_adjoint(args, mw, torch, dist, rank, world, dev):
     e2e = None
     if e2e_steps > 0:
         hA, hB, hW = (torch.from_numpy(x).pin_memory() for x in (A, B, Wm))
-        hgA = torch.empty_like(hA).pin_memory()
-        hgB = torch.empty_like(hB).pin_memory()
-        hL = torch.empty((m,), dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(e2e_steps + 1):          # the first run is an untimed warm-up
-            if i == 1:
-                t0 = time.perf_counter()
-            a = hA.to(dev, non_blocking=True).requires_grad_(True)
-            b = hB.to(dev, non_blocking=True).requires_grad_(True)
-            w = hW.to(dev, non_blocking=True)
+
+        def train_step(d):
+            a = d[0].detach().requires_grad_(True)     # fresh leaves every step
+            b = d[1].detach().requires_grad_(True)
             Cg = mw.MWGemm.apply(a, b)
-            loss = (Cg * w).sum(dim=(1, 2))        # per-plane sums: the loss's m words
+            loss = (Cg * d[2]).sum(dim=(1, 2))       # per-plane sums: the loss's m words
             loss.sum().backward()
-            hL.copy_(loss.detach(), non_blocking=True)
-            hgA.copy_(a.grad, non_blocking=True)
-            hgB.copy_(b.grad, non_blocking=True)
-            torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+            return [loss.detach(), a.grad, b.grad]
+        e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB, hW], train_step)
         e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": int((hA.numel() + hB.numel() + hW.numel()) * 8),
-               "d2h_bytes_per_step": int((hL.numel() + hgA.numel() + hgB.numel()) * 8)}
+               "d2h_bytes_per_step": int((m + hA.numel() + hB.numel()) * 8), "how": E2E_HOW}
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
@@ -676,21 +698,12 @@ def run_table2(args, mw, torch, dist, rank, world, dev):
     e2e = None
     if e2e_steps > 0:
         hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
-        hC = torch.empty((m, count), dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(e2e_steps + 1):          # the first run is an untimed warm-up
-            if i == 1:
-                t0 = time.perf_counter()
-            eA = hA.to(dev, non_blocking=True)
-            eB = hB.to(dev, non_blocking=True)
-            out = mw.mw_dot_batched(eA, eB, check=False)   # plans from the data (synchronizes)
-            hC.copy_(out, non_blocking=True)
-            torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        # mw_dot_batched plans from the data (synchronizing the compute stream only)
+        e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB],
+                              lambda d: [mw.mw_dot_batched(d[0], d[1], check=False)])
         e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
-               "d2h_bytes_per_step": int(hC.numel() * 8)}
+               "d2h_bytes_per_step": int(m * count * 8), "how": E2E_HOW}
         mw.check_status()
     ordinary, vectorized = PAPER_TABLE2_MS[m]
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
