@@ -188,7 +188,10 @@ int mw_gemm_noalloc(const mw_plan *plan, int transA, int transB, int64_t M, int6
  * plan's exponent spreads.  a_i is row i of A (count x K, m planes, row stride
  * lda, plane stride plane_stride_a), b_i row i of B (likewise); c_i is entry i
  * of every plane of C (plane stride plane_stride_c).  One CTA per inner product;
- * no workspace, asynchronous.  MW_EINVAL for a plan of another form or bad
+ * no workspace, asynchronous.  The shared exponent of a vector (ilogb + 1 of
+ * its largest word) is found from the leading words and checked against every
+ * word while cutting; a vector whose later word is larger (input that is not
+ * normalised) is cut a second time.  MW_EINVAL for a plan of another form or bad
  * arguments, MW_EUNSUPPORTED for piece counts the kernel is not compiled for;
  * device status bits as for mw_gemm. */
 int mw_dot_batched(const mw_plan *plan, int64_t count, int64_t K, const double *A, int64_t lda,
