@@ -171,3 +171,60 @@ def test_planner_meets_bound_on_the_oracle(mw, m, mode, lo, hi):
     assert sp.A.in_range and sp.B.in_range
     ratio = exact.exact_product_full(A, B).error_ratio(sp.result())
     assert ratio.max() <= 1.0
+
+
+# ---- batches, host side (no GPU memory is touched) --------------------------------------
+
+def _describe(mw, shapes):
+    arr = np.ascontiguousarray(np.array(shapes, dtype=np.int64).reshape(-1, 3))
+    b = mw.mw_batch()
+    rc = mw._lib.mw_batch_describe(len(shapes), arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   ctypes.byref(b))
+    return rc, b
+
+
+def _ozaki_plan(mw, m, S=56, D=60):
+    p = mw.mw_plan()
+    p.m, p.mode, p.w, p.S_A, p.S_B, p.D, p.group, p.chunk = m, mw.MW_OZAKI, 8, S, S, D, 5, 256
+    p.range_A = p.range_B = -1
+    return p
+
+
+def test_batch_describe_sums(mw):
+    rc, b = _describe(mw, [(3, 5, 7), (128, 1, 64), (1, 90, 2)])
+    assert rc == mw.MW_OK
+    assert (b.count, b.sum_M, b.sum_N, b.sum_MN) == (3, 132, 96, 3 * 5 + 128 + 90)
+    assert (b.max_M, b.max_N, b.min_K, b.max_K) == (128, 90, 2, 64)
+    rc, _ = _describe(mw, [(3, 0, 7)])
+    assert rc == mw.MW_EINVAL
+
+
+def test_batch_workspace_grows_and_rejects_hexa_doubles(mw):
+    small, big = _describe(mw, [(8, 8, 8)] * 10)[1], _describe(mw, [(100, 100, 100)] * 10)[1]
+    size_s, size_b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    p = _ozaki_plan(mw, 8)
+    assert mw._lib.mw_gemm_batched_workspace_size(ctypes.byref(p), ctypes.byref(small),
+                                                  ctypes.byref(size_s)) == mw.MW_OK
+    assert mw._lib.mw_gemm_batched_workspace_size(ctypes.byref(p), ctypes.byref(big),
+                                                  ctypes.byref(size_b)) == mw.MW_OK
+    # the 100^3 problems at least hold their pieces: S bf16 planes of 100 x 128 per operand
+    assert size_b.value > size_s.value and size_b.value >= 2 * 10 * 56 * 100 * 128 * 2
+    p16 = _ozaki_plan(mw, 16, S=112, D=116)
+    assert mw._lib.mw_gemm_batched_workspace_size(ctypes.byref(p16), ctypes.byref(small),
+                                                  ctypes.byref(size_s)) == mw.MW_EINVAL
+
+
+def test_batch_spread_workspace_bound(mw):
+    """mw_measure_spread_batched: below the documented workspace bound the call
+    fails with MW_ENOSPC on the host before any GPU work."""
+    shapes = [(int(n), int(n), int(n)) for n in (8, 77, 128, 33)]
+    _, b = _describe(mw, shapes)
+    bound = 8192 + 256 * b.count + 16 * (b.sum_M + b.sum_N) + b.sum_MN // 32
+    ra, rb = ctypes.c_int(0), ctypes.c_int(0)
+    fake = ctypes.c_void_p(0x1000)       # never dereferenced on the host
+    rc = mw._lib.mw_measure_spread_batched(8, ctypes.byref(b), fake, None, bound,
+                                           ctypes.byref(ra), ctypes.byref(rb), None)
+    assert rc == mw.MW_ENOSPC
+    rc = mw._lib.mw_measure_spread_batched(8, ctypes.byref(b), fake, fake, 64,
+                                           ctypes.byref(ra), ctypes.byref(rb), None)
+    assert rc == mw.MW_ENOSPC
