@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(256) lookup_tables_kernel(const BInfo *info, c
 
 // ---- 2. split ---------------------------------------------------------------------
 // Rows of the A_i: one warp per row (k contiguous, coalesced reads); the shared
-// exponent by a warp reduction, then the balanced pieces of the row.  W8: the
+// exponent by a warp reduction (for m >= 8 over the leading words, checked
+// against every word while cutting), then the balanced pieces of the row.  W8: the
 // w = 8 digit cutter (compiled alone, so the kernel's code stays small).  Columns
 // from K up to K rounded to 64 are zero; the product never reads past them.
 template <int MW, int NL, bool W8>
@@ -343,8 +344,10 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
 
 // Columns of the B_i: one CTA (32 x 8 threads) per 32-column stripe of one
 // problem.  Pass 1 reads rows of the stripe (coalesced) and reduces the column
-// exponents in shared memory; pass 2 stages 16 x 32 tiles of the stripe in
-// shared memory and cuts them so that the pieces are written k-contiguous.
+// exponents in shared memory (for m >= 8 from the leading words, checked
+// against every word in pass 2, which cuts the stripe again if a later word is
+// larger); pass 2 stages 16 x 32 tiles of the stripe in shared memory and cuts
+// them so that the pieces are written k-contiguous.
 template <int MW, int NL, bool W8>
 __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
     const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
