@@ -322,21 +322,22 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
           cut_one<MW, NL, __nv_bfloat16>(x, F, w, S, dst + k, plane, status);
         }
       }
-      if (!lead) break;
-      // the exponent over every word: the leading words' one for normalised
-      // input; otherwise the row is cut again with it
-      for (int o = 16; o; o >>= 1) {
-        tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-        tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+      if constexpr (kColumn) {   // (here lead: the spread measurement never cuts)
+        // the exponent over every word: the leading words' one for normalised
+        // input; otherwise the row is cut again with it
+        for (int o = 16; o; o >>= 1) {
+          tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+          tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+        }
+        const int Et = tmax == kExpZero ? 0 : tmax;
+        if (Et != E && attempt == 0) {
+          E = Et;
+          continue;
+        }
+        if (out_of_range) raise_status(status, MW_ERANGE);
+        finish(Et, tmax == kExpZero ? 0 : tmax - tmin,
+               __any_sync(0xffffffffu, tnonfinite || nonfinite));
       }
-      const int Et = tmax == kExpZero ? 0 : tmax;
-      if (Et != E && attempt == 0) {
-        E = Et;
-        continue;
-      }
-      if (out_of_range) raise_status(status, MW_ERANGE);
-      finish(Et, tmax == kExpZero ? 0 : tmax - tmin,
-             __any_sync(0xffffffffu, tnonfinite || nonfinite));
       break;
     }
   }
@@ -486,37 +487,38 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
         }
         __syncthreads();
       }
-      if (!lead) break;
-      // exponents over every word against the leading words' (normalised input:
-      // equal; otherwise the stripe is cut again with them)
+      if constexpr (kColumn) {   // (here lead: the spread measurement never cuts)
+        // exponents over every word against the leading words' (normalised input:
+        // equal; otherwise the stripe is cut again with them)
 #pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        const int jl = (threadIdx.x >> 4) + 16 * it;
-        atomicMax(&tmx[jl], tmax[it]);
-        atomicMin(&tmn[jl], tmin[it]);
-      }
-      __syncthreads();
-      if (ty == 0) {
-        const int Et = tmx[tx] == kExpZero ? 0 : tmx[tx];
-        if (j < b.N && Et != sE[tx]) redo = 1;
-      }
-      __syncthreads();
-      if (redo && attempt == 0) {
-        if (ty == 0) sE[tx] = tmx[tx] == kExpZero ? 0 : tmx[tx];
+        for (int it = 0; it < 2; ++it) {
+          const int jl = (threadIdx.x >> 4) + 16 * it;
+          atomicMax(&tmx[jl], tmax[it]);
+          atomicMin(&tmn[jl], tmin[it]);
+        }
         __syncthreads();
-        continue;
-      }
-      if (ty == 0 && j < b.N) {
-        const int Et = tmx[tx] == kExpZero ? 0 : tmx[tx];
-        const int sp = tmx[tx] == kExpZero ? 0 : tmx[tx] - tmn[tx];
-        eB[b.eB + j] = Et;
-        spB[b.eB + j] = sp;
-        atomicMax(max_spread, sp);
-        if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
-      }
-      if (threadIdx.x == 0) {
-        if (rflag[0]) raise_status(status, MW_ENONFINITE);
-        if (rflag[1]) raise_status(status, MW_ERANGE);
+        if (ty == 0) {
+          const int Et = tmx[tx] == kExpZero ? 0 : tmx[tx];
+          if (j < b.N && Et != sE[tx]) redo = 1;
+        }
+        __syncthreads();
+        if (redo && attempt == 0) {
+          if (ty == 0) sE[tx] = tmx[tx] == kExpZero ? 0 : tmx[tx];
+          __syncthreads();
+          continue;
+        }
+        if (ty == 0 && j < b.N) {
+          const int Et = tmx[tx] == kExpZero ? 0 : tmx[tx];
+          const int sp = tmx[tx] == kExpZero ? 0 : tmx[tx] - tmn[tx];
+          eB[b.eB + j] = Et;
+          spB[b.eB + j] = sp;
+          atomicMax(max_spread, sp);
+          if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
+        }
+        if (threadIdx.x == 0) {
+          if (rflag[0]) raise_status(status, MW_ENONFINITE);
+          if (rflag[1]) raise_status(status, MW_ERANGE);
+        }
       }
       break;
     }
