@@ -3,15 +3,18 @@
 //   add_shifted:    X += V 2^sh on an NL-limb (64-bit) two's complement integer;
 //   fuse_diagonals: X += sum_t s_t 2^(w (D-1-t)), any w, 64-bit limbs;
 //   fuse_w8:        the same sum for w = 8 straight into 32-bit limbs
-// (the rounding of X into m words is round_column in mw_column.cuh).
+// (the rounding of X into m words is round_column in mw_column.cuh).  All of it
+// compiles for the host too (checked against the oracle there).
 #pragma once
 #include <cstdint>
+
+#include "mw_column.cuh"   // MW_HD: host and device (plain integer code)
 
 namespace mw {
 namespace {
 
 template <int NL>
-__device__ __forceinline__ void add_shifted(uint64_t (&X)[NL], int64_t V, int sh) {
+MW_HD void add_shifted(uint64_t (&X)[NL], int64_t V, int sh) {
   const int li = sh >> 6, bo = sh & 63;
   const uint64_t lo = (uint64_t)V << bo;
   const uint64_t hi = bo ? (uint64_t)(V >> (64 - bo)) : (uint64_t)(V >> 63);
@@ -34,7 +37,7 @@ __device__ __forceinline__ void add_shifted(uint64_t (&X)[NL], int64_t V, int sh
 // of `group` consecutive diagonals (exact for the planner's group size) and one
 // multi-limb add per group.
 template <int NL>
-__device__ __forceinline__ void fuse_diagonals(uint64_t (&X)[NL], const int32_t *p, int64_t plane,
+MW_HD void fuse_diagonals(uint64_t (&X)[NL], const int32_t *p, int64_t plane,
                                                int D, int group, int w) {
   int64_t V = 0;
   int in_group = 0;
@@ -59,7 +62,7 @@ __device__ __forceinline__ void fuse_diagonals(uint64_t (&X)[NL], const int32_t 
 
 // The same integer as 2 NL 32-bit limbs (two's complement).
 template <int NL>
-__device__ __forceinline__ void to_limbs32(const uint64_t (&X)[NL], uint32_t (&U)[2 * NL]) {
+MW_HD void to_limbs32(const uint64_t (&X)[NL], uint32_t (&U)[2 * NL]) {
 #pragma unroll
   for (int k = 0; k < NL; ++k) {
     U[2 * k] = (uint32_t)X[k];
@@ -74,7 +77,7 @@ __device__ __forceinline__ void to_limbs32(const uint64_t (&X)[NL], uint32_t (&U
 // plus the signed carry out of limb j-1.  The sums are loaded sixteen at a time
 // (four limbs), so that more loads are in flight.
 template <int NL32>
-__device__ __forceinline__ void fuse_w8(uint32_t (&U)[NL32], const int32_t *p, int64_t plane,
+MW_HD void fuse_w8(uint32_t (&U)[NL32], const int32_t *p, int64_t plane,
                                         int D) {
   static_assert(NL32 % 2 == 0, "limbs in pairs");
   const int32_t *last = p + (int64_t)(D - 1) * plane;   // s_{D-1}, weight 2^0

@@ -7,6 +7,9 @@
 //                                  two's complement, as 8 hex digits)
 //     -> "w_0 .. w_{m-1}"            greedy words as 16 hex digits of their bits
 //   bf16 d                        -> the bfloat16 bits of the integer d (4 hex digits)
+//   fuse g n D s_0 .. s_{D-1}     (int32 diagonal sums, s_0 most significant)
+//     -> "u_0 .. u_{n-1} | v_0 .. v_{n-1}"  X = sum_t s_t 2^(8 (D-1-t)) in n 32-bit
+//        limbs by fuse_w8 and by fuse_diagonals with groups of g (two's complement)
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +19,7 @@
 #include <vector>
 
 #include "mw_column.cuh"
+#include "mw_fuse.cuh"
 
 using namespace mw;
 
@@ -78,6 +82,30 @@ static std::string round_m(int ex, int n, const std::vector<uint32_t> &u) {
   return "bad-limbs";
 }
 
+template <int NL32>
+static std::string fuse_n(int g, const std::vector<int32_t> &sv) {
+  const int D = (int)sv.size();
+  uint32_t U[NL32];
+  fuse_w8<NL32>(U, sv.data(), 1, D);
+  uint64_t X[NL32 / 2];
+  for (int i = 0; i < NL32 / 2; ++i) X[i] = 0;
+  fuse_diagonals<NL32 / 2>(X, sv.data(), 1, D, g, 8);
+  uint32_t V[NL32];
+  to_limbs32<NL32 / 2>(X, V);
+  std::ostringstream o;
+  char buf[16];
+  for (int i = 0; i < NL32; ++i) {
+    std::snprintf(buf, sizeof buf, "%08x", U[i]);
+    o << (i ? " " : "") << buf;
+  }
+  o << " |";
+  for (int i = 0; i < NL32; ++i) {
+    std::snprintf(buf, sizeof buf, "%08x", V[i]);
+    o << ' ' << buf;
+  }
+  return o.str();
+}
+
 int main() {
   std::string line;
   while (std::getline(std::cin, line)) {
@@ -113,6 +141,16 @@ int main() {
       if (m == 4) r = round_m<4>(ex, n, u);
       if (m == 8) r = round_m<8>(ex, n, u);
       if (m == 16) r = round_m<16>(ex, n, u);
+      std::cout << r << '\n';
+    } else if (op == "fuse") {
+      int g, n, D;
+      in >> g >> n >> D;
+      std::vector<int32_t> sv(D);
+      for (int t = 0; t < D; ++t) in >> sv[t];
+      std::string r = "bad-limbs";
+      if (n == 10) r = fuse_n<10>(g, sv);
+      if (n == 18) r = fuse_n<18>(g, sv);
+      if (n == 20) r = fuse_n<20>(g, sv);
       std::cout << r << '\n';
     } else if (op == "bf16") {
       int d;

@@ -1,9 +1,11 @@
 """The column arithmetic of the CUDA library (cut_column, round_column in
-csrc/mw_column.cuh), compiled for the host with g++ (tests/column_host.cpp)
-and compared with the oracle on seeded inputs: the balanced digits of
-T = sum_j trunc(x_j 2^F) (Section 2's pieces on the shared grid) and its range
-check, and the greedy round-to-nearest words of an exact integer (Section 4's
-final renormalisation).  No GPU; the device build of the same header is
+csrc/mw_column.cuh) and its fusion of diagonal sums (csrc/mw_fuse.cuh),
+compiled for the host with g++ (tests/column_host.cpp) and compared with the
+oracle on seeded inputs: the balanced digits of T = sum_j trunc(x_j 2^F)
+(Section 2's pieces on the shared grid) and its range check, the exact
+integer sum_t s_t 2^(w (D-1-t)) of the diagonal sums, and the greedy
+round-to-nearest words of an exact integer (Section 4's final
+renormalisation).  No GPU; the device build of the same header is
 checked by the GPU parity tests."""
 import math
 import os
@@ -141,3 +143,32 @@ def test_small_integers_to_bfloat16_bits(driver):
         b = struct.unpack("<I", struct.pack("<f", float(np.float32(d))))[0]
         assert b & 0xFFFF == 0
         assert int(g, 16) == b >> 16, d
+
+
+@pytest.mark.parametrize("nl32,D", [(10, 30), (18, 60), (20, 72)])
+def test_fusion_of_diagonal_sums_equals_the_oracle(driver, nl32, D):
+    """X = sum_t s_t 2^(8 (D-1-t)) for int32 sums s_t, by the four-at-a-time
+    Horner of fuse_w8 and by fuse_diagonals (groups of 1, 2, 4), against
+    slicing.fuse_integer, as nl32 two's complement 32-bit limbs."""
+    r = random.Random(nl32 * 100 + D)
+    lines, want = [], []
+    for i in range(200):
+        kind = i % 4
+        if kind == 0:
+            sv = [r.randint(-2 ** 31, 2 ** 31 - 1) for _ in range(D)]
+        elif kind == 1:
+            sv = [r.choice([-2 ** 31, 2 ** 31 - 1, -1, 0, 1]) for _ in range(D)]
+        elif kind == 2:
+            sv = [r.randint(-2 ** 20, 2 ** 20) for _ in range(D)]
+        else:
+            sv = [0] * D
+            sv[r.randrange(D)] = r.randint(-2 ** 31, 2 ** 31 - 1)
+        g = (1, 2, 4)[i % 3]
+        X = slicing.fuse_integer(sv, 8, D) % (1 << (32 * nl32))
+        lines.append(f"fuse {g} {nl32} {D} " + " ".join(str(v) for v in sv))
+        want.append(["%08x" % ((X >> (32 * k)) & 0xFFFFFFFF) for k in range(nl32)])
+    got = driver(lines)
+    for line, wv, g in zip(lines, want, got):
+        a, b = g.split("|")
+        assert a.split() == wv, line
+        assert b.split() == wv, line
