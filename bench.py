@@ -428,7 +428,7 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
         # synchronizing the compute stream only)
         e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB],
                               lambda d: [mw.mw_gemm(d[0], d[1], mode="ozaki", check=False)])
-        e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+        e2e = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
                "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
                "d2h_bytes_per_step": int(m * M * N * 8), "how": E2E_HOW}
 
@@ -523,7 +523,7 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
             mw.Batch.packed(d[0], d[1], eC, shapes, offsets).run()
             return [eC]
         e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB], batch_call)
-        e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+        e2e = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
                "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
                "d2h_bytes_per_step": int(8 * total * 8), "how": E2E_HOW}
         mw.check_status()
@@ -618,7 +618,7 @@ def run_adjoint(args, mw, torch, dist, rank, world, dev):
             loss.sum().backward()
             return [loss.detach(), a.grad, b.grad]
         e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB, hW], train_step)
-        e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+        e2e = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
                "h2d_bytes_per_step": int((hA.numel() + hB.numel() + hW.numel()) * 8),
                "d2h_bytes_per_step": int((m + hA.numel() + hB.numel()) * 8), "how": E2E_HOW}
 
@@ -701,7 +701,7 @@ def run_table2(args, mw, torch, dist, rank, world, dev):
         # mw_dot_batched plans from the data (synchronizing the compute stream only)
         e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB],
                               lambda d: [mw.mw_dot_batched(d[0], d[1], check=False)])
-        e2e = {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s",
+        e2e = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
                "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
                "d2h_bytes_per_step": int(m * count * 8), "how": E2E_HOW}
         mw.check_status()
