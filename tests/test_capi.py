@@ -87,7 +87,7 @@ def test_dot_plan_constraints(mw, m):
         mw.mw_plan_gemm(m, "dot", 4, 1, 100, 0, 0)            # one inner product per plan
 
 
-@pytest.mark.parametrize("m,lo,hi", [(2, -6, 6), (4, -20, 20), (8, -3, 3)])
+@pytest.mark.parametrize("m,lo,hi", [(2, -6, 6), (4, -20, 20), (8, -3, 3), (16, -2, 2)])
 def test_dot_planner_meets_bound_on_the_oracle(mw, m, lo, hi):
     """The MW_DOT plan from the measured spreads keeps the oracle's summation
     with 24-bit digits within the bound (one inner product of length 500)."""
@@ -149,7 +149,8 @@ def test_workspace_layout_is_consistent(mw):
 
 
 @pytest.mark.parametrize("m,mode,lo,hi", [(2, "ozaki", -20, 20), (2, "plain", -8, 8),
-                                          (4, "ozaki", -8, 8)])
+                                          (4, "ozaki", -8, 8), (8, "ozaki", -4, 4),
+                                          (16, "ozaki", -2, 2)])
 def test_planner_meets_bound_on_the_oracle(mw, m, mode, lo, hi):
     """The plan computed from the measured spreads gives errors within the bound
     when the CPU oracle carries out the method with it, including operands
