@@ -103,7 +103,9 @@ typedef struct mw_plan {
  * (2: 4..8, 4: 8..12, 8: 17..21, 16: 35..36) and D <= S + 4.
  * Returns MW_EINVAL for bad arguments, MW_EUNSUPPORTED if no plan fits the
  * exactness thresholds (e.g. K too long for MW_PLAIN) or for m = 16 with
- * MW_PLAIN. */
+ * MW_PLAIN.
+ * Cites: Section 2 (the exactness threshold on the number of summed
+ * products of pieces); the componentwise bound itself is the library's. */
 int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, int range_B,
                  mw_plan *plan);
 
@@ -129,7 +131,8 @@ int mw_split(int m, int trans, int64_t R, int64_t K, const double *X, int64_t ld
              int64_t plane_stride, int w, int S, int format, void *digits, int64_t digit_ld,
              int32_t *exps, int32_t *spread, int32_t *max_spread, int range, mw_stream_t stream);
 
-/* Bytes of device workspace mw_gemm needs for this plan and shape. */
+/* Bytes of device workspace mw_gemm needs for this plan and shape.
+ * No counterpart in the paper (device memory sizing). */
 int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K, size_t *bytes);
 
 /* Where mw_gemm keeps its intermediates inside ws, for inspection and tests:
@@ -143,7 +146,8 @@ int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
  *            int32 s_t, t < D; otherwise int64 planes g < G holding
  *            V = sum_t s_t 2^(w (t1 - t)) over the diagonals of group g,
  *            [g*group, t1 = min(D, (g+1)*group) - 1].
- * bytes = total workspace size (same as mw_gemm_workspace_size). */
+ * bytes = total workspace size (same as mw_gemm_workspace_size).
+ * No counterpart in the paper (device memory sizing). */
 int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
                              size_t offsets[4], size_t *bytes);
 
@@ -152,7 +156,9 @@ int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t 
  * (A stored K x M, B stored N x K).  plan->m words per entry in A, B and C.
  * ws: device workspace of at least mw_gemm_workspace_size() bytes; it holds the
  * pieces, the exponents and the diagonal partial sums; no memory is allocated.
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`.
+ * Cites: Section 2 (error-free summation of pieces, the s_i) and
+ * Section 4 (the matrix form, pieces of matrices on tensor cores). */
 int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, int64_t K,
             const double *A, int64_t lda, int64_t plane_stride_a,
             const double *B, int64_t ldb, int64_t plane_stride_b,
@@ -219,16 +225,19 @@ typedef struct mw_batch {
   int64_t sum_M, sum_N, sum_MN, max_M, max_N, min_K, max_K;
 } mw_batch;
 
-/* shapes: host array of count x {M, N, K}. Host only. */
+/* shapes: host array of count x {M, N, K}. Host only.
+ * No counterpart in the paper (batch bookkeeping). */
 int mw_batch_describe(int count, const int64_t *shapes, mw_batch *batch);
 
-/* Bytes of device workspace for mw_gemm_batched with this plan (MW_OZAKI). */
+/* Bytes of device workspace for mw_gemm_batched with this plan (MW_OZAKI).
+ * No counterpart in the paper (device memory sizing). */
 int mw_gemm_batched_workspace_size(const mw_plan *plan, const mw_batch *batch, size_t *bytes);
 
 /* Exponent spreads over all rows of the A_i and all columns of the B_i
  * (synchronizes); input to mw_plan_gemm for the batch.  ws: device workspace
  * of at least 8192 + 256 count + 16 (sum_M + sum_N) + sum_MN / 32 bytes
- * (MW_ENOSPC otherwise). */
+ * (MW_ENOSPC otherwise).
+ * Cites: Section 2 (the shared-exponent assumption the spreads measure). */
 int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *problems,
                               void *ws, size_t ws_bytes, int *range_A, int *range_B,
                               mw_stream_t stream);
@@ -241,13 +250,16 @@ int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *pr
  * operands, one persistent product kernel over (problem, tile, diagonal group)
  * work items, one fusion; no host synchronisation, so the call can be captured
  * in a CUDA graph and replayed while the descriptors and ws keep their
- * addresses.  For load balance order the problems by decreasing size. */
+ * addresses.  For load balance order the problems by decreasing size.
+ * Cites: Section 4 (matrix products of pieces); Section 1 (the power series
+ * that need many small products) motivates the batch. */
 int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem *problems,
                     void *ws, size_t ws_bytes, mw_stream_t stream);
 
 /* Exponent spreads (max over rows of op(A), columns of op(B)) measured on the
  * GPU; synchronizes the stream.  ws as for mw_gemm with any plan of this m
- * (only 2 * (M + N + 1) int32 are used).  Feed the results to mw_plan_gemm. */
+ * (only 2 * (M + N + 1) int32 are used).  Feed the results to mw_plan_gemm.
+ * Cites: Section 2 (the shared-exponent assumption the spreads measure). */
 int mw_measure_spread(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,
                       const double *A, int64_t lda, int64_t plane_stride_a,
                       const double *B, int64_t ldb, int64_t plane_stride_b,
@@ -257,7 +269,9 @@ int mw_measure_spread(int m, int transA, int transB, int64_t M, int64_t N, int64
  * dA = G B^T (M x K) and dB = A^T G (K x N), each computed like mw_gemm with
  * the transposes folded into the slicing.  plan_dA and plan_dB are plans of the
  * two products (shapes M x K x N and K x N x M).  ws: at least the larger of
- * their workspace sizes.  Either output may be NULL to skip it. */
+ * their workspace sizes.  Either output may be NULL to skip it.
+ * No counterpart in the paper (the adjoint); its two products are
+ * computed as mw_gemm computes C (Sections 2 and 4). */
 int mw_gemm_backward(const mw_plan *plan_dA, const mw_plan *plan_dB,
                      int64_t M, int64_t N, int64_t K,
                      const double *A, int64_t lda, int64_t plane_stride_a,
@@ -271,11 +285,13 @@ int mw_gemm_backward(const mw_plan *plan_dA, const mw_plan *plan_dB,
  * events[0] on its stream before the first launch, events[1] after the pieces
  * are cut (before the product kernel), events[2] after the product kernel and
  * events[3] after the last launch.  events are cudaEvent_t created by the caller; pass NULL (or
- * n = 0) to stop.  Process-wide setting, not thread safe. */
+ * n = 0) to stop.  Process-wide setting, not thread safe.
+ * No counterpart in the paper (profiling). */
 int mw_set_phase_events(void *const *events, int n);
 
 /* Read the device status word of the current device (synchronizes the device);
- * clear != 0 resets it to zero afterwards. */
+ * clear != 0 resets it to zero afterwards.
+ * No counterpart in the paper (error reporting). */
 int mw_get_status(int *bits, int clear);
 
 /* Message for the last host-side error of the calling thread ("" if none). */
