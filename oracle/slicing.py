@@ -45,25 +45,29 @@ from .exact import double_parts, greedy_words
 
 
 def ilogb(x: float) -> int:
-    """floor(log2 |x|) for a nonzero double."""
+    """floor(log2 |x|) for a nonzero double.
+    Section 2: the exponent a shared grid is built on."""
     return math.frexp(x)[1] - 1
 
 
 def entry_exponent(words: Sequence[float]) -> int | None:
-    """max over nonzero words of ilogb + 1, None when every word is zero."""
+    """max over nonzero words of ilogb + 1, None when every word is zero.
+    Section 2: the shared-exponent assumption, taken per row (column) over all words."""
     es = [ilogb(float(x)) + 1 for x in words if x != 0.0]
     return max(es) if es else None
 
 
 def logical(X: np.ndarray, trans: bool) -> np.ndarray:
     """Operand as (m, R, K): R the output dimension, K the reduction.
-    A (not transposed) is already (m, M, K); B (K x N) is used as B^T."""
+    A (not transposed) is already (m, M, K); B (K x N) is used as B^T.
+    Transposes as BLAS 'N'/'T' (no passage: the paper has no API)."""
     return np.ascontiguousarray(X.transpose(0, 2, 1)) if trans else X
 
 
 def row_exponents(L: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     """(E_r, range_r) for every row of a logical operand L (m, R, K).
-    range_r = E_r - min over nonzero entries of e (0 for an all-zero row)."""
+    range_r = E_r - min over nonzero entries of e (0 for an all-zero row).
+    Section 2: one shared exponent per row of op(A) (column of op(B)) and the spread from it."""
     m, R, K = L.shape
     E = np.zeros(R, dtype=np.int64)
     rng = np.zeros(R, dtype=np.int64)
@@ -77,7 +81,8 @@ def row_exponents(L: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
 
 
 def fixed_point(words: Sequence[float], F: int) -> int:
-    """sum_j trunc(x_j 2^F), each word truncated toward zero."""
+    """sum_j trunc(x_j 2^F), each word truncated toward zero.
+    Section 2: every word on the shared fixed-point grid, truncated toward zero."""
     T = 0
     for x in words:
         M, e = double_parts(float(x))
@@ -94,7 +99,8 @@ def fixed_point(words: Sequence[float], F: int) -> int:
 
 def balanced_digits(T: int, w: int, S: int) -> list[int]:
     """Digits d_0..d_{S-1} (d_0 most significant) of T in balanced base 2^w:
-    the low S-1 digits lie in [-2^(w-1), 2^(w-1)), d_0 takes what is left."""
+    the low S-1 digits lie in [-2^(w-1), 2^(w-1)), d_0 takes what is left.
+    Section 2 (Figure 1): the cut into pieces whose high bits are zero, as balanced digits."""
     half, base = 1 << (w - 1), 1 << w
     digits = [0] * S
     r = T
@@ -107,7 +113,8 @@ def balanced_digits(T: int, w: int, S: int) -> list[int]:
 
 
 def bitfield_digits(T: int, w: int, S: int) -> list[int]:
-    """Plain w-bit fields of |T| carrying T's sign (the paper's quarters)."""
+    """Plain w-bit fields of |T| carrying T's sign (the paper's quarters).
+    Section 2 (Figure 1)."""
     sgn = -1 if T < 0 else 1
     a = abs(T)
     mask = (1 << w) - 1
@@ -115,7 +122,8 @@ def bitfield_digits(T: int, w: int, S: int) -> list[int]:
 
 
 class Split:
-    """Digits of a logical operand L (m, R, K): ``digits[p, r, k]``, ``E[r]``."""
+    """Digits of a logical operand L (m, R, K): ``digits[p, r, k]``, ``E[r]``.
+    Section 2: steps 1 and 2 (shared exponent, pieces) for one operand."""
 
     def __init__(self, L: np.ndarray, w: int, S: int, rows: Sequence[int] | None = None):
         m, R, K = L.shape
@@ -140,12 +148,14 @@ class Split:
                     self.digits[p, a, k] = d[p]
 
     def digit_weight_exponent(self, a: int, p: int) -> int:
-        """Digit p of (local) row a weighs 2^(E + 2 - w(p+1))."""
+        """Digit p of (local) row a weighs 2^(E + 2 - w(p+1)).
+        Section 2: the weight of a piece on the shared grid."""
         return int(self.E[a]) + 2 - self.w * (p + 1)
 
 
 def pairs(S_A: int, S_B: int, D: int) -> list[tuple[int, int]]:
-    """Kept (p, q): p < S_A, q < S_B, p + q < D, ordered by diagonal then p."""
+    """Kept (p, q): p < S_A, q < S_B, p + q < D, ordered by diagonal then p.
+    Section 2: the products of pieces kept, by diagonal p + q."""
     return [(p, t - p) for t in range(D) for p in range(S_A) if 0 <= t - p < S_B]
 
 
@@ -173,7 +183,8 @@ def diagonal_sums(dA: np.ndarray, dB: np.ndarray, D: int) -> np.ndarray:
 
 
 def fuse_integer(s_ij: Sequence[int], w: int, D: int) -> int:
-    """X = sum_t s_t 2^(w(D-1-t))."""
+    """X = sum_t s_t 2^(w(D-1-t)).
+    Section 2: the diagonal sums s_i scaled by their weights; Section 4: added once at the end."""
     X = 0
     for t in range(D):
         X += int(s_ij[t]) << (w * (D - 1 - t))
@@ -181,12 +192,14 @@ def fuse_integer(s_ij: Sequence[int], w: int, D: int) -> int:
 
 
 def fused_value(s_ij: Sequence[int], w: int, D: int, EA: int, EB: int) -> Fraction:
+    """Section 2 and Section 4: the fused exact value with the shared exponents applied."""
     X = fuse_integer(s_ij, w, D)
     return Fraction(X) * Fraction(2) ** (EA + EB + 4 - w * (D + 1))
 
 
 def group_values(s_ij: Sequence[int], w: int, bounds: Sequence[tuple[int, int]]) -> list[int]:
-    """V_g = sum_{t=t0..t1} s_t 2^(w(t1 - t)) for each group [t0, t1] of diagonals."""
+    """V_g = sum_{t=t0..t1} s_t 2^(w(t1 - t)) for each group [t0, t1] of diagonals.
+    Section 2's diagonal sums joined in groups by Horner's rule (equal to fuse_integer on each group)."""
     out = []
     for t0, t1 in bounds:
         V = 0
@@ -198,7 +211,8 @@ def group_values(s_ij: Sequence[int], w: int, bounds: Sequence[tuple[int, int]])
 
 class SlicedProduct:
     """The whole method on a block of outputs: split A's rows and B's columns,
-    diagonal sums, exact fusion, greedy rounding to m words."""
+    diagonal sums, exact fusion, greedy rounding to m words.
+    Sections 2 and 4: the whole error-free summation on a block of outputs."""
 
     def __init__(self, A: np.ndarray, B: np.ndarray, w: int, S_A: int, S_B: int, D: int,
                  rows: Sequence[int] | None = None, cols: Sequence[int] | None = None,
@@ -212,13 +226,16 @@ class SlicedProduct:
         self.s = diagonal_sums(self.A.digits, self.B.digits, D)
 
     def value(self, a: int, b: int) -> Fraction:
+        """Sections 2 and 4: the fused exact value of one output."""
         return fused_value(self.s[:, a, b], self.w, self.D, int(self.A.E[a]), int(self.B.E[b]))
 
     def words(self, a: int, b: int) -> list[float]:
+        """Sections 2 and 4: the m words of one output."""
         return greedy_words(self.value(a, b), self.m)
 
     def result(self) -> np.ndarray:
-        """Greedy-rounded m words for the selected block, shape (m, rows, cols)."""
+        """Greedy-rounded m words for the selected block, shape (m, rows, cols).
+        Sections 2 and 4."""
         R, C = len(self.A.rows), len(self.B.rows)
         out = np.zeros((self.m, R, C))
         for a in range(R):

@@ -14,7 +14,7 @@
  *   two_prod     (Dekker, no fused multiply-add): p + e = a*b exactly, 17 flops.
  * m = 2 uses the classic double-double add (two two_sums, two fast_two_sums,
  * 20 flops, Table 1) and multiply (two_prod plus cross terms, 24 flops).
- * m = 4 and m = 8 form the exact partial products of each magnitude level
+ * m = 4, 8 and 16 form the exact partial products of each magnitude level
  * (i + j = l) with two_prod, keep the rounded products of level m, and
  * renormalise the level-ordered terms into m words by repeated bottom-up
  * two_sum sweeps, each sweep peeling off one word.

@@ -28,7 +28,8 @@ _lock = threading.Lock()
 
 
 def build(force: bool = False) -> str:
-    """Compile textbook.c into oracle/_build/libmwtextbook.so (gcc, OpenMP)."""
+    """Compile textbook.c into oracle/_build/libmwtextbook.so (gcc, OpenMP).
+    The textbook m-double arithmetic of Section 1 and Table 1, in C."""
     with _lock:
         src = os.path.join(_HERE, "textbook.c")
         if (not force and os.path.exists(_SO)
@@ -43,6 +44,7 @@ def build(force: bool = False) -> str:
 
 
 class TextbookC:
+    """Textbook m-double GEMM in C (Section 1's arithmetic, the operation counts of Table 1)."""
     def __init__(self):
         self.lib = ctypes.CDLL(build())
         i64, dp = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
@@ -57,11 +59,13 @@ class TextbookC:
         return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
     def max_threads(self) -> int:
+        """Threads the C oracle runs on (OpenMP)."""
         return self.lib.tb_max_threads()
 
     def gemm(self, A: np.ndarray, B: np.ndarray, rows: Sequence[int] | None = None,
              threads: int | None = None) -> np.ndarray:
-        """C = A B (m, M, N); only ``rows`` are computed when given (others stay 0)."""
+        """C = A B (m, M, N); only ``rows`` are computed when given (others stay 0).
+        Textbook m-double GEMM (Section 1's arithmetic, Table 1's 'ordinary' inner products)."""
         A = np.ascontiguousarray(A, dtype=np.float64)
         B = np.ascontiguousarray(B, dtype=np.float64)
         m, M, K = A.shape
@@ -75,6 +79,7 @@ class TextbookC:
         return C
 
     def op(self, name: str, a: Sequence[float], b: Sequence[float]) -> list[float]:
+        """One m-double add or multiply in C (Section 1's arithmetic)."""
         m = len(a)
         x = np.array(a, dtype=np.float64)
         y = np.array(b, dtype=np.float64)
@@ -84,7 +89,8 @@ class TextbookC:
 
 
 class Counting:
-    """The textbook algorithms in Python, counting floating-point operations."""
+    """The textbook algorithms in Python, counting floating-point operations.
+    Section 1 and Table 1."""
 
     def __init__(self):
         self.flops = 0
@@ -93,6 +99,7 @@ class Counting:
         self.flops += n
 
     def two_sum(self, a, b):
+        """Error-free sum of two doubles (Section 1's arithmetic; Table 1 counts its 6 operations)."""
         s = a + b
         bv = s - a
         av = s - bv
@@ -101,12 +108,14 @@ class Counting:
         return s, e
 
     def fast_two_sum(self, a, b):
+        """Error-free sum when |a| >= |b| (Section 1's arithmetic; 3 operations)."""
         s = a + b
         e = b - (s - a)
         self._f(3)
         return s, e
 
     def split(self, a):
+        """Dekker's split of a double into two halves (for two_prod without fused multiply-add)."""
         c = 134217729.0 * a
         hi = c - (c - a)
         lo = a - hi
@@ -114,6 +123,7 @@ class Counting:
         return hi, lo
 
     def two_prod(self, a, b):
+        """Error-free product of two doubles (Dekker; Section 1's arithmetic)."""
         p = a * b
         self._f(1)
         ah, al = self.split(a)
@@ -123,6 +133,7 @@ class Counting:
         return p, e
 
     def dd_add(self, a, b):
+        """Double double addition (Section 1; Table 1: 20 operations)."""
         s, e = self.two_sum(a[0], b[0])
         t, f = self.two_sum(a[1], b[1])
         e = e + t
@@ -134,6 +145,7 @@ class Counting:
         return [s, e]
 
     def dd_mul(self, a, b):
+        """Double double multiplication (Section 1; Table 1: 23 operations)."""
         p, e = self.two_prod(a[0], b[0])
         e = e + (a[0] * b[1] + a[1] * b[0])
         self._f(4)
@@ -141,6 +153,7 @@ class Counting:
         return [p, e]
 
     def renorm(self, x, m):
+        """Renormalisation of m + 1 words into m nonoverlapping words (Section 1's arithmetic)."""
         x = list(x)
         r = []
         for _ in range(m):
@@ -157,6 +170,7 @@ class Counting:
         return r
 
     def add(self, a, b):
+        """m-double addition (Section 1's arithmetic)."""
         m = len(a)
         if m == 2:
             return self.dd_add(a, b)
@@ -166,6 +180,7 @@ class Counting:
         return self.renorm(t, m)
 
     def mul(self, a, b):
+        """m-double multiplication (Section 1's arithmetic)."""
         m = len(a)
         if m == 2:
             return self.dd_mul(a, b)
@@ -185,6 +200,7 @@ class Counting:
         return self.renorm(t, m)
 
     def gemm(self, A: np.ndarray, B: np.ndarray) -> np.ndarray:
+        """Textbook m-double GEMM (Section 1's arithmetic, Table 1's 'ordinary' inner products)."""
         m, M, K = A.shape
         N = B.shape[2]
         C = np.zeros((m, M, N))
@@ -202,7 +218,8 @@ class Counting:
 def op_counts(m: int, trials: int = 1) -> tuple[int, int]:
     """(flops of one m-double add, flops of one m-double mul) on nonzero operands.
     The renormalisation of m >= 4 drops exact-zero terms, so its count is that
-    of generic (all terms nonzero) operands."""
+    of generic (all terms nonzero) operands.
+    Table 1: operations per m-double add and multiply."""
     from synthetic import SplitMix64, uniform_mdouble
     X = uniform_mdouble(SplitMix64(7), m, 1, 2)
     a = [float(X[j, 0, 0]) for j in range(m)]
