@@ -233,10 +233,16 @@ int mw_batch_describe(int count, const int64_t *shapes, mw_batch *batch);
  * No counterpart in the paper (device memory sizing). */
 int mw_gemm_batched_workspace_size(const mw_plan *plan, const mw_batch *batch, size_t *bytes);
 
+/* Bytes of device workspace mw_measure_spread_batched needs for this batch
+ * (host only; at most 8192 + 256 count + 16 (sum_M + sum_N) + sum_MN / 32).
+ * MW_EINVAL for m outside {2, 4, 8} or a bad batch summary.
+ * No counterpart in the paper (device memory sizing). */
+int mw_measure_spread_batched_workspace_size(int m, const mw_batch *batch, size_t *bytes);
+
 /* Exponent spreads over all rows of the A_i and all columns of the B_i
  * (synchronizes); input to mw_plan_gemm for the batch.  ws: device workspace
- * of at least 8192 + 256 count + 16 (sum_M + sum_N) + sum_MN / 32 bytes
- * (MW_ENOSPC otherwise).
+ * of at least mw_measure_spread_batched_workspace_size bytes (MW_ENOSPC
+ * otherwise).
  * Cites: Section 2 (the shared-exponent assumption the spreads measure). */
 int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *problems,
                               void *ws, size_t ws_bytes, int *range_A, int *range_B,

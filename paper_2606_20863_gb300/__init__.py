@@ -87,6 +87,8 @@ def _load():
                                            ctypes.POINTER(ctypes.c_size_t)],
         "mw_measure_spread_batched": [i32, ctypes.POINTER(mw_batch), vp, vp, ctypes.c_size_t,
                                       ip, ip, vp],
+        "mw_measure_spread_batched_workspace_size": [i32, ctypes.POINTER(mw_batch),
+                                                     ctypes.POINTER(ctypes.c_size_t)],
         "mw_gemm_batched": [pp, ctypes.POINTER(mw_batch), vp, vp, ctypes.c_size_t, vp],
         "mw_dot_batched": [pp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, vp],
         "mw_selftest_timeout": [ctypes.c_uint, vp],
@@ -107,7 +109,8 @@ EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_works
             "mw_gemm",
             "mw_measure_spread", "mw_gemm_backward", "mw_get_status", "mw_last_error",
             "mw_version", "mw_set_phase_events", "mw_gemm_noalloc", "mw_batch_describe",
-            "mw_gemm_batched_workspace_size", "mw_measure_spread_batched", "mw_gemm_batched",
+            "mw_gemm_batched_workspace_size", "mw_measure_spread_batched",
+            "mw_measure_spread_batched_workspace_size", "mw_gemm_batched",
             "mw_dot_batched", "mw_selftest_timeout")
 
 
@@ -400,8 +403,11 @@ class Batch:
     def measure_spread(self):
         """Largest exponent spreads over the batch (synchronizes)."""
         b = self.batch
-        need = 8192 + 256 * b.count + 16 * (b.sum_M + b.sum_N) + b.sum_MN // 32
-        ws = _workspace(need, self.d_problems.device)
+        need = ctypes.c_size_t(0)
+        _check(_lib.mw_measure_spread_batched_workspace_size(self.m, ctypes.byref(b),
+                                                             ctypes.byref(need)),
+               "mw_measure_spread_batched_workspace_size")
+        ws = _workspace(need.value, self.d_problems.device)
         ra, rb = ctypes.c_int(0), ctypes.c_int(0)
         _check(_lib.mw_measure_spread_batched(self.m, ctypes.byref(b),
                                               ctypes.c_void_p(self.d_problems.data_ptr()),

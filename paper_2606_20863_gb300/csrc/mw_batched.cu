@@ -738,12 +738,27 @@ int mw_gemm_batched_workspace_size(const mw_plan *plan, const mw_batch *batch, s
   return MW_OK;
 }
 
-int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *problems, void *ws,
-                              size_t ws_bytes, int *range_A, int *range_B, mw_stream_t stream) {
-  if (!range_A || !range_B || !problems) return fail(MW_EINVAL, "NULL argument");
+// The plan the spread measurement runs with: one piece, exponents only.
+static mw_plan spread_plan(int m) {
   mw_plan p{};
   p.m = m; p.mode = MW_OZAKI; p.w = 8; p.S_A = p.S_B = 1; p.D = 1; p.group = 1; p.chunk = 64;
   p.range_A = p.range_B = -1;
+  return p;
+}
+
+int mw_measure_spread_batched_workspace_size(int m, const mw_batch *batch, size_t *bytes) {
+  if (!bytes) return fail(MW_EINVAL, "bytes is NULL");
+  const mw_plan p = spread_plan(m);
+  int rc = check_batch(&p, batch);
+  if (rc) return rc;
+  *bytes = layout_of(p, *batch).pieceA;
+  return MW_OK;
+}
+
+int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *problems, void *ws,
+                              size_t ws_bytes, int *range_A, int *range_B, mw_stream_t stream) {
+  if (!range_A || !range_B || !problems) return fail(MW_EINVAL, "NULL argument");
+  const mw_plan p = spread_plan(m);
   int rc = check_batch(&p, batch);
   if (rc) return rc;
   Layout L = layout_of(p, *batch);

@@ -216,16 +216,25 @@ def test_batch_workspace_grows_and_rejects_hexa_doubles(mw):
 
 
 def test_batch_spread_workspace_bound(mw):
-    """mw_measure_spread_batched: below the documented workspace bound the call
-    fails with MW_ENOSPC on the host before any GPU work."""
-    shapes = [(int(n), int(n), int(n)) for n in (8, 77, 128, 33)]
-    _, b = _describe(mw, shapes)
-    bound = 8192 + 256 * b.count + 16 * (b.sum_M + b.sum_N) + b.sum_MN // 32
-    ra, rb = ctypes.c_int(0), ctypes.c_int(0)
-    fake = ctypes.c_void_p(0x1000)       # never dereferenced on the host
-    rc = mw._lib.mw_measure_spread_batched(8, ctypes.byref(b), fake, None, bound,
-                                           ctypes.byref(ra), ctypes.byref(rb), None)
-    assert rc == mw.MW_ENOSPC
-    rc = mw._lib.mw_measure_spread_batched(8, ctypes.byref(b), fake, fake, 64,
-                                           ctypes.byref(ra), ctypes.byref(rb), None)
-    assert rc == mw.MW_ENOSPC
+    """mw_measure_spread_batched: its workspace size stays within the bound the
+    header states, and one byte less fails with MW_ENOSPC on the host before any
+    GPU work (no GPU memory is touched)."""
+    for shapes in ([(8, 8, 8)], [(int(n), int(n), int(n)) for n in (8, 77, 128, 33)],
+                   [(1, 3000, 5), (700, 1, 2)] * 50, [(128, 128, 128)] * 2000):
+        _, b = _describe(mw, shapes)
+        size = ctypes.c_size_t(0)
+        assert mw._lib.mw_measure_spread_batched_workspace_size(
+            8, ctypes.byref(b), ctypes.byref(size)) == mw.MW_OK
+        bound = 8192 + 256 * b.count + 16 * (b.sum_M + b.sum_N) + b.sum_MN // 32
+        assert 0 < size.value <= bound
+        ra, rb = ctypes.c_int(0), ctypes.c_int(0)
+        fake = ctypes.c_void_p(0x1000)       # never dereferenced: the size check comes first
+        rc = mw._lib.mw_measure_spread_batched(8, ctypes.byref(b), fake, fake, size.value - 1,
+                                               ctypes.byref(ra), ctypes.byref(rb), None)
+        assert rc == mw.MW_ENOSPC
+        rc = mw._lib.mw_measure_spread_batched(8, ctypes.byref(b), fake, None, size.value,
+                                               ctypes.byref(ra), ctypes.byref(rb), None)
+        assert rc == mw.MW_ENOSPC
+    size = ctypes.c_size_t(0)
+    assert mw._lib.mw_measure_spread_batched_workspace_size(
+        16, ctypes.byref(b), ctypes.byref(size)) == mw.MW_EINVAL
