@@ -1,19 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the m-double matrix product on GB300.
 
-Workload: quad-double C = A B, M = N = K = 1024, every leading word of
-magnitude 2^U[-8, 8) with a random sign and lower words scaled by 2^-53 U[-1,1)
-(seed 1).  One step is the whole product through the C interface: exponents
-and pieces of both operands, the tensor-core slice products with their exact
-int64 drains, and the exact fusion into four words (MW_OZAKI).  The plain FP64
-form of the paper (MW_PLAIN) is timed on the same operands and the same error
-bound for the comparison the metric asks for.
+Default workload (the benchmark line): M = N = K = 4096, quad double and
+double double, every leading word of magnitude 2^U[-20, 20) with a random sign
+and lower words scaled by 2^-53 U[-1,1) (seed 2).  One step is the whole
+product through the C interface: exponents and pieces of both operands, the
+tensor-core products of pieces with their exact integer drains, and the exact
+fusion into m words (the Ozaki form).  `value` is the quad-double step; the
+double-double step, the plain FP64 form of the paper (MW_PLAIN) on the same
+operands and error bound, and the quad-double 1024^3 product are sub-records of
+the same line.
 
 Printed: one JSON line (rank 0).  value = m-double GFLOP/s = 2 M N K / time,
 summed over ranks (each rank a replica).  L2 is flushed (a 256 MiB write)
 before every timed step; steps are timed with CUDA events on the stream the
 library launches on.  `--impl reference` times the CPU oracle (textbook
-m-double product, all host cores) on a bounded row sample of the same workload.
+m-double product, all host cores) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -31,10 +33,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "m-double GEMM GFLOP/s (dd,qd) Ozaki-INT8 vs FP64 plain, same error bound"
-WORKLOAD = ("quad-double GEMM C=A*B, M=N=K=1024, leading words 2^U[-8,8) random sign, "
-            "lower words x2^-53 U[-1,1), seed 1")
-M_WORDS, N_DIM = 4, 1024
+HEADLINE = ("m-double GEMM C=A*B, M=N=K=4096, quad double (value) and double double, leading "
+            "words 2^U[-20,20) random sign, lower words x2^-53 U[-1,1), seed 2; Ozaki form next "
+            "to the plain FP64 form at the same error bound")
 KERNELS_PER_STEP = 8   # per operand: exponent, finalize, pieces (x2); product; combine
+WORD_NAMES = {2: "double double", 4: "quad double", 8: "octo double", 16: "hexa double"}
+
+
+def dtype_of(m, pieces="exact integer slices in bf16 on tcgen05"):
+    """The arithmetic the path computes in: an m-double result built from exact
+    integer pieces (not a reduced-precision result)."""
+    return f"f64x{m} ({WORD_NAMES[m]} result; {pieces})"
 
 
 def parse():
@@ -43,22 +52,26 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mw", choices=["mw", "reference"])
-    ap.add_argument("--plain-steps", type=int, default=2,
+    ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed runs of the plain FP64 form (0 = leave it out)")
     ap.add_argument("--e2e-steps", type=int, default=-1,
                     help="end-to-end runs from host memory (-1 = steps/4, at least 3; 0 = leave out)")
-    ap.add_argument("--cpu-rows", type=int, default=0, help="rows in the CPU sample (0 = auto)")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0,
+                    help="target seconds of each CPU oracle sample (0 = leave the CPU leg out)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-graph", action="store_true",
                     help="single products: launch each step directly instead of replaying a graph")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="headline: leave out the quad-double 1024^3 sub-record")
     ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8, 16],
                     help="table2: words per m-double (2, 4, 8 or 16)")
     ap.add_argument("--count", type=int, default=20000,
                     help="od_batch: number of products (20,000 is the benchmark; fewer for profiling)")
-    ap.add_argument("--workload", default="qd1024",
-                    choices=["qd1024", "dd4096", "qd4096", "od_batch", "adjoint", "table2"],
-                    help="qd1024 (default): the benchmark line; the others measure the other "
-                         "configurations of the method")
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "qd1024", "dd4096", "qd4096", "od_batch", "adjoint",
+                             "table2"],
+                    help="headline (default): the benchmark line, quad and double double at "
+                         "4096^3; the others measure one configuration of the method each")
     return ap.parse_args()
 
 
@@ -138,53 +151,58 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs():
-    from synthetic import qd_1024
-    return qd_1024(seed=1, n=N_DIM)
-
-
-def cpu_baseline(A, B, rows, label):
-    """The oracle's textbook m-double product on a bounded row sample."""
+def cpu_sample(A, B, target_s, label):
+    """The oracle's textbook m-double product on a bounded sample of C: a block
+    of rows (spread over A) times the first columns of B, sized from a short
+    single-thread calibration so that the sample takes about target_s seconds
+    on all host cores.  Returns the cpu_baseline record."""
     from oracle import textbook
     tc = textbook.TextbookC()
     threads = tc.max_threads()
-    sel = np.linspace(0, A.shape[1] - 1, rows).astype(np.int64)
+    m, M, K = A.shape
+    N = B.shape[2]
+    cols = min(N, 256)
+    Bs = np.ascontiguousarray(B[:, :, :cols])
     t0 = time.perf_counter()
-    tc.gemm(A, B, rows=sel, threads=threads)
+    tc.gemm(A, Bs, rows=[0], threads=1)
+    one = max(time.perf_counter() - t0, 1e-6)            # one row of `cols` outputs
+    rows = int(max(threads, min(M, target_s * threads / one)))
+    if rows >= M and cols < N:                            # the whole block is cheap: widen it
+        cols = int(min(N, cols * max(1.0, target_s * threads / (one * M))))
+        Bs = np.ascontiguousarray(B[:, :, :cols])
+        rows = M
+    sel = np.linspace(0, M - 1, rows).astype(np.int64)
+    t0 = time.perf_counter()
+    tc.gemm(A, Bs, rows=sel, threads=threads)
     dt = time.perf_counter() - t0
-    flops = 2.0 * rows * B.shape[2] * A.shape[2]
+    flops = 2.0 * rows * cols * K
     return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
-            "sample": f"{rows} of {A.shape[1]} rows of C ({label}), {dt:.2f} s"}
-
-
-def auto_rows(A, B, target_s=12.0):
-    from oracle import textbook
-    tc = textbook.TextbookC()
-    t0 = time.perf_counter()
-    tc.gemm(A, B, rows=[0], threads=1)
-    one = time.perf_counter() - t0
-    return int(max(tc.max_threads(), min(A.shape[1], target_s * tc.max_threads() / max(one, 1e-6))))
+            "sample": f"{rows} rows x {cols} columns of the {M}x{N} C ({label}, every output a "
+                      f"full K = {K} inner product), {dt:.2f} s"}
 
 
 def run_reference(args):
-    dist, rank, world = None, 0, 1
-    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
-        rank = int(os.environ.get("RANK", "0"))
-        if rank != 0:
-            return
-    A, B = make_inputs()
-    rows = args.cpu_rows or auto_rows(A, B, target_s=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
+    """The oracle's textbook product on the benchmark line's workload (quad
+    double 4096^3), every step a bounded sample of it on all host cores."""
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0:
+        return
+    import synthetic
+    A, B = synthetic.ozaki_4096(4)
+    per_step = max(1.0, 90.0 / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
-        cpu_baseline(A, B, max(1, rows // 8), "warm-up")
-    vals = [cpu_baseline(A, B, rows, "quad double") for _ in range(args.steps)]
-    dt = statistics.mean(2.0 * rows * N_DIM * N_DIM / (v["value"] * 1e9) for v in vals)
+        cpu_sample(A, B, per_step / 4, "warm-up")
+    vals = [cpu_sample(A, B, per_step, "quad double") for _ in range(args.steps)]
     value = statistics.mean(v["value"] for v in vals)
+    ms = 2.0 * 4096 ** 3 / (value * 1e9) * 1e3                  # one whole product
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": M_WORDS, "M": N_DIM, "N": N_DIM, "K": N_DIM,
-                       "form": "textbook m-double (two-sum, Dekker two-product), CPU oracle"},
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64x4 (quad double result; textbook two-sum and "
+                                          "Dekker two-product on the host)",
+            "data": "synthetic",
+            "config": {"workload": HEADLINE, "m": 4, "M": 4096, "N": 4096, "K": 4096,
+                       "form": "textbook m-double (two-sum, Dekker two-product), CPU oracle",
+                       "ms_per_step_is": "one whole 4096^3 product at the sampled rate"},
             "cpu_baseline": vals[-1],
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -193,7 +211,8 @@ def run_reference(args):
 
 WORKLOADS = {
     # name: (m, n, generator, description)
-    "qd1024": (4, 1024, "qd_1024", WORKLOAD),
+    "qd1024": (4, 1024, "qd_1024", "quad-double GEMM C=A*B, M=N=K=1024, leading words "
+               "2^U[-8,8) random sign, lower words x2^-53 U[-1,1), seed 1"),
     "dd4096": (2, 4096, "ozaki_4096", "double-double GEMM M=N=K=4096, leading words 2^U[-20,20) "
                "random sign, lower words x2^-53 U[-1,1), seed 2"),
     "qd4096": (4, 4096, "ozaki_4096", "quad-double GEMM M=N=K=4096, leading words 2^U[-20,20) "
@@ -245,12 +264,12 @@ def timed(step, steps, flush, mw, dist, dev, phase=True):
     return step_ms, kern_ms, clk
 
 
-# DRAM bytes (read + write) of one product-kernel launch, from the ncu captures
-# summarised in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), with
-# the digest of the kernel's sources at capture time: a changed kernel reports
-# no traffic until it is captured again.
+# DRAM bytes (read + write) of one product-kernel launch, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum), with the digest of the
+# kernel's sources at capture time: a changed kernel reports no traffic until it
+# is captured again.
 KERNEL_SOURCES = ("mw_ozaki.cu", "mw_tc.cuh", "mw_device.cuh", "mw_work.cuh")
-TRAFFIC = {   # profiles/dram_traffic_ozaki_kernel.md
+TRAFFIC = {
     "qd1024": {"bytes": 395363328 + 91096832, "digest": "c15848e119b2e400"},
     "dd4096": {"bytes": 47455044352 + 1611938048, "digest": "c15848e119b2e400"},
     "qd4096": {"bytes": 181198118656 + 2540828672, "digest": "c15848e119b2e400"},
@@ -266,6 +285,12 @@ def kernel_digest():
         with open(os.path.join(ROOT, "paper_2606_20863_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def workload_key(m, M, N, K):
+    """Name of a captured single-product workload, for its DRAM traffic."""
+    return {(4, 1024): "qd1024", (2, 4096): "dd4096", (4, 4096): "qd4096"}.get(
+        (m, M), None) if M == N == K else None
 
 
 def traffic_of(workload):
@@ -364,14 +389,21 @@ E2E_HOW = ("pinned host inputs copied in and results copied out every step, on t
            "streams overlapping the neighbouring steps' compute (two steps in flight)")
 
 
-def run_single(args, name, mw, torch, dist, rank, world, dev):
-    m, n, _, desc = WORKLOADS[name]
-    A, B = single_inputs(name)
+def measure_single(args, mw, torch, dist, rank, dev, A, B, workload, mode="ozaki",
+                   graph=False, plain_steps=0, e2e_steps=0, cpu_s=0.0, pipes=None):
+    """One single-product workload: the Ozaki-form step (`steps` timed runs, L2
+    flushed before each), its product-kernel time from phase events around
+    direct calls, optionally the plain FP64 form on the same operands (same
+    error bound), the end-to-end rate through the public call from pinned host
+    buffers (one plan made before the loop, as a caller with fixed-range
+    operands would), and the CPU oracle on a bounded sample.  Returns a record
+    with the device-timed value of this rank and the aggregate over ranks."""
+    m, M, K = A.shape
+    N = B.shape[2]
     tA = torch.from_numpy(A).to(dev)
     tB = torch.from_numpy(B).to(dev)
-    M = N = K = n
     flops = 2.0 * M * N * K
-    plan = mw.plan_for(tA, tB, "ozaki")
+    plan = mw.plan_for(tA, tB, mode)
     ws = torch.empty(mw.workspace_size(plan, M, N, K), dtype=torch.uint8, device=dev)
     C = torch.empty((m, M, N), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -380,21 +412,19 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
     def call():
         mw.mw_gemm(tA, tB, plan, C=C, ws=ws, check=False)
 
-    # one product call captured in a CUDA graph and replayed per step (the
-    # launches of the splits, product and fusion without host gaps)
     call()
     torch.cuda.synchronize()
     mw.check_status()
-    graph = None
-    # short steps (1024^3) lose a few percent to launch gaps; at 4096^3 direct calls
-    # measured about 2 % faster than a replayed graph
-    if not args.no_graph and n <= 1024:
-        graph = torch.cuda.CUDAGraph()
+    g = None
+    if graph:
+        # one product call captured in a CUDA graph and replayed per step (the
+        # launches of the splits, product and fusion without host gaps)
+        g = torch.cuda.CUDAGraph()
         gs = torch.cuda.Stream()
         with torch.cuda.stream(gs):
-            with torch.cuda.graph(graph, stream=gs):
+            with torch.cuda.graph(g, stream=gs):
                 call()
-    step = graph.replay if graph is not None else call
+    step = g.replay if g is not None else call
     for _ in range(args.warmup):
         step()
     mw.check_status()
@@ -405,68 +435,133 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
     # recorded inside a graph), as many runs as timed steps
     _, kern_ms, _ = timed(call, args.steps, flush, mw, None, dev)
     phases = timed.phases
+    rec = {"workload": workload, "m": m, "M": M, "N": N, "K": K, "value": value,
+           "unit": "GFLOP/s", "ms_per_step": t_step * 1e3 / args.steps,
+           "step_ms_min": min(step_ms), "product_kernel_ms": statistics.mean(kern_ms),
+           "phases_ms_direct_calls": phases, "plan": plan.as_dict(), "slice_pairs": pairs,
+           "form": "Ozaki: bf16 integer slices on tcgen05, fp32 drained to integers",
+           "launch": "one mw_gemm call captured in a CUDA graph, replayed per step"
+                     if g is not None else "direct mw_gemm calls",
+           "roofline": roofline_of(pairs, flops, kern_ms, workload_key(m, M, N, K)),
+           "clocks": clk, "gpu_launches": KERNELS_PER_STEP * args.steps}
+    del g
 
     # plain FP64 form on the same operands and bound (the comparison of the metric)
-    pplan = mw.plan_for(tA, tB, "plain")
-    plain_gflops = None
-    if args.plain_steps > 0:
+    if plain_steps > 0:
+        pplan = mw.plan_for(tA, tB, "plain")
         pws = torch.empty(mw.workspace_size(pplan, M, N, K), dtype=torch.uint8, device=dev)
         Cp = torch.empty_like(C)
-        mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws)
-        pms, _, _ = timed(lambda: mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws, check=False),
-                          args.plain_steps, flush, mw, None, dev, phase=False)
-        plain_gflops = flops * args.plain_steps / (sum(pms) / 1e3) / 1e9
+        if M * N * K <= 1024 ** 3:                 # one untimed call (4096^3 takes seconds)
+            mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws)
+        pms, _, pclk = timed(lambda: mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws, check=False),
+                             plain_steps, flush, mw, None, dev, phase=False)
+        plain = flops * plain_steps / (sum(pms) / 1e3) / 1e9
+        rec["plain"] = {"value": plain, "unit": "GFLOP/s", "steps": plain_steps,
+                        "ms_per_step": sum(pms) / plain_steps, "plan": pplan.as_dict(),
+                        "form": "MW_PLAIN: double pieces, FP64 FMA, m-double fusion",
+                        "clocks": pclk}
+        if pipes:
+            fp64_peak = pipes[0]
+            ppairs = count_pairs(pplan)
+            roof = 2.0 * fp64_peak * 1e3 / TABLE1_MUL_ADD[m]     # m-double GFLOP/s
+            rec["plain"]["roofline"] = {
+                "bound": "fp64", "peak_from_table1_gflops": roof,
+                "frac_of_table1_roofline": plain / roof,
+                "fp64_pipe_tflops": ppairs * plain / 1e3,
+                "fp64_pipe_frac": ppairs * plain / 1e3 / fp64_peak,
+                "fp64_peak_tflops_measured": fp64_peak}
+        rec["speedup_vs_plain"] = value / plain
         del pws, Cp
 
     # end to end through the public call: pinned host operands in, host result out
-    e2e_steps = args.e2e_steps if args.e2e_steps >= 0 else max(3, args.steps // 4)
-    e2e = None
     if e2e_steps > 0:
         hA = torch.from_numpy(A).pin_memory()
         hB = torch.from_numpy(B).pin_memory()
-        # mw_gemm plans from the data (exponent spreads measured on the device,
-        # synchronizing the compute stream only)
         e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB],
-                              lambda d: [mw.mw_gemm(d[0], d[1], mode="ozaki", check=False)])
-        e2e = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
-               "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
-               "d2h_bytes_per_step": int(m * M * N * 8), "how": E2E_HOW}
+                              lambda d: [mw.mw_gemm(d[0], d[1], plan, check=False)])
+        mw.check_status()
+        rec["e2e"] = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
+                      "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
+                      "d2h_bytes_per_step": int(m * M * N * 8),
+                      "how": E2E_HOW + "; the plan (slice counts) made once before the loop"}
+        del hA, hB
+    if rank == 0 and cpu_s > 0:
+        rec["cpu_baseline"] = cpu_sample(A, B, cpu_s, WORD_NAMES[m])
+    del tA, tB, ws, C, flush
+    torch.cuda.empty_cache()
+    return rec
 
-    kern_s = statistics.mean(kern_ms) / 1e3
-    fp64_peak, int8_peak = measure_pipes(torch, dev)
-    plain_roof = None
-    if plain_gflops:
-        ppairs = count_pairs(pplan)
-        roof = 2.0 * fp64_peak * 1e3 / TABLE1_MUL_ADD[m]          # GFLOP/s of m-double flops
-        plain_roof = {"bound": "fp64", "achieved": plain_gflops, "unit": "GFLOP/s",
-                      "peak_from_table1": roof, "frac_of_table1_roofline": plain_gflops / roof,
-                      "fp64_pipe_tflops": ppairs * flops * plain_gflops / flops / 1e3,
-                      "fp64_pipe_frac": ppairs * plain_gflops / 1e3 / fp64_peak,
-                      "fp64_peak_tflops_measured": fp64_peak}
-    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
-            "data": "synthetic",
-            "config": {"workload": desc, "m": m, "M": M, "N": N, "K": K,
-                       "form": "Ozaki: bf16 integer slices on tcgen05, fp32 drained to integers",
-                       "plan": plan.as_dict(), "slice_pairs": pairs,
-                       "l2": "flushed (256 MiB write) before every timed step",
-                       "launch": "direct calls" if graph is None else
-                                 "one mw_gemm call captured in a CUDA graph, replayed per step",
+
+def e2e_count(args):
+    return args.e2e_steps if args.e2e_steps >= 0 else max(3, args.steps // 4)
+
+
+def run_single(args, name, mw, torch, dist, rank, world, dev):
+    """One of the single-product workloads on its own (profiling and sweeps)."""
+    m, n, _, desc = WORKLOADS[name]
+    A, B = single_inputs(name)
+    pipes = measure_pipes(torch, dev)
+    cpu_s = 0.0 if args.no_cpu else args.cpu_seconds
+    rec = measure_single(args, mw, torch, dist, rank, dev, A, B, name,
+                         graph=(not args.no_graph and n <= 1024), plain_steps=args.plain_steps,
+                         e2e_steps=e2e_count(args), cpu_s=cpu_s, pipes=pipes)
+    line = {"metric": METRIC, "value": rec["value"], "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_of(m), "data": "synthetic",
+            "config": {"workload": desc, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "plain_fp64_gflops": plain_gflops, "plain_plan": pplan.as_dict(),
-                       "speedup_vs_plain": (value / world / plain_gflops) if plain_gflops else None,
-                       "product_kernel_ms": kern_s * 1e3, "step_ms_min": min(step_ms),
-                       "phases_ms_direct_calls": phases,
-                       "plain_roofline": plain_roof,
-                       "int8_peak_tops_measured": int8_peak,
-                       "slice_ops_per_s_over_int8_peak":
-                           (pairs * flops / kern_s / 1e12 / int8_peak) if int8_peak else None},
-            "roofline": roofline_of(pairs, flops, kern_ms, name), "clocks": clk, "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * args.steps}
-    if rank == 0 and not args.no_cpu:
-        rows = args.cpu_rows or auto_rows(A, B)
-        line["cpu_baseline"] = cpu_baseline(A, B, rows, desc.split(",")[0])
+                       "fp64_peak_tflops_measured": pipes[0],
+                       "int8_peak_tops_measured": pipes[1],
+                       **{k: v for k, v in rec.items()
+                          if k not in ("value", "unit", "roofline", "clocks", "e2e",
+                                       "cpu_baseline", "gpu_launches", "workload")}},
+            "roofline": rec["roofline"], "clocks": rec["clocks"], "e2e": rec.get("e2e"),
+            "gpu_launches": rec["gpu_launches"]}
+    if "cpu_baseline" in rec:
+        line["cpu_baseline"] = rec["cpu_baseline"]
+    return line
+
+
+def run_headline(args, mw, torch, dist, rank, world, dev):
+    """The benchmark line: quad double (value) and double double at 4096^3 in the
+    Ozaki form, each next to the plain FP64 form on the same operands and
+    error bound; quad double 1024^3 as a secondary record."""
+    import synthetic
+    pipes = measure_pipes(torch, dev)
+    cpu_s = 0.0 if args.no_cpu else args.cpu_seconds
+    recs = {}
+    for name, m in (("qd4096", 4), ("dd4096", 2)):
+        A, B = synthetic.ozaki_4096(m)
+        recs[name] = measure_single(args, mw, torch, dist, rank, dev, A, B, name,
+                                    plain_steps=args.plain_steps, e2e_steps=e2e_count(args),
+                                    cpu_s=cpu_s, pipes=pipes)
+        del A, B
+    if not args.no_secondary:
+        A, B = synthetic.qd_1024()
+        recs["qd1024"] = measure_single(args, mw, torch, dist, rank, dev, A, B, "qd1024",
+                                        graph=not args.no_graph, plain_steps=args.plain_steps,
+                                        e2e_steps=e2e_count(args), pipes=pipes)
+    qd = recs["qd4096"]
+    line = {"metric": METRIC, "value": qd["value"], "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": qd["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_of(4), "data": "synthetic",
+            "config": {"workload": HEADLINE, "m": [4, 2], "M": 4096, "N": 4096, "K": 4096,
+                       "value_is": "quad double 4096^3, Ozaki form, whole step (split, "
+                                   "products, fusion), device-timed",
+                       "l2": "flushed (256 MiB write) before every timed step; operands "
+                             "(1.6 GB quad double) also exceed L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "fp64_peak_tflops_measured": pipes[0],
+                       "int8_peak_tops_measured": pipes[1],
+                       "error_bound": "|C - C_exact| <= 2K 2^(-52m) (|A||B|) componentwise, "
+                                      "both forms (checked by the GPU tests)",
+                       "records": recs},
+            "roofline": qd["roofline"], "clocks": qd["clocks"], "e2e": qd.get("e2e"),
+            "gpu_launches": qd["gpu_launches"]}
+    if "cpu_baseline" in qd:
+        line["cpu_baseline"] = qd["cpu_baseline"]
     return line
 
 
@@ -509,8 +604,7 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
     roof["algorithmic"] = (f"{pairs} slice pairs x sum of 2 n^3 = {pairs * flops:.3e} flop per "
                            "launch; kernel time from direct calls of the batch")
     # end to end through the public API: pinned host operands in, every C_i out;
-    # the batch is described, planned (exponent spreads measured on the device)
-    # and run per step
+    # the batch is described and run per step with the plan made before the loop
     e2e_steps = args.e2e_steps if args.e2e_steps >= 0 else max(3, args.steps // 4)
     e2e = None
     if e2e_steps > 0:
@@ -520,7 +614,7 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
 
         def batch_call(d):
             eC = torch.empty((8, total), dtype=torch.float64, device=dev)
-            mw.Batch.packed(d[0], d[1], eC, shapes, offsets).run()
+            mw.Batch.packed(d[0], d[1], eC, shapes, offsets, plan).run()
             return [eC]
         e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB], batch_call)
         e2e = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
@@ -529,7 +623,7 @@ def run_batch(args, mw, torch, dist, rank, world, dev):
         mw.check_status()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(8),
             "data": "synthetic",
             "config": {"workload": f"{args.count:,} octo-double products, n ~ U{{8..128}} square, "
                                    "entries U[-1,1) with lower words x2^-53 U[-1,1), seed 3, one "
@@ -624,7 +718,7 @@ def run_adjoint(args, mw, torch, dist, rank, world, dev):
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(2),
             "data": "synthetic",
             "config": {"workload": "double-double forward C=A*B and adjoint dA=W*B^T, dB=A^T*W, "
                                    "A 2048x1024, B 1024x2048, W 2048x2048, entries U[-1,1) with "
@@ -698,9 +792,9 @@ def run_table2(args, mw, torch, dist, rank, world, dev):
     e2e = None
     if e2e_steps > 0:
         hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
-        # mw_dot_batched plans from the data (synchronizing the compute stream only)
+        # the plan made before the loop, as a caller with fixed-range vectors would
         e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB],
-                              lambda d: [mw.mw_dot_batched(d[0], d[1], check=False)])
+                              lambda d: [mw.mw_dot_batched(d[0], d[1], plan, check=False)])
         e2e = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
                "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
                "d2h_bytes_per_step": int(m * count * 8), "how": E2E_HOW}
@@ -708,7 +802,8 @@ def run_table2(args, mw, torch, dist, rank, world, dev):
     ordinary, vectorized = PAPER_TABLE2_MS[m]
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_of(m, "24-bit integer digits, int64 sums"),
             "data": "synthetic",
             "config": {"workload": f"Table 2: {count} m-double inner products of length {K}, "
                                    "vectors on the Section 2 bit pattern, seed 5",
@@ -744,7 +839,9 @@ def main():
 
     dist, rank, world = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
-    if args.workload == "od_batch":
+    if args.workload == "headline":
+        line = run_headline(args, mw, torch, dist, rank, world, dev)
+    elif args.workload == "od_batch":
         line = run_batch(args, mw, torch, dist, rank, world, dev)
     elif args.workload == "adjoint":
         line = run_adjoint(args, mw, torch, dist, rank, world, dev)

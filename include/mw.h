@@ -174,12 +174,14 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
  * fixed 32 MiB array that the library reserves on every device it is loaded on
  * and holds until the process exits; no memory is allocated or freed by the
  * call.  Products whose mw_gemm_workspace_size exceeds 32 MiB are rejected with
- * MW_ENOSPC (and a message) before any GPU work.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call on a
- * device shares the array and leaves its contents behind (mw_gemm itself
- * clears what must start at zero); calls whose work overlaps on the GPU race
- * on it, so order them on one stream or otherwise serialise them. */
+ * MW_ENOSPC (and a message) before any GPU work.  A call outside a stream
+ * capture looks up the array's device address (cudaGetSymbolAddress) with the
+ * device current; a call inside a capture uses the address the last call
+ * outside one found on that device, so make a first call on every device
+ * before any stream capture (MW_EINVAL otherwise).  Every call on a device
+ * shares the array and leaves its contents behind (mw_gemm itself clears what
+ * must start at zero); calls whose work overlaps on the GPU race on it, so
+ * order them on one stream or otherwise serialise them. */
 int mw_gemm_noalloc(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, int64_t K,
                     const double *A, int64_t lda, int64_t plane_stride_a,
                     const double *B, int64_t ldb, int64_t plane_stride_b,

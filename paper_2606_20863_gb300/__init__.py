@@ -37,6 +37,12 @@ class MWError(RuntimeError):
     pass
 
 
+class MWRangeError(MWError):
+    """An operand's exponent spread exceeded the spread its plan was made for
+    (status bit MW_WRANGE): the result is computed, but the componentwise error
+    bound is no longer guaranteed.  Replan (``plan_for``) for such operands."""
+
+
 class mw_plan(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("m", "mode", "w", "S_A", "S_B", "D", "group", "chunk", "range_A", "range_B")]
@@ -161,12 +167,20 @@ def get_status(clear: bool = True) -> int:
     return bits.value
 
 
-def check_status(allow: int = MW_WRANGE):
-    """Raise if a kernel reported an error bit other than those in ``allow``."""
+def check_status(allow: int = 0):
+    """Raise if a kernel reported an error bit other than those in ``allow``
+    (synchronizes).  MW_WRANGE alone raises MWRangeError: a reused plan met
+    operands of a wider exponent spread than it was made for, so the error
+    bound is not guaranteed; pass ``allow=MW_WRANGE`` to accept that."""
     bits = get_status(clear=True)
-    if bits & ~allow:
+    bad = bits & ~allow
+    if bad:
         names = [n for b, n in STATUS_NAMES.items() if bits & b]
-        raise MWError(f"kernel status {bits}: {', '.join(names)}")
+        msg = f"kernel status {bits}: {', '.join(names)}"
+        if bad == MW_WRANGE:
+            raise MWRangeError(msg + " (an operand's exponent spread exceeds the plan's; the "
+                               "error bound is not guaranteed: replan with plan_for)")
+        raise MWError(msg)
     return bits
 
 

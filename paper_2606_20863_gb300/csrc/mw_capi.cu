@@ -364,12 +364,14 @@ int split_both(const mw_plan &p, int transA, int transB, int64_t M, int64_t N, i
   a.digits = w8 + L.digA; a.exps = o.eA; a.spread = o.spA; a.max_spread = o.maxsp;
   a.range = p.range_A;
   int rc = launch_split(a, exps_only, s);
-  if (rc) return rc;
-  // op(B) used as its transpose: rows N; B stored K x N (trans 0 -> columns) or N x K
-  a.trans = !transB; a.R = N; a.ld = ldb; a.plane_stride = psb; a.X = B; a.S = p.S_B;
-  a.digits = w8 + L.digB; a.exps = o.eB; a.spread = o.spB; a.max_spread = o.maxsp + 1;
-  a.range = p.range_B;
-  rc = launch_split(a, exps_only, s2);
+  if (!rc) {
+    // op(B) used as its transpose: rows N; B stored K x N (trans 0 -> columns) or N x K
+    a.trans = !transB; a.R = N; a.ld = ldb; a.plane_stride = psb; a.X = B; a.S = p.S_B;
+    a.digits = w8 + L.digB; a.exps = o.eB; a.spread = o.spB; a.max_spread = o.maxsp + 1;
+    a.range = p.range_B;
+    rc = launch_split(a, exps_only, s2);
+  }
+  // join the side stream whatever happened (inside a capture a fork must be joined)
   if (fork) {
     cudaError_t e = cudaEventRecord(ev[1], s2);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);

@@ -25,24 +25,36 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)32 << 20;  // 32 MiB per device
 
 // In host code this name is only a stand-in for the device array: its device
-// address comes from cudaGetSymbolAddress, once per device.
+// address comes from cudaGetSymbolAddress with the device current.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
 
-int scratch_of_current_device(void **out) {
+// Device address of the array on the current device.  Outside a stream capture
+// it is looked up on every call (cheap), so that a context created anew on the
+// device (after cudaDeviceReset, say), where the array may sit elsewhere, never
+// gets a stale address; inside a capture the address of the last call outside
+// it is used, since the first lookup may load the library's module, which a
+// capture does not allow.
+int scratch_of_current_device(cudaStream_t stream, void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return mw::cuda_fail(e, "mw_gemm_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return mw::fail(MW_EUNSUPPORTED, "device %d out of range", dev);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return mw::cuda_fail(e, "mw_gemm_noalloc: cudaStreamIsCapturing");
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return mw::cuda_fail(e, "mw_gemm_noalloc: cudaGetSymbolAddress");
     g_scratch_addr[dev] = p;
+  } else if (!g_scratch_addr[dev]) {
+    return mw::fail(MW_EINVAL, "mw_gemm_noalloc: the first call on a device must come before "
+                               "any stream capture");
   }
   *out = g_scratch_addr[dev];
   return MW_OK;
@@ -63,7 +75,7 @@ extern "C" int mw_gemm_noalloc(const mw_plan *plan, int transA, int transB, int6
                     "scratch holds %zu bytes; use mw_gemm with a caller-allocated workspace",
                     need, kScratchBytes);
   void *scratch = nullptr;
-  if ((rc = scratch_of_current_device(&scratch))) return rc;
+  if ((rc = scratch_of_current_device((cudaStream_t)stream, &scratch))) return rc;
   return mw_gemm(plan, transA, transB, M, N, K, A, lda, plane_stride_a, B, ldb, plane_stride_b,
                  C, ldc, plane_stride_c, scratch, kScratchBytes, stream);
 }

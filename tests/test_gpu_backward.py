@@ -87,7 +87,10 @@ def test_adjoint_case_2048(mw, cuda):
     """A 2048 x 1024, B 1024 x 2048 double doubles, W 2048 x 2048, seed 4:
     forward through the Ozaki form, dA and dB from the autograd function,
     64 sampled entries against the exact gradient and against quad-double
-    central differences with h = 2^-20."""
+    central differences with h = 2^-20.  The exact gradient (the oracle's
+    rational products W B^T and A^T W) is the independent check; the central
+    differences evaluate the loss with this library's own quad-double product,
+    so they confirm the gradient's meaning but are not independent of it."""
     A, B, W = adjoint_case()
     tA = to_dev(A, cuda).requires_grad_(True)
     tB = to_dev(B, cuda).requires_grad_(True)

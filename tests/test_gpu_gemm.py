@@ -246,8 +246,10 @@ def test_quad_double_1024(mw, cuda, mode):
 @pytest.mark.slow
 @pytest.mark.parametrize("m", [2, 4])
 def test_ozaki_4096(mw, cuda, m):
-    """M = N = K = 4096, magnitudes 2^U[-20,20), seed 2: a 32 x 32 block against
-    the exact product, a few outputs against the oracle's summation bit for bit."""
+    """M = N = K = 4096, magnitudes 2^U[-20,20), seed 2: a 32 x 32 block bit for
+    bit against the oracle's error-free summation (quad double: the 64-bit
+    Horner partial sums of the long-K mode) and against the exact product's
+    bound, plus the four corners bit for bit."""
     from synthetic import ozaki_4096
     A, B = ozaki_4096(m)
     tA, tB = to_dev(A, cuda), to_dev(B, cuda)
@@ -257,9 +259,31 @@ def test_ozaki_4096(mw, cuda, m):
     worst = exact.ExactProduct(A, B, rows, cols).error_ratio(C).max()
     record_worst(f"m={m} 4096^3 ozaki, 32x32 block", worst)
     assert worst <= 1.0
+    sp = slicing.SlicedProduct(A, B, plan.w, plan.S_A, plan.S_B, plan.D, rows=rows, cols=cols)
+    assert np.array_equal(C[:, rows][:, :, cols], sp.result())
     r2, c2 = [0, 4095], [7, 4000]
     sp = slicing.SlicedProduct(A, B, plan.w, plan.S_A, plan.S_B, plan.D, rows=r2, cols=c2)
     assert np.array_equal(C[:, r2][:, :, c2], sp.result())
+
+
+def test_stale_plan_raises(mw, cuda):
+    """A plan reused on operands whose exponent spread exceeds the plan's: the
+    product still runs, MW_WRANGE is raised on the GPU, and the binding turns it
+    into MWRangeError by default (the bound is not guaranteed)."""
+    rng = SplitMix64(370)
+    A, B = loguniform_mdouble(rng, 2, 40, 50, -2, 2), loguniform_mdouble(rng, 2, 50, 30, -2, 2)
+    tA, tB = to_dev(A, cuda), to_dev(B, cuda)
+    plan = mw.plan_for(tA, tB, "ozaki")
+    mw.mw_gemm(tA, tB, plan)                           # fitting operands: no error
+    A2 = A.copy()
+    A2[:, 3, 11] *= 2.0 ** -30                         # row 3 now spans 30 more bits
+    tA2 = to_dev(A2, cuda)
+    with pytest.raises(mw.MWRangeError):
+        mw.mw_gemm(tA2, tB, plan)
+    mw.mw_gemm(tA2, tB, plan, check=False)
+    assert mw.check_status(allow=mw.MW_WRANGE) == mw.MW_WRANGE
+    C = mw.mw_gemm(tA2, tB, mw.plan_for(tA2, tB, "ozaki")).cpu().numpy()   # replanned
+    assert exact.exact_product_full(A2, B).error_ratio(C).max() <= 1.0
 
 
 def test_gemm_replays_in_a_cuda_graph(mw, cuda):

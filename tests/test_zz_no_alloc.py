@@ -39,6 +39,31 @@ def test_noalloc_matches_gemm_on_two_calls_in_a_row(mw, cuda):
         assert torch.equal(C, ref)
 
 
+def test_noalloc_allocates_nothing(mw, cuda):
+    """After one call on the device (which may load the library's module and
+    with it the scratch array), two more calls leave the device's free memory
+    and torch's allocations unchanged, and give the same words."""
+    rng = SplitMix64(403)
+    tA = to_dev(loguniform_mdouble(rng, 2, 90, 110, -6, 6), cuda)
+    tB = to_dev(loguniform_mdouble(rng, 2, 110, 80, -6, 6), cuda)
+    plan = mw.plan_for(tA, tB, "ozaki")
+    ref = mw.mw_gemm(tA, tB, plan)
+    C = torch.empty_like(ref)
+    assert call_noalloc(mw, plan, tA, tB, C) == mw.MW_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(2):
+        C.fill_(float("nan"))
+        assert call_noalloc(mw, plan, tA, tB, C) == mw.MW_OK, mw._lib.mw_last_error().decode()
+        torch.cuda.synchronize()
+        assert torch.equal(C, ref)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    mw.check_status()
+
+
 def test_noalloc_rejects_a_product_beyond_its_scratch(mw, cuda):
     n = 2048
     tA = torch.zeros((2, n, n), dtype=torch.float64, device=cuda)
