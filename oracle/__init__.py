@@ -17,6 +17,10 @@ Parts, each a plain and slow restatement of what the paper defines:
                   row (column), fixed-point pieces with zero high bits, the
                   diagonal sums s_i of Section 2 / Section 4, exact fusion.
                   Bit-exact reference for the GPU digits and integer sums.
+* ``crt``      -- the residue form the Ozaki scheme points to (Sections 1 and
+                  4): the same fixed-point integers multiplied exactly through
+                  residues modulo pairwise coprime moduli and the Chinese
+                  remainder theorem, then rounded greedily.
 * ``textbook`` -- the "ordinary" m-double product of Table 2: multiply-add in
                   m-double arithmetic with two-sum and Dekker two-product, in C
                   (``textbook.c``) for timing and in Python for operation counts
