@@ -40,7 +40,7 @@ KERNELS_PER_STEP = 8   # per operand: exponent, finalize, pieces (x2); product; 
 WORD_NAMES = {2: "double double", 4: "quad double", 8: "octo double", 16: "hexa double"}
 
 
-def dtype_of(m, pieces="exact integer slices in bf16 on tcgen05"):
+def dtype_of(m, pieces="exact integer slices; bf16 operands on tcgen05"):
     """The arithmetic the path computes in: an m-double result built from exact
     integer pieces (not a reduced-precision result)."""
     return f"f64x{m} ({WORD_NAMES[m]} result; {pieces})"
@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-graph", action="store_true",
                     help="single products: launch each step directly instead of replaying a graph")
+    ap.add_argument("--forms", default="ozaki,crt", type=lambda s: s.split(","),
+                    help="headline: Ozaki forms to time (ozaki = digit slices, crt = residues)")
+    ap.add_argument("--mode", default="crt", choices=["ozaki", "crt"],
+                    help="single workloads: the form to time")
     ap.add_argument("--no-secondary", action="store_true",
                     help="headline: leave out the quad-double 1024^3 sub-record")
     ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8, 16],
@@ -287,10 +291,11 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def workload_key(m, M, N, K):
+def workload_key(m, M, N, K, mode="ozaki"):
     """Name of a captured single-product workload, for its DRAM traffic."""
-    return {(4, 1024): "qd1024", (2, 4096): "dd4096", (4, 4096): "qd4096"}.get(
+    base = {(4, 1024): "qd1024", (2, 4096): "dd4096", (4, 4096): "qd4096"}.get(
         (m, M), None) if M == N == K else None
+    return None if base is None else (base if mode == "ozaki" else f"{base}_{mode}")
 
 
 def traffic_of(workload):
@@ -304,10 +309,11 @@ def roofline_of(pairs, flops_per_pair, kern_ms, workload=None):
     achieved = pairs * flops_per_pair / kern_s / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
             "frac": achieved / bf16_burst, "traffic": traffic_of(workload),
-            "kernel": "ozaki_kernel (tcgen05 kind::f16, bf16 integer slices)",
+            "kernel": "ozaki_kernel (tcgen05 kind::f16, bf16 integer slices or residues)",
             "peak_source": f"{peak_src} bf16 dense burst (MEASURED_PEAKS.json)",
-            "algorithmic": f"{pairs} slice pairs x {flops_per_pair:.4g} flop = "
-                           f"{pairs * flops_per_pair:.3e} flop per launch"}
+            "algorithmic": f"{pairs} tensor-core products (slice pairs or moduli) x "
+                           f"{flops_per_pair:.4g} flop = {pairs * flops_per_pair:.3e} flop "
+                           "per launch"}
 
 
 TABLE1_MUL_ADD = {2: 43, 4: 425, 8: 2011}   # Table 1: double ops of one m-double add + mul
@@ -338,7 +344,17 @@ def measure_pipes(torch, dev):
 
 
 def count_pairs(plan):
+    """Tensor-core products of one launch: kept slice pairs, or one per modulus
+    in the residue form."""
+    if plan.mode == 3:                                   # MW_CRT
+        return plan.D
     return sum(1 for t in range(plan.D) for p in range(plan.S_A) if 0 <= t - p < plan.S_B)
+
+
+FORMS = {"ozaki": "Ozaki slices: bf16 integer digits on tcgen05, every kept pair of digit "
+                  "matrices, fp32 drained to integers, exact fusion",
+         "crt": "Ozaki residues (scheme II): balanced residues modulo pairwise coprime moduli "
+                "on tcgen05, one product per modulus, Chinese-remainder reconstruction"}
 
 
 def e2e_pipelined(torch, steps, h_in, compute):
@@ -391,13 +407,13 @@ E2E_HOW = ("pinned host inputs copied in and results copied out every step, on t
 
 def measure_single(args, mw, torch, dist, rank, dev, A, B, workload, mode="ozaki",
                    graph=False, plain_steps=0, e2e_steps=0, cpu_s=0.0, pipes=None):
-    """One single-product workload: the Ozaki-form step (`steps` timed runs, L2
-    flushed before each), its product-kernel time from phase events around
+    """One single-product workload in one form: the step (`steps` timed runs,
+    L2 flushed before each), its product-kernel time from phase events around
     direct calls, optionally the plain FP64 form on the same operands (same
     error bound), the end-to-end rate through the public call from pinned host
     buffers (one plan made before the loop, as a caller with fixed-range
     operands would), and the CPU oracle on a bounded sample.  Returns a record
-    with the device-timed value of this rank and the aggregate over ranks."""
+    with the device-timed value aggregated over ranks."""
     m, M, K = A.shape
     N = B.shape[2]
     tA = torch.from_numpy(A).to(dev)
@@ -435,22 +451,35 @@ def measure_single(args, mw, torch, dist, rank, dev, A, B, workload, mode="ozaki
     # recorded inside a graph), as many runs as timed steps
     _, kern_ms, _ = timed(call, args.steps, flush, mw, None, dev)
     phases = timed.phases
-    rec = {"workload": workload, "m": m, "M": M, "N": N, "K": K, "value": value,
+    rec = {"workload": workload, "mode": mode, "m": m, "M": M, "N": N, "K": K, "value": value,
            "unit": "GFLOP/s", "ms_per_step": t_step * 1e3 / args.steps,
            "step_ms_min": min(step_ms), "product_kernel_ms": statistics.mean(kern_ms),
-           "phases_ms_direct_calls": phases, "plan": plan.as_dict(), "slice_pairs": pairs,
-           "form": "Ozaki: bf16 integer slices on tcgen05, fp32 drained to integers",
+           "phases_ms_direct_calls": phases, "plan": plan.as_dict(),
+           "tensor_products_per_launch": pairs, "form": FORMS[mode],
            "launch": "one mw_gemm call captured in a CUDA graph, replayed per step"
                      if g is not None else "direct mw_gemm calls",
-           "roofline": roofline_of(pairs, flops, kern_ms, workload_key(m, M, N, K)),
+           "roofline": roofline_of(pairs, flops, kern_ms, workload_key(m, M, N, K, mode)),
            "clocks": clk, "gpu_launches": KERNELS_PER_STEP * args.steps}
     del g
+    extras(args, mw, torch, dist, rank, dev, A, B, tA, tB, plan, rec, plain_steps, e2e_steps,
+           cpu_s, pipes)
+    del tA, tB, ws, C, flush
+    torch.cuda.empty_cache()
+    return rec
 
+
+def extras(args, mw, torch, dist, rank, dev, A, B, tA, tB, plan, rec, plain_steps, e2e_steps,
+           cpu_s, pipes):
+    """The plain FP64 form, the end-to-end rate and the CPU oracle for a record."""
+    m, M, K = A.shape
+    N = B.shape[2]
+    flops = 2.0 * M * N * K
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     # plain FP64 form on the same operands and bound (the comparison of the metric)
     if plain_steps > 0:
         pplan = mw.plan_for(tA, tB, "plain")
         pws = torch.empty(mw.workspace_size(pplan, M, N, K), dtype=torch.uint8, device=dev)
-        Cp = torch.empty_like(C)
+        Cp = torch.empty((m, M, N), dtype=torch.float64, device=dev)
         if M * N * K <= 1024 ** 3:                 # one untimed call (4096^3 takes seconds)
             mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws)
         pms, _, pclk = timed(lambda: mw.mw_gemm(tA, tB, pplan, C=Cp, ws=pws, check=False),
@@ -470,9 +499,7 @@ def measure_single(args, mw, torch, dist, rank, dev, A, B, workload, mode="ozaki
                 "fp64_pipe_tflops": ppairs * plain / 1e3,
                 "fp64_pipe_frac": ppairs * plain / 1e3 / fp64_peak,
                 "fp64_peak_tflops_measured": fp64_peak}
-        rec["speedup_vs_plain"] = value / plain
         del pws, Cp
-
     # end to end through the public call: pinned host operands in, host result out
     if e2e_steps > 0:
         hA = torch.from_numpy(A).pin_memory()
@@ -483,13 +510,11 @@ def measure_single(args, mw, torch, dist, rank, dev, A, B, workload, mode="ozaki
         rec["e2e"] = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
                       "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8),
                       "d2h_bytes_per_step": int(m * M * N * 8),
-                      "how": E2E_HOW + "; the plan (slice counts) made once before the loop"}
+                      "how": E2E_HOW + "; the plan made once before the loop"}
         del hA, hB
     if rank == 0 and cpu_s > 0:
         rec["cpu_baseline"] = cpu_sample(A, B, cpu_s, WORD_NAMES[m])
-    del tA, tB, ws, C, flush
-    torch.cuda.empty_cache()
-    return rec
+    del flush
 
 
 def e2e_count(args):
@@ -502,13 +527,15 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
     A, B = single_inputs(name)
     pipes = measure_pipes(torch, dev)
     cpu_s = 0.0 if args.no_cpu else args.cpu_seconds
-    rec = measure_single(args, mw, torch, dist, rank, dev, A, B, name,
+    rec = measure_single(args, mw, torch, dist, rank, dev, A, B, name, mode=args.mode,
                          graph=(not args.no_graph and n <= 1024), plain_steps=args.plain_steps,
                          e2e_steps=e2e_count(args), cpu_s=cpu_s, pipes=pipes)
     line = {"metric": METRIC, "value": rec["value"], "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": dtype_of(m), "data": "synthetic",
+            "dtype": dtype_of(m, "exact integer residues" if args.mode == "crt" else
+                              "exact integer slices") + "; bf16 operands on tcgen05",
+            "data": "synthetic",
             "config": {"workload": desc, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "fp64_peak_tflops_measured": pipes[0],
@@ -524,39 +551,55 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
 
 
 def run_headline(args, mw, torch, dist, rank, world, dev):
-    """The benchmark line: quad double (value) and double double at 4096^3 in the
-    Ozaki form, each next to the plain FP64 form on the same operands and
-    error bound; quad double 1024^3 as a secondary record."""
+    """The benchmark line: quad double (value) and double double at 4096^3, each
+    in both Ozaki forms (digit slices and residues) on the same operands and the
+    same error bound, the faster one next to the plain FP64 form; quad double
+    1024^3 as a secondary record."""
     import synthetic
     pipes = measure_pipes(torch, dev)
     cpu_s = 0.0 if args.no_cpu else args.cpu_seconds
-    recs = {}
+    recs, best = {}, {}
     for name, m in (("qd4096", 4), ("dd4096", 2)):
         A, B = synthetic.ozaki_4096(m)
-        recs[name] = measure_single(args, mw, torch, dist, rank, dev, A, B, name,
-                                    plain_steps=args.plain_steps, e2e_steps=e2e_count(args),
-                                    cpu_s=cpu_s, pipes=pipes)
-        del A, B
+        forms = {f: measure_single(args, mw, torch, dist, rank, dev, A, B, name, mode=f,
+                                   pipes=pipes) for f in args.forms}
+        win = max(forms, key=lambda f: forms[f]["value"])
+        tA, tB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        extras(args, mw, torch, dist, rank, dev, A, B, tA, tB, mw.plan_for(tA, tB, win),
+               forms[win], args.plain_steps, e2e_count(args), cpu_s, pipes)
+        if "plain" in forms[win]:
+            for f in forms:
+                forms[f]["speedup_vs_plain"] = forms[f]["value"] / forms[win]["plain"]["value"]
+        del tA, tB, A, B
+        torch.cuda.empty_cache()
+        best[name] = forms[win]
+        for f, r in forms.items():
+            recs[f"{name}_{f}"] = r
     if not args.no_secondary:
         A, B = synthetic.qd_1024()
-        recs["qd1024"] = measure_single(args, mw, torch, dist, rank, dev, A, B, "qd1024",
-                                        graph=not args.no_graph, plain_steps=args.plain_steps,
-                                        e2e_steps=e2e_count(args), pipes=pipes)
-    qd = recs["qd4096"]
+        for f in args.forms:
+            recs[f"qd1024_{f}"] = measure_single(args, mw, torch, dist, rank, dev, A, B, "qd1024",
+                                                 mode=f, graph=not args.no_graph, pipes=pipes)
+    qd = best["qd4096"]
     line = {"metric": METRIC, "value": qd["value"], "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": qd["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": dtype_of(4), "data": "synthetic",
+            "dtype": dtype_of(4, "exact integer residues" if qd["mode"] == "crt" else
+                              "exact integer slices") + "; bf16 operands on tcgen05",
+            "data": "synthetic",
             "config": {"workload": HEADLINE, "m": [4, 2], "M": 4096, "N": 4096, "K": 4096,
-                       "value_is": "quad double 4096^3, Ozaki form, whole step (split, "
-                                   "products, fusion), device-timed",
+                       "value_is": f"quad double 4096^3, Ozaki form '{qd['mode']}' (the faster "
+                                   "of slices and residues), whole step (split, products, "
+                                   "fusion), device-timed",
+                       "dd4096_value": best["dd4096"]["value"],
+                       "dd4096_form": best["dd4096"]["mode"],
                        "l2": "flushed (256 MiB write) before every timed step; operands "
                              "(1.6 GB quad double) also exceed L2",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "fp64_peak_tflops_measured": pipes[0],
                        "int8_peak_tops_measured": pipes[1],
                        "error_bound": "|C - C_exact| <= 2K 2^(-52m) (|A||B|) componentwise, "
-                                      "both forms (checked by the GPU tests)",
+                                      "every form (checked by the GPU tests)",
                        "records": recs},
             "roofline": qd["roofline"], "clocks": qd["clocks"], "e2e": qd.get("e2e"),
             "gpu_launches": qd["gpu_launches"]}

@@ -28,7 +28,15 @@
  *             before that), the "stepping stone to the Ozaki scheme" of
  *             Section 1; step 4 is exact integer fusion and rounding to nearest
  *             of each word in turn.
- * Inner products (mw_dot_batched, the workload of Table 2) use a third form:
+ *   MW_CRT    the residue form (the second Ozaki scheme): the same fixed-point
+ *             integers T of step 2, reduced modulo n small pairwise coprime
+ *             moduli (balanced residues, exact in bfloat16); one tensor-core
+ *             product per modulus gives every sum of products mod p_i, and the
+ *             Chinese remainder theorem rebuilds the exact integer products,
+ *             which step 4 rounds as in MW_OZAKI.  n grows with the bits of
+ *             T_A + T_B, where MW_OZAKI's pair count grows with their square
+ *             (m = 2 and 4).
+ * Inner products (mw_dot_batched, the workload of Table 2) use a fourth form:
  *   MW_DOT    pieces are 24-bit integers, products summed in int64 on the
  *             integer units (no operand reuse, so no tensor cores); exact
  *             integer fusion and rounding as for MW_OZAKI.
@@ -72,7 +80,7 @@ enum {
 };
 
 /* forms of the product */
-enum { MW_PLAIN = 0, MW_OZAKI = 1, MW_DOT = 2 };
+enum { MW_PLAIN = 0, MW_OZAKI = 1, MW_DOT = 2, MW_CRT = 3 };
 
 /* digit formats written by mw_split */
 enum { MW_DIGITS_BF16 = 0, MW_DIGITS_F64 = 1 };
@@ -86,7 +94,10 @@ enum { MW_DIGITS_BF16 = 0, MW_DIGITS_F64 = 1 };
  *   chunk  products of pieces accumulated in fp32 before a drain (MW_OZAKI;
  *          multiple of 64)
  *   range_A, range_B  exponent spread (bits) the plan assumes for the rows of
- *          op(A) / columns of op(B); larger spreads raise MW_WRANGE. */
+ *          op(A) / columns of op(B); larger spreads raise MW_WRANGE.
+ * MW_CRT reads the fields so: w = 1, S_A / S_B = fixed-point bits L_A / L_B of
+ * the entries of op(A) / op(B) (T = sum_j trunc(x_j 2^(L - 2 - E))), D = number
+ * of moduli (the first D of mw_crt_moduli), group = 1, chunk unused. */
 typedef struct mw_plan {
   int m, mode, w, S_A, S_B, D, group, chunk, range_A, range_B;
 } mw_plan;
@@ -101,9 +112,12 @@ typedef struct mw_plan {
  * the call.  MW_DOT plans one inner product of length K (M = N = 1) with
  * S_A = S_B = the smallest compiled piece count that covers the analysis
  * (2: 4..8, 4: 8..12, 8: 17..21, 16: 35..36) and D <= S + 4.
+ * MW_CRT takes L_A, L_B from the same truncation analysis (at bit
+ * granularity) and the fewest moduli whose product P exceeds
+ * 8 K 2^(L_A + L_B - 2) >= 8 max|X| (m = 2 or 4).
  * Returns MW_EINVAL for bad arguments, MW_EUNSUPPORTED if no plan fits the
- * exactness thresholds (e.g. K too long for MW_PLAIN) or for m = 16 with
- * MW_PLAIN.
+ * exactness thresholds (e.g. K too long for MW_PLAIN, more bits than the
+ * moduli of MW_CRT hold) or for m = 16 with MW_PLAIN.
  * Cites: Section 2 (the exactness threshold on the number of summed
  * products of pieces); the componentwise bound itself is the library's. */
 int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, int range_B,
@@ -131,6 +145,13 @@ int mw_split(int m, int trans, int64_t R, int64_t K, const double *X, int64_t ld
              int64_t plane_stride, int w, int S, int format, void *digits, int64_t digit_ld,
              int32_t *exps, int32_t *spread, int32_t *max_spread, int range, mw_stream_t stream);
 
+/* The residue form's moduli, in the order plans use them (a plan with D moduli
+ * uses the first D): pairwise coprime, at most 513.  Copies min(n, total) of
+ * them to moduli (may be NULL) and returns the total.  Host only.
+ * Cites: Sections 1 and 4 (the Ozaki scheme the residue form follows); the
+ * table itself is the library's. */
+int mw_crt_moduli(int *moduli, int n);
+
 /* Bytes of device workspace mw_gemm needs for this plan and shape.
  * No counterpart in the paper (device memory sizing). */
 int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K, size_t *bytes);
@@ -139,13 +160,16 @@ int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
  * offsets[0] int32 exponents and spreads: E_A[M], spread_A[M], E_B[N], spread_B[N];
  * offsets[1] pieces of op(A): S_A planes of M x Kp (Kp = K rounded up to 64),
  *            bfloat16 (MW_OZAKI) or double (MW_PLAIN), layout as in mw_split;
- * offsets[2] pieces of op(B)^T: S_B planes of N x Kp;
+ *            MW_CRT: D planes of balanced residues (bfloat16), plane i mod p_i;
+ * offsets[2] pieces of op(B)^T: S_B planes of N x Kp (MW_CRT: D residue planes);
  * offsets[3] (MW_OZAKI) partial sums, one column-major plane per entry (entry
  *            (i, j) of a plane at j*M + i).  When min(S_A, S_B) * Kp * 2^(2w-2)
  *            < 2^31 every diagonal sum fits in 32 bits and the planes are the
  *            int32 s_t, t < D; otherwise int64 planes g < G holding
  *            V = sum_t s_t 2^(w (t1 - t)) over the diagonals of group g,
  *            [g*group, t1 = min(D, (g+1)*group) - 1].
+ *            MW_CRT: D int32 planes, plane i congruent mod p_i to the sum of
+ *            products of residues (equal to it while K (p_i/2)^2 < 2^31).
  * bytes = total workspace size (same as mw_gemm_workspace_size).
  * No counterpart in the paper (device memory sizing). */
 int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
@@ -158,7 +182,8 @@ int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t 
  * pieces, the exponents and the diagonal partial sums; no memory is allocated.
  * Asynchronous on `stream`.
  * Cites: Section 2 (error-free summation of pieces, the s_i) and
- * Section 4 (the matrix form, pieces of matrices on tensor cores). */
+ * Section 4 (the matrix form, pieces of matrices on tensor cores; the Ozaki
+ * scheme, whose residue form MW_CRT computes). */
 int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, int64_t K,
             const double *A, int64_t lda, int64_t plane_stride_a,
             const double *B, int64_t ldb, int64_t plane_stride_b,

@@ -95,9 +95,12 @@ class ResidueSplit:
             row = [fixed_point(L[:, r, k], F) for k in range(K)]
             self.in_range &= all(-lim <= t < lim for t in row)
             self.T.append(row)
-        self.residues = np.array(
-            [[[balanced_residue(t, p) for t in row] for row in self.T] for p in moduli],
-            dtype=np.int64).reshape(len(moduli), len(self.rows), K)
+        # balanced_residue of every T, over an object array of Python integers
+        Tobj = np.array(self.T, dtype=object).reshape(len(self.rows), K)
+        self.residues = np.zeros((len(moduli), len(self.rows), K), dtype=np.int64)
+        for i, p in enumerate(moduli):
+            h = int(p) // 2
+            self.residues[i] = (((Tobj + h) % int(p)) - h).astype(np.int64)
 
 
 def residue_products(RA: np.ndarray, RB: np.ndarray) -> np.ndarray:

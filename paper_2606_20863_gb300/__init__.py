@@ -26,9 +26,9 @@ _LIB_PATH = os.path.join(_HERE, "libmw.so")
 
 MW_OK, MW_EINVAL, MW_ERANGE, MW_ENONFINITE, MW_ECUDA, MW_ETIMEOUT, MW_ENOSPC, MW_WRANGE = (
     0, 1, 2, 4, 8, 16, 32, 64)
-MW_PLAIN, MW_OZAKI, MW_DOT = 0, 1, 2
+MW_PLAIN, MW_OZAKI, MW_DOT, MW_CRT = 0, 1, 2, 3
 MW_DIGITS_BF16, MW_DIGITS_F64 = 0, 1
-_MODES = {"plain": MW_PLAIN, "ozaki": MW_OZAKI, "dot": MW_DOT}
+_MODES = {"plain": MW_PLAIN, "ozaki": MW_OZAKI, "dot": MW_DOT, "crt": MW_CRT}
 STATUS_NAMES = {MW_ERANGE: "ERANGE", MW_ENONFINITE: "ENONFINITE", MW_ETIMEOUT: "ETIMEOUT",
                 MW_WRANGE: "WRANGE"}
 
@@ -98,6 +98,7 @@ def _load():
         "mw_gemm_batched": [pp, ctypes.POINTER(mw_batch), vp, vp, ctypes.c_size_t, vp],
         "mw_dot_batched": [pp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, vp],
         "mw_selftest_timeout": [ctypes.c_uint, vp],
+        "mw_crt_moduli": [ip, i32],
         "mw_set_phase_events": [ctypes.POINTER(ctypes.c_void_p), i32],
     }
     for name, args in sig.items():
@@ -117,7 +118,7 @@ EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_works
             "mw_version", "mw_set_phase_events", "mw_gemm_noalloc", "mw_batch_describe",
             "mw_gemm_batched_workspace_size", "mw_measure_spread_batched",
             "mw_measure_spread_batched_workspace_size", "mw_gemm_batched",
-            "mw_dot_batched", "mw_selftest_timeout")
+            "mw_dot_batched", "mw_selftest_timeout", "mw_crt_moduli")
 
 
 def _check(rc: int, what: str):
@@ -182,6 +183,15 @@ def check_status(allow: int = 0):
                                "error bound is not guaranteed: replan with plan_for)")
         raise MWError(msg)
     return bits
+
+
+def crt_moduli(n: int | None = None) -> list[int]:
+    """The residue form's moduli in the order plans use them (the first n)."""
+    total = _lib.mw_crt_moduli(None, 0)
+    n = total if n is None else min(n, total)
+    buf = (ctypes.c_int * max(n, 1))()
+    _lib.mw_crt_moduli(buf, n)
+    return list(buf[:n])
 
 
 def mw_plan_gemm(m: int, mode: str | int, M: int, N: int, K: int, range_A: int,

@@ -84,17 +84,21 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 Layout layout(const mw_plan &p, int64_t M, int64_t N, int64_t K) {
   Layout L{};
   L.Kp = round_up(K, 64);
-  const size_t elem = p.mode == MW_OZAKI ? 2 : 8;
+  const size_t elem = p.mode == MW_PLAIN ? 8 : 2;
+  // planes of pieces: S_A / S_B digits, or D residues in the residue form
+  const size_t planesA = p.mode == MW_CRT ? p.D : p.S_A, planesB = p.mode == MW_CRT ? p.D : p.S_B;
   L.exps = 0;
   size_t off = align256(sizeof(int32_t) * (2 * (size_t)M + 2 * (size_t)N + 2));
   L.digA = off;
-  off = align256(off + (size_t)p.S_A * M * L.Kp * elem);
+  off = align256(off + planesA * M * L.Kp * elem);
   L.digB = off;
-  off = align256(off + (size_t)p.S_B * N * L.Kp * elem);
+  off = align256(off + planesB * N * L.Kp * elem);
   L.partials = off;
   if (p.mode == MW_OZAKI)
     off = align256(off + ozaki_partials_bytes(M, N, p.D, p.group,
                                               narrow_partials(p.S_A, p.S_B, p.w, L.Kp)));
+  else if (p.mode == MW_CRT)
+    off = align256(off + ozaki_partials_bytes(M, N, p.D, 1, true));
   L.total = off;
   return L;
 }
@@ -111,6 +115,18 @@ int check_plan(const mw_plan *p, int64_t M, int64_t N, int64_t K) {
     const int gmax = group_size(S_min, K, p->w);
     if (gmax < 1 || p->group > gmax)
       return fail(MW_EINVAL, "group %d exceeds the int64 limit %d", p->group, gmax);
+  } else if (p->mode == MW_CRT) {
+    if (p->m != 2 && p->m != 4)
+      return fail(MW_EUNSUPPORTED, "the residue form (MW_CRT) takes m = 2 and 4");
+    if (p->w != 1) return fail(MW_EINVAL, "MW_CRT plans have w = 1 (S_A, S_B are bits)");
+    if (p->S_A < 2 || p->S_B < 2 || p->S_A > 381 || p->S_B > 381)
+      return fail(MW_EUNSUPPORTED, "MW_CRT fixed-point bits must be 2..381");
+    if (p->D > crt_table_size())
+      return fail(MW_EUNSUPPORTED, "MW_CRT: %d moduli, the table has %d", p->D, crt_table_size());
+    const double need = p->S_A + p->S_B + 1 + std::log2((double)K);
+    if (crt_bits(p->D) <= need)
+      return fail(MW_EINVAL, "MW_CRT: %d moduli hold %.1f bits, the products need %.1f", p->D,
+                  crt_bits(p->D), need);
   } else if (p->mode == MW_PLAIN) {
     if (p->m == 16) return fail(MW_EUNSUPPORTED, "m = 16 has no MW_PLAIN form (MW_OZAKI and MW_DOT take it)");
     if (p->w < 1 || p->w > 26) return fail(MW_EINVAL, "plain piece width w must be 1..26");
@@ -118,7 +134,7 @@ int check_plan(const mw_plan *p, int64_t M, int64_t N, int64_t K) {
     const double bits = std::log2((double)S_min * (double)K) + 2.0 * p->w - 2.0;
     if (bits > 53.0) return fail(MW_EINVAL, "plain plan not exact: pairs*K*2^(2w-2) > 2^53");
   } else {
-    return fail(MW_EINVAL, "mode must be MW_PLAIN or MW_OZAKI");
+    return fail(MW_EINVAL, "mode must be MW_PLAIN, MW_OZAKI or MW_CRT");
   }
   return MW_OK;
 }
@@ -170,7 +186,16 @@ int mw_selftest_timeout(unsigned int limit_us, mw_stream_t stream) {
   return cuda_fail(cudaGetLastError(), "self-test launch");
 }
 
-const char *mw_version(void) { return "mw 0.1 (sm_103a, tcgen05 bf16 slices, fp64 pieces)"; }
+const char *mw_version(void) {
+  return "mw 0.2 (sm_103a, tcgen05 bf16 slices and residues, fp64 pieces)";
+}
+
+int mw_crt_moduli(int *moduli, int n) {
+  const int total = crt_table_size();
+  if (moduli)
+    for (int i = 0; i < n && i < total; ++i) moduli[i] = crt_modulus(i);
+  return total;
+}
 
 int mw_set_phase_events(void *const *events, int n) {
   if (!events || n <= 0) {
@@ -245,6 +270,26 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
     if (w < 4) return fail(MW_EUNSUPPORTED, "K = %lld too long for exact FP64 sums", (long long)K);
     p.group = 1;
     p.chunk = 0;
+  } else if (mode == MW_CRT) {
+    // fixed-point bits as for the slice form's digits (w = 1: no rounding up to
+    // whole digits); no products are dropped, so the moduli only have to hold
+    // |X| <= K 2^(L_A + L_B - 2) below P/8
+    if (want_w != 0 && want_w != 1) return fail(MW_EINVAL, "MW_CRT plans have w = 1");
+    if (m != 2 && m != 4) return fail(MW_EUNSUPPORTED, "the residue form (MW_CRT) takes m = 2 and 4");
+    p.w = 1;
+    p.S_A = std::max(2, ceil_div_bits(bitsA, 1));
+    p.S_B = std::max(2, ceil_div_bits(bitsB, 1));
+    if (p.S_A > 381 || p.S_B > 381)
+      return fail(MW_EUNSUPPORTED, "MW_CRT: %d / %d fixed-point bits (at most 381)", p.S_A, p.S_B);
+    const double need = p.S_A + p.S_B + 1 + lgK;
+    int n = 1;
+    while (n <= crt_table_size() && crt_bits(n) <= need) ++n;
+    if (n > crt_table_size())
+      return fail(MW_EUNSUPPORTED, "MW_CRT: the products need %.1f bits, the moduli hold %.1f",
+                  need, crt_bits(crt_table_size()));
+    p.D = n;
+    p.group = 1;
+    p.chunk = 0;
   } else if (mode == MW_DOT) {
     if (want_w != 0 && want_w != 24) return fail(MW_EINVAL, "MW_DOT pieces are 24 bits");
     if (M != 1 || N != 1) return fail(MW_EINVAL, "MW_DOT plans one inner product: M = N = 1");
@@ -263,7 +308,7 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
     p.group = 1;
     p.chunk = 0;
   } else {
-    return fail(MW_EINVAL, "mode must be MW_PLAIN, MW_OZAKI or MW_DOT");
+    return fail(MW_EINVAL, "mode must be MW_PLAIN, MW_OZAKI, MW_CRT or MW_DOT");
   }
   *plan = p;
   return MW_OK;
@@ -357,7 +402,8 @@ int split_both(const mw_plan &p, int transA, int transB, int64_t M, int64_t N, i
   Operands o = ops_in(ws, M, N);
   uint8_t *w8 = static_cast<uint8_t *>(ws);
   SplitArgs a{};
-  a.m = p.m; a.w = p.w; a.format = p.mode == MW_OZAKI ? MW_DIGITS_BF16 : MW_DIGITS_F64;
+  a.m = p.m; a.w = p.w; a.format = p.mode == MW_PLAIN ? MW_DIGITS_F64 : MW_DIGITS_BF16;
+  a.nmod = p.mode == MW_CRT ? p.D : 0;
   a.K = K; a.digit_ld = L.Kp;
   // op(A): rows M; stored M x K (trans 0) or K x M (trans 1)
   a.trans = transA; a.R = M; a.ld = lda; a.plane_stride = psa; a.X = A; a.S = p.S_A;
@@ -427,6 +473,7 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
   OzakiArgs a{};
   a.m = p.m; a.w = p.w; a.S_A = p.S_A; a.S_B = p.S_B; a.D = p.D; a.group = p.group;
   a.chunk = p.chunk; a.M = M; a.N = N; a.Kp = L.Kp;
+  a.crt = p.mode == MW_CRT;
   a.dA = w8 + L.digA; a.dB = w8 + L.digB; a.eA = o.eA; a.eB = o.eB;
   a.partials = w8 + L.partials;
   a.C = C; a.ldc = ldc; a.psc = psc;

@@ -22,6 +22,7 @@ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 // ---- split (mw_split.cu) ----------------------------------------------------
 struct SplitArgs {
   int m, trans, w, S, format, range;
+  int nmod;                     // residue form: moduli (planes), S = fixed-point bits; else 0
   int64_t R, K, ld, plane_stride, digit_ld;
   const double *X;
   void *digits;
@@ -43,6 +44,7 @@ int launch_plain(const PlainArgs &a, cudaStream_t s);
 // ---- Ozaki form (mw_ozaki.cu) ------------------------------------------------
 struct OzakiArgs {
   int m, w, S_A, S_B, D, group, chunk;
+  bool crt;                     // residue form: S_A, S_B fixed-point bits, D moduli
   int64_t M, N, Kp;
   const void *dA, *dB;          // bf16 pieces, S x rows x Kp
   const int32_t *eA, *eB;
@@ -68,6 +70,7 @@ struct ProductLaunch {
   int64_t M, N, K;
   void *partials;                 // int32 [t][M][N] (narrow) or int64 [g][M][N]
   bool narrow;
+  bool crt;                       // residue form: one product per modulus t < D
   unsigned long long *next_item;  // work counter (reset by launch_product)
 };
 int launch_product(const ProductLaunch &a, cudaStream_t s);
@@ -82,6 +85,20 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
 bool narrow_partials(int S_A, int S_B, int w, int64_t max_K);
 size_t ozaki_partials_planes_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
+
+// ---- residue form (mw_crt.cu) -------------------------------------------------
+constexpr int kCrtMaxModuli = 96;   // capacity of the moduli tables
+constexpr int kCrtMaxLimbs = 24;    // 32-bit limbs of the largest modulus product
+int crt_table_size();               // moduli in the library's table
+int crt_modulus(int i);             // modulus i of the table (0 past its end)
+int crt_chunk(int i);               // products per fp32 accumulation: 256, 128 or 64
+double crt_bits(int n);             // log2 of the product of the first n moduli
+// Balanced residues of the fixed-point values (a.S bits) modulo the first
+// a.nmod moduli, bfloat16 planes laid out as mw_split's digits.
+int launch_residues(const SplitArgs &a, cudaStream_t s);
+// Reconstruction of the exact products from the D int32 planes of the product
+// kernel and greedy rounding into m words.
+int launch_crt_combine(const OzakiArgs &a, cudaStream_t s);
 
 // Number of diagonal groups.
 inline int n_groups(int D, int group) { return (D + group - 1) / group; }

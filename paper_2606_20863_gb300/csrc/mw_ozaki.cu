@@ -74,7 +74,11 @@ template <int BN_, bool NARROW> struct Shape {
   static_assert(TMEM_COLS <= 512, "tensor memory holds 512 columns");
 };
 
-constexpr int MAX_GROUPS = 64;
+constexpr int MAX_GROUPS = 128;
+static_assert(MAX_GROUPS >= kCrtMaxModuli, "a work item per modulus");
+// Residue form: drains between two reductions of the int32 accumulators mod p.
+// A drain adds at most 2^22 in magnitude, so 511 of them stay below 2^31.
+constexpr int kCrtReduceEvery = 511;
 constexpr int RING = 4;   // work items the producer may run ahead
 
 struct PParams {
@@ -88,6 +92,9 @@ struct PParams {
   unsigned long long *next_item;  // work counter, zero before the launch
   unsigned int *status;
   int gorder[MAX_GROUPS]; // diagonal groups, most expensive first
+  // residue form: per modulus t, k-blocks per drain and the modulus
+  uint8_t crt_chunk_kb[MAX_GROUPS];
+  uint16_t crt_p[MAX_GROUPS];
   BInfo single;
 };
 
@@ -146,11 +153,33 @@ __device__ __forceinline__ int nsteps(const PParams &P, int t, int rs, int KB) {
   return n > 0 ? n * KB : 0;
 }
 
+// The pairs of "diagonal" t and their k-blocks: the slice form sweeps
+// p = plo..phi against B slice t - p; the residue form (CRT) has one pair per
+// modulus t, residue plane t of A against residue plane t of B.
+template <bool CRT>
+__device__ __forceinline__ int pair_lo(const PParams &P, int t) { return CRT ? t : plo(P, t); }
+template <bool CRT>
+__device__ __forceinline__ int pair_hi(const PParams &P, int t, int rs) {
+  return CRT ? t : phi(P, t, rs);
+}
+template <bool CRT>
+__device__ __forceinline__ int steps_of(const PParams &P, int t, int rs, int KB) {
+  return CRT ? KB : nsteps(P, t, rs, KB);
+}
+template <bool CRT>
+__device__ __forceinline__ int chunk_of(const PParams &P, int t) {
+  return CRT ? (int)P.crt_chunk_kb[t] : P.chunk_kb;
+}
+
 // STACK: B slices side by side (batches of small products); otherwise one
 // slice per MMA and the drain stores one diagonal per tile column.
-template <int BN_, bool NARROW, bool STACK>
+// CRT: the residue form, one product of residue planes per modulus (narrow,
+// not stacked); its int32 sums are reduced mod p every kCrtReduceEvery drains,
+// so they stay congruent to the exact sums for any K.
+template <int BN_, bool NARROW, bool STACK, bool CRT = false>
 __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
     ozaki_kernel(const __grid_constant__ Maps maps, const PParams P) {
+  static_assert(!CRT || (NARROW && !STACK), "the residue form is narrow, one product per item");
   using SH = Shape<BN_, NARROW>;
   constexpr int BN = SH::BN, STAGES = SH::STAGES, TMEM_COLS = SH::TMEM_COLS;
   constexpr uint32_t STAGE_B = SH::STAGE_B;
@@ -227,8 +256,8 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         // the boxes of maps.a are at most BM rows and of maps.b at most BN rows
         const uint32_t bytes = (uint32_t)(min(box_rows(ia), BM) + min(box_rows(ib), BN)) * BK * 2;
         for (int t = x.t0; t <= x.t1 && !*abort; t += x.rs) {
-          for (int p = plo(P, t); p <= phi(P, t, x.rs) && !*abort; ++p) {
-            const int q = t - p;                  // first of the rs B slices
+          for (int p = pair_lo<CRT>(P, t); p <= pair_hi<CRT>(P, t, x.rs) && !*abort; ++p) {
+            const int q = CRT ? t : t - p;        // first of the rs B slices
             const int ra = (int)(x.rowA + (int64_t)p * x.M + (int64_t)x.tm * BM);
             const int rb = (int)(x.rowB + (int64_t)(q + x.rs - 1) * x.N + (int64_t)x.tn * BN);
             for (int kb = 0; kb < x.KB; ++kb, ++it) {
@@ -258,9 +287,10 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         const int ncols = (int)min((int64_t)BN, x.rs * x.N - (int64_t)x.tn * BN);
         const uint32_t idesc = idesc_bf16(BM, (ncols + 15) & ~15);
         for (int t = x.t0; t <= x.t1 && !*abort; t += x.rs) {
-          const int tot = nsteps(P, t, x.rs, x.KB);
+          const int tot = steps_of<CRT>(P, t, x.rs, x.KB);
+          const int ck = chunk_of<CRT>(P, t);
           for (int j = 0; j < tot && !*abort; ++ch) {
-            const int nk = min(P.chunk_kb, tot - j);
+            const int nk = min(ck, tot - j);
             const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
             if (!mbar_wait(&acce[b], bph ^ 1, P.status, abort)) break;
             tc_fence_after();
@@ -312,7 +342,9 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
           uint32_t acc[COLS];
 #pragma unroll
           for (int i = 0; i < COLS; ++i) acc[i] = 0;
-          const int nch = (nsteps(P, t, x.rs, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
+          const int ck = chunk_of<CRT>(P, t);
+          const int nch = (steps_of<CRT>(P, t, x.rs, x.KB) + ck - 1) / ck;
+          int since = 0;                          // drains since the last reduction
           for (int c = 0; c < nch; ++c, ++ch) {
             const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
             if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], bph, P.status, abort))) {
@@ -334,11 +366,21 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
               for (int i = 0; i < 32; ++i)
                 acc[32 * h + i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
             }
+            ++since;
+            if constexpr (CRT) {
+              if (since == kCrtReduceEvery && c + 1 < nch) {
+                const int pm = P.crt_p[t];
+                const uint32_t bs = (uint32_t)since * MAGIC_BITS;
+#pragma unroll
+                for (int i = 0; i < COLS; ++i) acc[i] = (uint32_t)((int32_t)(acc[i] - bs) % pm);
+                since = 0;
+              }
+            }
           }
           if (!ok) break;
           if (r < x.M) {
             // planes are column-major: lanes (consecutive rows) store consecutive words
-            const uint32_t bias = (uint32_t)nch * MAGIC_BITS;
+            const uint32_t bias = (uint32_t)since * MAGIC_BITS;
             if constexpr (STACK) {
               const int nd = min(x.rs, x.t1 - t + 1);     // diagonals of this block to keep
               int j = (int)(c0 / x.N);
@@ -457,9 +499,16 @@ int make_map_2d(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows,
 int launch_product(const ProductLaunch &a, cudaStream_t s) {
   const int G = n_groups(a.D, a.group);
   if (G > MAX_GROUPS) return fail(MW_EUNSUPPORTED, "more than %d diagonal groups", MAX_GROUPS);
-  if (a.chunk < BK || a.chunk % BK) return fail(MW_EINVAL, "chunk must be a positive multiple of 64");
-  if (a.w < 2 || a.w > 8 || (int64_t)a.chunk << (2 * a.w - 2) > (1 << 22))
-    return fail(MW_EINVAL, "chunk * 2^(2w-2) must not exceed 2^22 (w=%d chunk=%d)", a.w, a.chunk);
+  if (a.crt) {
+    if (a.D > crt_table_size() || a.info || !a.narrow)
+      return fail(MW_EINVAL, "residue form: single products, at most %d moduli", crt_table_size());
+  } else {
+    if (a.chunk < BK || a.chunk % BK)
+      return fail(MW_EINVAL, "chunk must be a positive multiple of 64");
+    if (a.w < 2 || a.w > 8 || (int64_t)a.chunk << (2 * a.w - 2) > (1 << 22))
+      return fail(MW_EINVAL, "chunk * 2^(2w-2) must not exceed 2^22 (w=%d chunk=%d)", a.w,
+                  a.chunk);
+  }
   if (a.rowsA > 0x7fffffffLL || a.rowsB > 0x7fffffffLL)
     return fail(MW_EUNSUPPORTED, "more than 2^31 piece rows");
   // 128 x 256 tiles for a single wide product in narrow mode (half the A-operand
@@ -472,7 +521,12 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   P.item_problem = a.item_problem;
   P.count = a.count;
   P.S_A = a.S_A; P.S_B = a.S_B; P.D = a.D; P.w = a.w; P.group = a.group; P.G = G;
-  P.chunk_kb = a.chunk / BK;
+  P.chunk_kb = a.crt ? 1 : a.chunk / BK;
+  if (a.crt)
+    for (int t = 0; t < a.D; ++t) {
+      P.crt_chunk_kb[t] = (uint8_t)(crt_chunk(t) / BK);
+      P.crt_p[t] = (uint16_t)crt_modulus(t);
+    }
   P.partials = a.partials;
   P.next_item = a.next_item;
   P.status = status_ptr();
@@ -490,7 +544,7 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   for (int g = 0; g < G; ++g) {
     cost[g] = 0;
     for (int t = g * a.group; t < std::min(a.D, (g + 1) * a.group); ++t)
-      cost[g] += std::max(0, std::min(t, a.S_A - 1) - std::max(0, t - a.S_B + 1) + 1);
+      cost[g] += a.crt ? 1 : std::max(0, std::min(t, a.S_A - 1) - std::max(0, t - a.S_B + 1) + 1);
     P.gorder[g] = g;
   }
   for (int i = 1; i < G; ++i)
@@ -520,6 +574,14 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
       e = cudaFuncSetAttribute(ozaki_kernel<256, true, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)Shape<256, true>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ozaki_kernel<256, true, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Shape<256, true>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ozaki_kernel<128, true, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Shape<128, true>::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "product kernel smem attribute");
     attr_set = true;
   }
@@ -533,7 +595,11 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   using S256 = Shape<256, true>;
   using S128 = Shape<128, true>;
   using W128 = Shape<128, false>;
-  if (a.narrow && bn == 256 && a.info)
+  if (a.crt && bn == 256)
+    ozaki_kernel<256, true, false, true><<<grid, S256::THREADS, S256::SMEM, s>>>(maps, P);
+  else if (a.crt)
+    ozaki_kernel<128, true, false, true><<<grid, S128::THREADS, S128::SMEM, s>>>(maps, P);
+  else if (a.narrow && bn == 256 && a.info)
     ozaki_kernel<256, true, true><<<grid, S256::THREADS, S256::SMEM, s>>>(maps, P);
   else if (a.narrow && bn == 256)
     ozaki_kernel<256, true, false><<<grid, S256::THREADS, S256::SMEM, s>>>(maps, P);
@@ -562,12 +628,18 @@ size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow)
 int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()> &between_kernels) {
   if (a.Kp % BK) return fail(MW_EINVAL, "padded K must be a multiple of %d", BK);
   const int G = n_groups(a.D, a.group);
-  const bool narrow = narrow_partials(a.S_A, a.S_B, a.w, a.Kp);
+  // the residue form keeps one int32 sum per modulus (reduced mod p as it goes)
+  const bool narrow = a.crt || narrow_partials(a.S_A, a.S_B, a.w, a.Kp);
   ProductLaunch L{};
   L.pieceA = a.dA; L.pieceB = a.dB;
-  L.rowsA = (int64_t)a.S_A * a.M; L.rowsB = (int64_t)a.S_B * a.N; L.Kpitch = a.Kp;
+  // rows the piece arrays hold: S_A / S_B digit planes, or D residue planes (the
+  // tensor maps' extent, beyond which TMA fills zeros)
+  L.rowsA = (int64_t)(a.crt ? a.D : a.S_A) * a.M;
+  L.rowsB = (int64_t)(a.crt ? a.D : a.S_B) * a.N;
+  L.Kpitch = a.Kp;
   L.S_A = a.S_A; L.S_B = a.S_B; L.D = a.D; L.w = a.w; L.chunk = a.chunk;
-  L.group = sched_group(a.D, a.group, narrow);
+  L.group = a.crt ? 1 : sched_group(a.D, a.group, narrow);
+  L.crt = a.crt;
   L.info = nullptr; L.hdr = nullptr; L.count = 1;
   L.M = a.M; L.N = a.N; L.K = a.Kp;
   L.partials = a.partials;
@@ -578,7 +650,7 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
   int rc = launch_product(L, s);
   if (rc) return rc;
   if (between_kernels) between_kernels();
-  return launch_combine(a, G, narrow, s);
+  return a.crt ? launch_crt_combine(a, s) : launch_combine(a, G, narrow, s);
 }
 
 }  // namespace mw

@@ -259,6 +259,7 @@ int launch_split(const SplitArgs &a, bool exponents_only, cudaStream_t s) {
       a.R, a.exps, a.spread, a.max_spread, a.range, status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split finalize launch");
   if (exponents_only) return MW_OK;
+  if (a.nmod > 0) return launch_residues(a, s);
   if (a.format == MW_DIGITS_BF16) return launch_pieces_m<__nv_bfloat16>(a, s);
   return launch_pieces_m<double>(a, s);
 }
