@@ -65,6 +65,9 @@ def parse():
                     help="headline: Ozaki forms to time (ozaki = digit slices, crt = residues)")
     ap.add_argument("--mode", default="crt", choices=["ozaki", "crt"],
                     help="single workloads: the form to time")
+    ap.add_argument("--size", type=int, default=0,
+                    help="single workloads: M = N = K (0 = the workload's own size; smaller "
+                         "sizes of the same recipe are for profiling)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="headline: leave out the quad-double 1024^3 sub-record")
     ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8, 16],
@@ -224,9 +227,10 @@ WORKLOADS = {
 }
 
 
-def single_inputs(name):
+def single_inputs(name, size=0):
     import synthetic
     m, n, gen, _ = WORKLOADS[name]
+    n = size or n
     if gen == "qd_1024":
         return synthetic.qd_1024(seed=1, n=n)
     return synthetic.ozaki_4096(m, seed=2, n=n)
@@ -524,7 +528,10 @@ def e2e_count(args):
 def run_single(args, name, mw, torch, dist, rank, world, dev):
     """One of the single-product workloads on its own (profiling and sweeps)."""
     m, n, _, desc = WORKLOADS[name]
-    A, B = single_inputs(name)
+    if args.size:
+        n = args.size
+        desc = desc.replace("M=N=K=4096", f"M=N=K={n}").replace("M=N=K=1024", f"M=N=K={n}")
+    A, B = single_inputs(name, args.size)
     pipes = measure_pipes(torch, dev)
     cpu_s = 0.0 if args.no_cpu else args.cpu_seconds
     rec = measure_single(args, mw, torch, dist, rank, dev, A, B, name, mode=args.mode,

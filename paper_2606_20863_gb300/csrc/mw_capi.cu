@@ -391,7 +391,10 @@ cudaStream_t side_stream() {
 int split_both(const mw_plan &p, int transA, int transB, int64_t M, int64_t N, int64_t K,
                const double *A, int64_t lda, int64_t psa, const double *B, int64_t ldb,
                int64_t psb, void *ws, const Layout &L, bool exps_only, cudaStream_t s) {
-  cudaStream_t s2 = side_stream();
+  // residue splits hold tensor memory on every SM they run on: with more than
+  // 64 moduli two of them would not fit side by side, so they run one after the
+  // other on the caller's stream
+  cudaStream_t s2 = (p.mode == MW_CRT && !exps_only && p.D > 64) ? nullptr : side_stream();
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool fork = s2 != nullptr &&
               cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess &&

@@ -21,6 +21,7 @@
 // This file holds the table of moduli, the residue split and the
 // reconstruction; the product kernel is the slice form's, one pair per modulus.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cmath>
 #include <vector>
@@ -29,32 +30,46 @@
 #include "mw_device.cuh"
 #include "mw_internal.h"
 #include "mw_pieces.cuh"
+#include "mw_tc.cuh"
 
 namespace mw {
 namespace {
 
-// Pairwise coprime moduli, at most 513 (balanced residues within bfloat16's
-// exact integers).  The set: greedy from 363 downwards (keep a number when it
-// is coprime to every number kept), then every prime in 364..513.  The order:
-// by bits per tensor-core product, log2(p), divided by 1.15 for the moduli
-// above 363, whose products need a drain every 64 products (a drain is due
-// before chunk * floor(p/2)^2 passes 2^22: 256 products for p <= 257, 128 for
-// p <= 363, 64 for p <= 513).  A product uses the first n moduli.
+// Pairwise coprime odd moduli, at most 513 (balanced residues within
+// bfloat16's exact integers; odd, so that no sum lies halfway between two
+// multiples of a modulus and the rounding of z / p below needs no correction).
+// An fp32 sum of `chunk` products of residues stays exact below 2^22 when
+// chunk floor(p/2)^2 <= 2^22: 1024 products for p <= 129, 512 for p <= 181, 256
+// for p <= 257, 128 for p <= 363, 64 for p <= 513.  A modulus costs the tensor
+// cores one product of residue matrices, k-blocks of 64 at about 625 cycles a
+// 128 x 256 tile, plus one drain of its fp32 accumulators every chunk, about 775
+// cycles (both measured on GB300).  The table: greedy by log2(p) / cost at
+// K = 4096, each step the best odd number coprime to every one taken; a
+// product uses the first n moduli.
 constexpr uint16_t kModuli[] = {
-    363, 362, 361, 359, 355, 353, 349, 347, 343, 337, 331, 317, 313, 311, 307, 299,
-    293, 289, 283, 281, 277, 271, 269, 263, 257, 251, 241, 239, 233, 229, 227, 509,
-    503, 223, 499, 491, 487, 479, 211, 467, 463, 461, 457, 449, 443, 199, 439, 197,
-    433, 431, 193, 421, 191, 419, 409, 401, 397, 179, 389, 383, 379, 173, 373, 367,
-    167, 163, 157, 151, 149, 139, 137, 131, 127, 113, 109, 107, 103, 101, 97,  89,
-    83,  79,  73,  67,  61,  59,  53,  47,  43,  41,  37,  31,  29};
+    129, 181, 127, 179, 125, 173, 121, 169, 119, 167, 163, 113, 157, 109, 151, 107,
+    149, 103, 101, 139, 137, 97,  257, 131, 251, 241, 239, 89,  233, 229, 227, 223,
+    83,  211, 79,  199, 197, 193, 191, 73,  71,  67,  61,  59,  53,  361, 359, 353,
+    349, 347, 337, 331, 47,  317, 313, 311, 307, 293, 283, 281, 277, 271, 269, 41,
+    263, 37,  31,  29,  23,  509, 503, 499, 491, 487, 479, 467, 463, 461, 457, 449,
+    443, 439, 433, 431, 421, 419, 409, 401, 397, 389, 383, 379, 373, 367};
 constexpr int kNumModuli = sizeof(kModuli) / sizeof(kModuli[0]);
 static_assert(kNumModuli <= kCrtMaxModuli, "moduli table too long");
+constexpr bool all_odd() {
+  for (int i = 0; i < kNumModuli; ++i)
+    if (kModuli[i] % 2 == 0 || kModuli[i] > 513) return false;
+  return true;
+}
+static_assert(all_odd(), "the moduli must be odd and at most 513");
 constexpr int kPow16 = 65;   // 2^(16 j) mod p for j = 0..64 (T of up to 16 64-bit limbs)
 
-// Per modulus: p, floor(2^32 / p) for reducing 32-bit values, 2^(16 j) mod p.
+// Per modulus: p, floor(2^32 / p) for reducing 32-bit values, p and 1/p in
+// float (table entries, so that no conversion instruction runs per residue),
+// and 2^(16 j) mod p.
 struct CrtTab {
   uint32_t p[kCrtMaxModuli];
   uint32_t m32[kCrtMaxModuli];
+  float pf[kCrtMaxModuli], rcp[kCrtMaxModuli];
   uint32_t pow16[kCrtMaxModuli][kPow16];
 };
 constexpr CrtTab make_crt_tab() {
@@ -63,6 +78,8 @@ constexpr CrtTab make_crt_tab() {
     const uint32_t p = kModuli[i];
     t.p[i] = p;
     t.m32[i] = (uint32_t)((1ull << 32) / p);
+    t.pf[i] = (float)p;
+    t.rcp[i] = 1.0f / (float)p;
     uint32_t x = 1u % p;
     for (int j = 0; j < kPow16; ++j) {
       t.pow16[i][j] = x;
@@ -84,6 +101,29 @@ __device__ __forceinline__ int balanced(uint32_t r, uint32_t p) {
   return r >= p - (p >> 1) ? (int)r - (int)p : (int)r;
 }
 
+// The balanced residue of an exactly represented float integer z (|z| < 2^22)
+// modulo an odd p, in [-floor(p/2), floor(p/2)]: z - q p with q the nearest
+// integer to z / p.  fmaf(z, 1/p, 1.5 2^23) rounds the exact product z fl(1/p)
+// to an integer; that product differs from z / p by less than |z| 2^-24 / p <
+// 1 / (4p), while an integer z over an odd p lies at least 1 / (2p) from any
+// half integer, so q is the nearest integer to z / p itself.  Every step is
+// exact (|q p| < 2^23).
+__device__ __forceinline__ float balanced_f(float z, int t) {
+  const float q = fmaf(z, kCrt.rcp[t], 12582912.0f) - 12582912.0f;
+  return fmaf(-q, kCrt.pf[t], z);
+}
+
+// bfloat16 bits of an integer-valued float of magnitude at most 256 (at most 8
+// significant bits): its top 16 bits.
+__device__ __forceinline__ uint16_t bf16_bits_small(float r) {
+  return (uint16_t)(__float_as_uint(r) >> 16);
+}
+
+// The float of an integer |d| <= 2^22 without a conversion instruction.
+__device__ __forceinline__ float small_int_float(int d) {
+  return __uint_as_float(0x4B400000u + (uint32_t)d) - 12582912.0f;
+}
+
 // T in [-2^(L-1), 2^(L-1)): every bit from L-1 up equals the sign.
 template <int NL>
 __device__ __forceinline__ bool in_range_bits(const uint64_t (&T)[NL], int L) {
@@ -99,125 +139,226 @@ __device__ __forceinline__ bool in_range_bits(const uint64_t (&T)[NL], int L) {
   return ok;
 }
 
-// Balanced residues of two fixed-point values (entries k, k+1 of one row)
-// modulo the first nmod moduli, stored as bfloat16 pairs in planes 0..nmod-1.
-// T = sum_j v_j 2^(16 j) - s 2^(64 NL) with 16-bit pieces v_j and the sign s,
-// so T mod p = sum_j v_j (2^(16j) mod p) + s (p - 2^(64 NL) mod p), a sum below
-// 64 NL 2^25 + 2^9 <= 2^32 for NL <= 16.
-template <int MW, int NL>
-__device__ __forceinline__ void residue_pair(const double (&w0)[MW], const double (&w1)[MW], int F,
-                                             int L, int nmod, __nv_bfloat16 *dst, int64_t plane,
-                                             unsigned int *status) {
-  uint64_t T0[NL], T1[NL];
-  fixed_point<MW, NL>(w0, F, T0);
-  fixed_point<MW, NL>(w1, F, T1);
-  if (!(in_range_bits<NL>(T0, L) && in_range_bits<NL>(T1, L))) raise_status(status, MW_ERANGE);
-  const bool n0 = (int64_t)T0[NL - 1] < 0, n1 = (int64_t)T1[NL - 1] < 0;
-  uint32_t v0[4 * NL], v1[4 * NL];
-#pragma unroll
-  for (int l = 0; l < NL; ++l)
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      v0[4 * l + h] = (uint32_t)(T0[l] >> (16 * h)) & 0xFFFFu;
-      v1[4 * l + h] = (uint32_t)(T1[l] >> (16 * h)) & 0xFFFFu;
-    }
-  for (int i = 0; i < nmod; ++i) {
-    const uint32_t p = kCrt.p[i], m32 = kCrt.m32[i];
-    const uint32_t top = p - kCrt.pow16[i][4 * NL];
-    uint32_t s0 = n0 ? top : 0u, s1 = n1 ? top : 0u;
-#pragma unroll
-    for (int j = 0; j < 4 * NL; ++j) {
-      const uint32_t c = kCrt.pow16[i][j];
-      s0 += v0[j] * c;
-      s1 += v1[j] * c;
-    }
-    const int r0 = balanced(mod_u32(s0, p, m32), p), r1 = balanced(mod_u32(s1, p, m32), p);
-    *reinterpret_cast<uint32_t *>(dst + (int64_t)i * plane) =
-        (uint32_t)small_int_bf16(r0) | ((uint32_t)small_int_bf16(r1) << 16);
-  }
-}
+// ---- residue split on the tensor cores -------------------------------------------
+// T = sum_q d_q 2^(8q) with balanced base-256 digits d_q (|d| <= 128, the digits
+// the slice form cuts with w = 8), so T mod p_t = sum_q d_q c_qt mod p_t with
+// c_qt = 2^(8q) mod p_t taken balanced (|c| <= 256).  One MMA per tile of 128
+// entries: A (128 x 64) holds the digits of the tile's entries, written by the
+// threads; B (64 x n) the constants c_qt, built once per CTA, zero for q >= S;
+// both in fp16 (exact for integers up to 2048).  The fp32 sums
+// |sum_q d_q c_qt| <= 64 2^15 = 2^21 are exact, and the epilogue reduces them
+// mod p_t (balanced_f) into the bfloat16 residue planes.
+// Digits from bytes: with H = 128 (1 + 2^8 + ... + 2^(8(S-2))), byte q of T + H
+// is d_q + 128 for q < S-1; the fp16 number with exponent field 0x64 and that
+// byte as low mantissa bits is 1024 + byte, so one byte permute and one packed
+// fp16 add of -1152 give two digits.  Every column gets byte - 128, the top
+// one too, whose digit is byte S-1 less 256 for a negative T + H: the
+// difference, +128 or -128, goes into column 63, whose constants are those of
+// column S-1 (S <= 48).  The other columns q >= S multiply zero constants and
+// may hold anything finite.
+// TRANS = false: a tile is 128 consecutive k of one row r; TRANS = true (the
+// operand stored K x R): 4 consecutive r x 32 consecutive k, so that the loads
+// along r and the stores along k both fill whole sectors.
+constexpr int kResTile = 128;
+constexpr uint32_t kTileBytes = 128 * 128;        // 128 rows x 64 bf16
 
-// trans = 0: one thread per (row, pair of columns), pairs over the padded width.
-template <int MW, int NL>
-__global__ void residues_rows_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t ld,
-                                     int64_t ps, int L, int nmod, __nv_bfloat16 *res,
-                                     int64_t dld, const int *E, unsigned int *status) {
-  const int64_t npair = dld / 2;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= R * npair) return;
-  const int64_t r = idx / npair, k = 2 * (idx % npair);
-  double a[MW], b[MW];
-  const bool v0 = k < K, v1 = k + 1 < K;
-  const double *row = X + r * ld;
-  const bool vec = v1 && ((((uintptr_t)(row + k)) & 15) == 0) && ((ps & 1) == 0);
-#pragma unroll
-  for (int j = 0; j < MW; ++j) {
-    if (vec) {
-      const double2 v = *reinterpret_cast<const double2 *>(row + j * ps + k);  // 128-bit load
-      a[j] = v.x;
-      b[j] = v.y;
-    } else {
-      a[j] = v0 ? row[j * ps + k] : 0.0;
-      b[j] = v1 ? row[j * ps + k + 1] : 0.0;
-    }
-  }
-  residue_pair<MW, NL>(a, b, L - 2 - E[r], L, nmod, res + r * dld + k, R * dld, status);
-}
+template <int MW>
+struct SplitEntry {      // one thread's entry of a tile: position and words
+  int64_t r, k;
+  bool valid;
+  double x[MW];
+};
 
-// trans = 1: 32 x 32 tiles (32 rows r, 32 columns k of the logical operand)
-// staged through shared memory, then reduced like trans = 0.
-template <int MW, int NL>
-__global__ void residues_cols_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t ld,
-                                     int64_t ps, int L, int nmod, __nv_bfloat16 *res,
-                                     int64_t dld, const int *E, unsigned int *status) {
-  extern __shared__ double tile[];  // [m][32 k][33]
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int64_t r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-#pragma unroll
-  for (int j = 0; j < MW; ++j)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int kl = ty + 8 * i;
-      const int64_t k = k0 + kl, r = r0 + tx;
-      tile[(j * 32 + kl) * 33 + tx] = (k < K && r < R) ? X[j * ps + k * ld + r] : 0.0;
+template <int MW, int NL, bool TRANS>
+__global__ void __launch_bounds__(kResTile, 2)
+    residues_mma_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t ld,
+                        int64_t ps, int L, int S, int nmod, int npad, __nv_bfloat16 *res,
+                        int64_t dld, const int *E, unsigned int *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);  // 2 tiles
+  uint8_t *sB = sA + 2 * kTileBytes;               // npad rows x 64
+  uint64_t *bar = (uint64_t *)(sB + (size_t)npad * 128);
+  uint32_t *holder = (uint32_t *)(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int idx = tid; idx < npad * 64; idx += kResTile) {
+    const int t = idx >> 6, qc = idx & 63;
+    const int q = qc == 63 ? S - 1 : qc;       // column 63 repeats the top digit's
+    int c = 0;
+    if (t < nmod && (q < S || qc == 63)) {
+      const uint32_t p = kCrt.p[t];
+      uint32_t x = kCrt.pow16[t][q >> 1];
+      if (q & 1) x = mod_u32(x * 256u, p, kCrt.m32[t]);
+      c = balanced(x, p);
     }
+    *reinterpret_cast<uint16_t *>(sB + sw128_offset(t, qc)) = __half_as_ushort(__int2half_rn(c));
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  // two accumulator regions, one per tile in flight
+  const uint32_t ncols = npad <= 64 ? 128u : 256u, region = ncols / 2;
+  if (warp == 0) tmem_alloc(holder, ncols);
+  fence_proxy_async_smem();
   __syncthreads();
-  const int tid = ty * 32 + tx;
-  for (int it = 0; it < 2; ++it) {
-    const int e = tid + 256 * it;      // 512 pairs per tile
-    const int rl = e >> 4, kl = 2 * (e & 15);
-    const int64_t r = r0 + rl, k = k0 + kl;
-    if (r >= R || k >= dld) continue;
-    double a[MW], b[MW];
-#pragma unroll
-    for (int j = 0; j < MW; ++j) {
-      a[j] = tile[(j * 32 + kl) * 33 + rl];
-      b[j] = tile[(j * 32 + kl + 1) * 33 + rl];
+  tc_fence_after();
+  const uint32_t tmem = *holder;
+  const uint32_t idesc = idesc_f16(128, npad);
+  const int64_t ktiles = TRANS ? (dld + 31) / 32 : (dld + 127) / 128;
+  const int64_t ntiles = (TRANS ? (R + 3) / 4 : R) * ktiles;
+  const int64_t plane = R * dld;
+  volatile int abort_flag = 0;
+
+  auto fetch = [&](int64_t tile, SplitEntry<MW> &e) {
+    e.valid = false;
+    e.r = e.k = 0;
+    if (tile < ntiles) {
+      const int64_t rt = tile / ktiles, kt = tile - rt * ktiles;
+      e.r = TRANS ? rt * 4 + (tid & 3) : rt;
+      e.k = TRANS ? kt * 32 + (tid >> 2) : kt * 128 + tid;
+      e.valid = e.r < R && e.k < dld;
     }
-    residue_pair<MW, NL>(a, b, L - 2 - E[r], L, nmod, res + r * dld + k, R * dld, status);
+    const bool in = e.valid && e.k < K;
+#pragma unroll
+    for (int j = 0; j < MW; ++j)
+      e.x[j] = in ? (TRANS ? X[j * ps + e.k * ld + e.r] : X[j * ps + e.r * ld + e.k]) : 0.0;
+  };
+  // digits of the entry into row tid of A tile `slot`, then the tile's MMA
+  auto stage = [&](int slot, const SplitEntry<MW> &e) {
+    uint64_t T[NL];
+    fixed_point<MW, NL>(e.x, e.valid ? L - 2 - E[e.r] : 0, T);
+    if (e.valid && !in_range_bits<NL>(T, L)) raise_status(status, MW_ERANGE);
+    const bool neg = add_bias_w8<NL>(T, S);
+    uint8_t *a = sA + slot * kTileBytes;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {               // 16-byte chunk c: digits 8c .. 8c+7
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      if (c < NL) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t word = (uint32_t)(T[c < NL ? c : 0] >> (32 * h));
+          uint32_t lo, hi;
+          asm("prmt.b32 %0, %1, %2, 0x5140;" : "=r"(lo) : "r"(word), "r"(0x64646464u));
+          asm("prmt.b32 %0, %1, %2, 0x7362;" : "=r"(hi) : "r"(word), "r"(0x64646464u));
+          asm("add.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * h]) : "r"(lo), "r"(0xE480E480u));
+          asm("add.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * h + 1]) : "r"(hi), "r"(0xE480E480u));
+        }
+      }
+      if (c == 7) w[3] = neg ? 0xD8000000u : 0x58000000u;   // column 63: -128 / +128 in fp16
+      *reinterpret_cast<uint4 *>(a + sw128_offset(tid, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint64_t ad = sw128_desc(smem_u32(a)), bd = sw128_desc(smem_u32(sB));
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc_mma(tmem + slot * region, ad + 2 * kk, bd + 2 * kk, idesc, kk ? 1u : 0u);
+      tc_commit(&bar[slot]);
+    }
+  };
+  // wait for the tile's MMA, reduce every sum mod p_t and store the residues
+  auto drain = [&](int slot, uint32_t parity, const SplitEntry<MW> &e) -> bool {
+    if (!__syncthreads_and(mbar_wait(&bar[slot], parity, status, &abort_flag))) return false;
+    tc_fence_after();
+    const uint32_t ta = tmem + slot * region + ((uint32_t)(warp * 32) << 16);
+    uint16_t *dst = reinterpret_cast<uint16_t *>(res + e.r * dld + e.k);
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {               // 32 moduli at a time
+      if (32 * h >= npad) break;
+      uint32_t v[32];
+      if (32 * h + 32 <= npad) tc_ld32(ta + 32 * h, v);
+      else tc_ld16(ta + 32 * h, v);
+      tc_wait_ld();
+      if (e.valid) {
+        if (32 * h + 32 <= nmod) {              // a whole chunk: no bound per modulus
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            *dst = bf16_bits_small(balanced_f(__uint_as_float(v[u]), 32 * h + u));
+            dst += plane;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            if (32 * h + u >= nmod) break;
+            *dst = bf16_bits_small(balanced_f(__uint_as_float(v[u]), 32 * h + u));
+            dst += plane;
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    return true;
+  };
+
+  // two tiles in flight: the next tile's MMA runs while this one drains, and
+  // the words of the tile after it are loaded before this drain
+  int64_t cur = blockIdx.x;
+  if (cur < ntiles) {
+    SplitEntry<MW> ec, en, e2;
+    fetch(cur, ec);
+    stage(0, ec);
+    fetch(cur + gridDim.x, en);
+    uint32_t ph0 = 0, ph1 = 0;
+    int slot = 0;
+    for (;;) {
+      const int64_t nxt = cur + gridDim.x;
+      if (nxt < ntiles) stage(slot ^ 1, en);
+      fetch(nxt + gridDim.x, e2);
+      if (!drain(slot, slot ? ph1 : ph0, ec)) break;
+      if (slot) ph1 ^= 1; else ph0 ^= 1;
+      if (nxt >= ntiles) break;
+      ec = en;
+      en = e2;
+      cur = nxt;
+      slot ^= 1;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tmem, ncols);
   }
 }
 
 template <int MW, int NL>
 int launch_residues_t(const SplitArgs &a, cudaStream_t s) {
   auto *res = static_cast<__nv_bfloat16 *>(a.digits);
-  if (!a.trans) {
-    const int64_t n = a.R * (a.digit_ld / 2);
-    const int threads = 256;
-    residues_rows_kernel<MW, NL><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
-        a.X, a.R, a.K, a.ld, a.plane_stride, a.S, a.nmod, res, a.digit_ld, a.exps, status_ptr());
-  } else {
-    dim3 grid((unsigned)((a.R + 31) / 32), (unsigned)((a.digit_ld + 31) / 32));
-    const size_t sm = (size_t)MW * 32 * 33 * sizeof(double);
-    static bool attr_set = false;  // once per instantiation
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(residues_cols_kernel<MW, NL>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int S = (a.S + 7) / 8;                     // base-256 digits of an L-bit T
+  const int npad = (a.nmod + 15) / 16 * 16;
+  if (S > 8 * NL || S > 48 || NL > 6 || npad > 96)
+    return fail(MW_EUNSUPPORTED, "residue split: %d digits, %d moduli", S, a.nmod);
+  const size_t smem = 1024 + 2 * kTileBytes + (size_t)npad * 128 + 32;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ktiles = a.trans ? (a.digit_ld + 31) / 32 : (a.digit_ld + 127) / 128;
+  const int64_t ntiles = (a.trans ? (a.R + 3) / 4 : a.R) * ktiles;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, 2 * (int64_t)nsm);
+  if (a.trans) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(residues_mma_kernel<MW, NL, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 49152);
       if (e != cudaSuccess) return cuda_fail(e, "residue split smem attribute");
-      attr_set = true;
+      attr = true;
     }
-    residues_cols_kernel<MW, NL><<<grid, dim3(32, 8), sm, s>>>(
-        a.X, a.R, a.K, a.ld, a.plane_stride, a.S, a.nmod, res, a.digit_ld, a.exps, status_ptr());
+    residues_mma_kernel<MW, NL, true><<<grid, kResTile, smem, s>>>(
+        a.X, a.R, a.K, a.ld, a.plane_stride, a.S, S, a.nmod, npad, res, a.digit_ld, a.exps,
+        status_ptr());
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(residues_mma_kernel<MW, NL, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 49152);
+      if (e != cudaSuccess) return cuda_fail(e, "residue split smem attribute");
+      attr = true;
+    }
+    residues_mma_kernel<MW, NL, false><<<grid, kResTile, smem, s>>>(
+        a.X, a.R, a.K, a.ld, a.plane_stride, a.S, S, a.nmod, npad, res, a.digit_ld, a.exps,
+        status_ptr());
   }
   return cuda_fail(cudaGetLastError(), "residue split launch");
 }
@@ -231,63 +372,252 @@ int launch_residues_nl(const SplitArgs &a, cudaStream_t s) {
   return fail(MW_EUNSUPPORTED, "residue form: %d fixed-point bits (at most 381)", a.S);
 }
 
-// ---- reconstruction -----------------------------------------------------------
-// Constants of the first D moduli, computed on the host for every launch and
-// passed by value (kernel parameters, so that a captured launch keeps them).
+// ---- reconstruction on the tensor cores ----------------------------------------------
+// With r_t the balanced residue of Y_t mod p_t and Q'_t = inv_t (P / p_t), where
+// inv_t = (P / p_t)^(-1) mod p_t, X' = sum_t r_t Q'_t = X mod P and
+// X'/P = sum_t r_t inv_t / p_t, so X = X' - k P with k = round(sum_t r_t inv_t / p_t)
+// (|X| < P/8 leaves that sum within 1/8 of k; its float evaluation errs by less
+// than 0.13 for D <= 96, |r_t| <= 256).  Modulo 2^(32 NL32) (enough for |X| < P/8)
+// X' = sum_n z_n 2^(8n) with z_n = sum_t r_t b_tn, b_tn the balanced bytes of
+// Q'_t mod 2^(32 NL32): one MMA per tile of 128 outputs, A (128 x D) the residues
+// written by the threads, B (D x 4 NL32) the bytes; |z_n| <= 96 2^15 < 2^22, exact
+// in fp32.  The epilogue joins the z_n into 32-bit limbs (Horner, as the slice
+// form's fusion joins its diagonal sums), subtracts k P and rounds into m words.
 struct CrtFuse {
-  int D, pad;
-  uint32_t p[kCrtMaxModuli], m32[kCrtMaxModuli], inv[kCrtMaxModuli], c31[kCrtMaxModuli];
-  float rcp[kCrtMaxModuli];
-  uint32_t Q[kCrtMaxModuli][kCrtMaxLimbs];   // P / p_i, 32-bit limbs
+  int D, nlimb;
+  uint32_t p[kCrtMaxModuli], m32[kCrtMaxModuli], c31[kCrtMaxModuli];
+  float rk[kCrtMaxModuli];                         // inv_t / p_t
+  int8_t qb[kCrtMaxModuli][4 * kCrtMaxLimbs];      // balanced bytes of Q'_t
   uint32_t P[kCrtMaxLimbs];
 };
 
-// One thread per output (i along the column-major planes): Y_t -> y_t ->
-// X = sum_t y_t Q_t - k P in NL32 32-bit limbs (two's complement, mod 2^(32 NL32),
-// enough for |X| < P/8), then the greedy words of X 2^(E_i + E_j + ex0).
+template <int NL32>
+struct FuseSizes {
+  static constexpr int NB = 4 * NL32;              // byte positions, N of the MMA
+  // moduli a thread loads: a product of 32 NL32 bits needs at most 5 NL32 of the
+  // table's moduli (every modulus has more than 6.4 bits), at most 96
+  static constexpr int DMAX = 5 * NL32 < 96 ? (5 * NL32 + 7) / 8 * 8 : 96;
+};
+
 template <int MW, int NL32>
-__global__ void __launch_bounds__(128) crt_combine_kernel(
-    const int32_t *__restrict__ partials, const int32_t *eA, const int32_t *eB, int64_t M,
-    int64_t N, int ex0, double *C, int64_t ldc, int64_t psc, const __grid_constant__ CrtFuse F) {
-  __shared__ uint32_t limbs[NL32][128];
-  const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
-  if (i >= M || j >= N) return;
-  uint64_t acc[NL32];
-#pragma unroll
-  for (int l = 0; l < NL32; ++l) acc[l] = 0;
-  float kf = 0.f;
-  const int32_t *y_in = partials + j * M + i;
+__global__ void __launch_bounds__(128, 2)
+    crt_fuse_mma_kernel(const int32_t *__restrict__ partials, const int32_t *eA,
+                        const int32_t *eB, int64_t M, int64_t N, int ex0, double *C, int64_t ldc,
+                        int64_t psc, unsigned int *status, const __grid_constant__ CrtFuse F) {
+  constexpr int NB = FuseSizes<NL32>::NB, DMAX = FuseSizes<NL32>::DMAX;
+  extern __shared__ uint8_t smem_raw[];
+  const int kc = (F.D + 63) / 64;                  // K chunks of 64 moduli
+  uint8_t *sA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);  // 2 x kc tiles
+  uint8_t *sB = sA + 2 * kc * kTileBytes;          // kc chunks of NB rows x 64
+  uint32_t *col = (uint32_t *)(sB + (size_t)kc * NB * 128);   // [NL32][128] rounding columns
+  uint64_t *bar = (uint64_t *)(col + NL32 * 128);
+  uint32_t *holder = (uint32_t *)(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int idx = tid; idx < kc * 64 * NB; idx += 128) {
+    const int t = idx / NB, n = idx - t * NB;
+    const int b = t < F.D ? F.qb[t][n] : 0;
+    *reinterpret_cast<uint16_t *>(sB + (t >> 6) * (NB * 128) + sw128_offset(n, t & 63)) =
+        small_int_bf16(b);
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(holder, 256);          // two regions of 128 columns (NB <= 96)
+  fence_proxy_async_smem();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *holder;
+  const uint32_t idesc = idesc_bf16(128, NB);
+  const int64_t itiles = (M + 127) / 128;
+  const int64_t ntiles = itiles * N;
   const int64_t plane = M * N;
-  int32_t nxt = y_in[0];
-  for (int t = 0; t < F.D; ++t) {
-    const int32_t v = nxt;
-    if (t + 1 < F.D) nxt = y_in[(t + 1) * plane];
-    const uint32_t p = F.p[t], m32 = F.m32[t];
-    // v mod p from v + 2^31 >= 0, then y = v (P/p)^(-1) mod p
-    int r = (int)mod_u32((uint32_t)v ^ 0x80000000u, p, m32) - (int)F.c31[t];
-    if (r < 0) r += (int)p;
-    const uint32_t y = mod_u32((uint32_t)r * F.inv[t], p, m32);
-    kf = fmaf((float)y, F.rcp[t], kf);
+  volatile int abort_flag = 0;
+
+  struct Out {
+    int64_t i, j;
+    bool valid;
+    float kf;
+  };
+  auto fetch = [&](int64_t tile, Out &o, int32_t (&Y)[DMAX]) {
+    o.valid = false;
+    o.i = o.j = 0;
+    if (tile < ntiles) {
+      o.j = tile / itiles;
+      o.i = (tile - o.j * itiles) * 128 + tid;
+      o.valid = o.i < M;
+    }
+    const int32_t *y = partials + o.j * M + (o.valid ? o.i : 0);
 #pragma unroll
-    for (int l = 0; l < NL32; ++l) acc[l] += (uint64_t)y * F.Q[t][l];
-  }
-  const uint32_t k = (uint32_t)rintf(kf);
-  uint32_t U[NL32];
-  uint64_t carry = 0, mc = 0;
-  uint32_t br = 0;
+    for (int t = 0; t < DMAX; ++t) Y[t] = (o.valid && t < F.D) ? y[t * plane] : 0;
+  };
+  // balanced residues of the Y_t into row tid of A tile `slot`, then the MMA
+  auto stage = [&](int slot, Out &o, const int32_t (&Y)[DMAX]) {
+    uint8_t *a = sA + slot * kc * kTileBytes;
+    float kf = 0.f;
 #pragma unroll
-  for (int l = 0; l < NL32; ++l) {
-    const uint64_t s = acc[l] + carry;
-    carry = s >> 32;
-    const uint64_t kp = (uint64_t)k * F.P[l] + mc;
-    mc = kp >> 32;
-    const uint64_t d = (uint64_t)(uint32_t)s - (uint32_t)kp - br;
-    U[l] = (uint32_t)d;
-    br = (uint32_t)(d >> 63);
+    for (int t0 = 0; t0 < 128; t0 += 8) {
+      if (t0 >= kc * 64) break;
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        int rr[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int t = t0 + u + e;
+          rr[e] = 0;
+          if (t < DMAX && t < F.D) {
+            const uint32_t p = F.p[t];
+            int r = (int)mod_u32((uint32_t)Y[t < DMAX ? t : 0] ^ 0x80000000u, p, F.m32[t]) -
+                    (int)F.c31[t];
+            if (r < 0) r += (int)p;
+            rr[e] = balanced((uint32_t)r, p);
+            kf = fmaf(small_int_float(rr[e]), F.rk[t], kf);
+          }
+        }
+        w[u >> 1] = (uint32_t)small_int_bf16(rr[0]) | ((uint32_t)small_int_bf16(rr[1]) << 16);
+      }
+      *reinterpret_cast<uint4 *>(a + (t0 >> 6) * kTileBytes + sw128_offset(tid, t0 & 63)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    o.kf = kf;
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int c = 0; c < kc; ++c) {
+        const uint64_t ad = sw128_desc(smem_u32(a + c * kTileBytes));
+        const uint64_t bd = sw128_desc(smem_u32(sB + c * NB * 128));
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          tc_mma(tmem + slot * 128, ad + 2 * kk, bd + 2 * kk, idesc, (c | kk) ? 1u : 0u);
+      }
+      tc_commit(&bar[slot]);
+    }
+  };
+  // X' from the byte sums, X = X' - k P, greedy words
+  auto drain = [&](int slot, uint32_t parity, const Out &o) -> bool {
+    if (!__syncthreads_and(mbar_wait(&bar[slot], parity, status, &abort_flag))) return false;
+    tc_fence_after();
+    uint32_t z[NB];
+    const uint32_t ta = tmem + slot * 128 + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int h = 0; h < NB / 32; ++h)
+      tc_ld32(ta + 32 * h, *reinterpret_cast<uint32_t(*)[32]>(z + 32 * h));
+    if constexpr (NB % 32) tc_ld16(ta + NB / 32 * 32, z + NB / 32 * 32);
+    tc_wait_ld();
+    tc_fence_before();
+    // X' mod 2^(32 NL32) in 32-bit limbs: limb l = sum of z_(4l+u) 2^(8u) plus the carry
+    uint32_t U[NL32];
+    int64_t Rc = 0;
+#pragma unroll
+    for (int l = 0; l < NL32; ++l) {
+      int64_t V = (int32_t)(__float_as_uint(__uint_as_float(z[4 * l + 3]) + 12582912.0f) -
+                            0x4B400000u);
+#pragma unroll
+      for (int u = 2; u >= 0; --u)
+        V = V * 256 + (int32_t)(__float_as_uint(__uint_as_float(z[4 * l + u]) + 12582912.0f) -
+                                0x4B400000u);
+      Rc += V;
+      U[l] = (uint32_t)Rc;
+      Rc >>= 32;
+    }
+    const int k = (int)rintf(o.kf);                // X = X' - k P (mod 2^(32 NL32))
+    const uint32_t ak = (uint32_t)(k < 0 ? -k : k);
+    uint64_t mc = 0;
+    uint32_t cb = 0;
+#pragma unroll
+    for (int l = 0; l < NL32; ++l) {
+      const uint64_t kp = (uint64_t)ak * F.P[l] + mc;
+      mc = kp >> 32;
+      const uint32_t lo = (uint32_t)kp;
+      if (k >= 0) {
+        const uint64_t d = (uint64_t)U[l] - lo - cb;
+        U[l] = (uint32_t)d;
+        cb = (uint32_t)(d >> 63);
+      } else {
+        const uint64_t s2 = (uint64_t)U[l] + lo + cb;
+        U[l] = (uint32_t)s2;
+        cb = (uint32_t)(s2 >> 32);
+      }
+    }
+    if (o.valid) {
+      double *c = C + o.i * ldc + o.j;
+      round_column<MW, NL32>(U, col + tid, 128, eA[o.i] + eB[o.j] + ex0,
+                             [&](int wd, double v) { c[wd * psc] = v; });
+    }
+    return true;
+  };
+
+  // two tiles in flight, the partial sums of the tile after them loaded before
+  // each drain
+  int64_t cur = blockIdx.x;
+  if (cur < ntiles) {
+    Out oc, on;
+    int32_t Y[DMAX];
+    fetch(cur, oc, Y);
+    stage(0, oc, Y);
+    fetch(cur + gridDim.x, on, Y);
+    uint32_t ph0 = 0, ph1 = 0;
+    int slot = 0;
+    for (;;) {
+      const int64_t nxt = cur + gridDim.x;
+      if (nxt < ntiles) stage(slot ^ 1, on, Y);
+      Out o2;
+      fetch(nxt + gridDim.x, o2, Y);
+      if (!drain(slot, slot ? ph1 : ph0, oc)) break;
+      if (slot) ph1 ^= 1; else ph0 ^= 1;
+      if (nxt >= ntiles) break;
+      oc = on;
+      on = o2;
+      cur = nxt;
+      slot ^= 1;
+    }
   }
-  double *c = C + i * ldc + j;
-  round_column<MW, NL32>(U, &limbs[0][threadIdx.x], 128, eA[i] + eB[j] + ex0,
-                         [&](int w, double x) { c[w * psc] = x; });
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tmem, 256);
+  }
+}
+
+template <int MW, int NL32>
+int launch_crt_combine_t(const OzakiArgs &a, const CrtFuse &F, cudaStream_t s) {
+  constexpr int NB = FuseSizes<NL32>::NB;
+  if (F.D > FuseSizes<NL32>::DMAX)
+    return fail(MW_EUNSUPPORTED, "residue form: %d moduli for %d limbs", F.D, NL32);
+  const int kc = (F.D + 63) / 64;
+  const size_t smem = 1024 + kc * (2 * kTileBytes + NB * 128) + NL32 * 128 * 4 + 32;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(crt_fuse_mma_kernel<MW, NL32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         1024 + 2 * (2 * kTileBytes + 96 * 128) + 24 * 128 * 4 + 32);
+    if (e != cudaSuccess) return cuda_fail(e, "reconstruction smem attribute");
+    attr = true;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = (a.M + 127) / 128 * a.N;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, 2 * (int64_t)nsm);
+  crt_fuse_mma_kernel<MW, NL32><<<grid, 128, smem, s>>>(
+      static_cast<const int32_t *>(a.partials), a.eA, a.eB, a.M, a.N, 4 - a.S_A - a.S_B, a.C,
+      a.ldc, a.psc, status_ptr(), F);
+  return cuda_fail(cudaGetLastError(), "residue reconstruction launch");
+}
+
+template <int MW>
+int launch_crt_combine_m(const OzakiArgs &a, const CrtFuse &F, cudaStream_t s) {
+  switch (F.nlimb) {
+    case 8: return launch_crt_combine_t<MW, 8>(a, F, s);
+    case 12: return launch_crt_combine_t<MW, 12>(a, F, s);
+    case 16: return launch_crt_combine_t<MW, 16>(a, F, s);
+    case 20: return launch_crt_combine_t<MW, 20>(a, F, s);
+    case 24: return launch_crt_combine_t<MW, 24>(a, F, s);
+  }
+  return fail(MW_EUNSUPPORTED, "residue form: %d limbs", F.nlimb);
 }
 
 // ---- host arithmetic on the constants ------------------------------------------
@@ -322,33 +652,15 @@ uint32_t inverse_mod(uint32_t a, uint32_t p) {   // a^(-1) mod p, gcd(a, p) = 1
   return (uint32_t)(t < 0 ? t + p : t);
 }
 
-template <int MW, int NL32>
-int launch_crt_combine_t(const OzakiArgs &a, const CrtFuse &F, cudaStream_t s) {
-  dim3 grid((unsigned)((a.M + 127) / 128), (unsigned)a.N);
-  crt_combine_kernel<MW, NL32><<<grid, 128, 0, s>>>(
-      static_cast<const int32_t *>(a.partials), a.eA, a.eB, a.M, a.N, 4 - a.S_A - a.S_B, a.C,
-      a.ldc, a.psc, F);
-  return cuda_fail(cudaGetLastError(), "residue reconstruction launch");
-}
-
-template <int MW>
-int launch_crt_combine_m(const OzakiArgs &a, const CrtFuse &F, int bitsP, cudaStream_t s) {
-  const int need = bitsP + 1;   // |X| < P/8 < 2^bitsP, and a sign bit
-  if (need <= 256) return launch_crt_combine_t<MW, 8>(a, F, s);
-  if (need <= 384) return launch_crt_combine_t<MW, 12>(a, F, s);
-  if (need <= 512) return launch_crt_combine_t<MW, 16>(a, F, s);
-  if (need <= 640) return launch_crt_combine_t<MW, 20>(a, F, s);
-  if (need <= 768) return launch_crt_combine_t<MW, 24>(a, F, s);
-  return fail(MW_EUNSUPPORTED, "residue form: modulus product of %d bits", bitsP);
-}
-
 }  // namespace
 
 int crt_table_size() { return kNumModuli; }
 int crt_modulus(int i) { return (i >= 0 && i < kNumModuli) ? kModuli[i] : 0; }
 int crt_chunk(int i) {
-  const int h = crt_modulus(i) / 2;
-  return h * h <= (1 << 14) ? 256 : h * h <= (1 << 15) ? 128 : 64;
+  const int64_t h = crt_modulus(i) / 2;
+  for (int c = 1024; c > 64; c /= 2)
+    if (c * h * h <= (1 << 22)) return c;
+  return 64;
 }
 double crt_bits(int n) {
   double b = 0;
@@ -369,28 +681,38 @@ int launch_residues(const SplitArgs &a, cudaStream_t s) {
 int launch_crt_combine(const OzakiArgs &a, cudaStream_t s) {
   const int D = a.D;
   if (D < 1 || D > kNumModuli) return fail(MW_EINVAL, "residue form: %d moduli", D);
+  const int bitsP = (int)std::ceil(crt_bits(D));
   CrtFuse F{};
   F.D = D;
+  F.nlimb = 0;
+  for (int n : {8, 12, 16, 20, 24})
+    if (!F.nlimb && 32 * n >= bitsP) F.nlimb = n;    // |X| < P/8 with its sign fits
+  if (!F.nlimb) return fail(MW_EUNSUPPORTED, "residue form: modulus product of %d bits", bitsP);
   Big P{1};
   for (int t = 0; t < D; ++t) big_mul_small(P, kModuli[t]);
-  if ((int)P.size() > kCrtMaxLimbs) return fail(MW_EUNSUPPORTED, "modulus product too long");
   for (int t = 0; t < D; ++t) {
     const uint32_t p = kModuli[t];
     Big Q;
-    big_div_small(P, p, &Q);
-    const uint32_t qm = big_div_small(Q, p, nullptr);
+    big_div_small(P, p, &Q);                         // P / p_t
+    const uint32_t inv = inverse_mod(big_div_small(Q, p, nullptr), p);
+    big_mul_small(Q, inv);                           // Q'_t = inv_t P / p_t
     F.p[t] = p;
     F.m32[t] = (uint32_t)((1ull << 32) / p);
-    F.inv[t] = inverse_mod(qm, p);
     F.c31[t] = (uint32_t)((1ull << 31) % p);
-    F.rcp[t] = 1.0f / (float)p;
-    for (int l = 0; l < kCrtMaxLimbs; ++l) F.Q[t][l] = l < (int)Q.size() ? Q[l] : 0u;
+    F.rk[t] = (float)((double)inv / (double)p);
+    // balanced bytes of Q'_t mod 2^(32 nlimb), least significant first
+    int carry = 0;
+    for (int n = 0; n < 4 * F.nlimb; ++n) {
+      const int byte = (size_t)(n / 4) < Q.size() ? (int)((Q[n / 4] >> (8 * (n % 4))) & 0xFF) : 0;
+      int x = byte + carry;
+      carry = x >= 128;
+      F.qb[t][n] = (int8_t)(x - 256 * carry);
+    }
   }
   for (int l = 0; l < kCrtMaxLimbs; ++l) F.P[l] = l < (int)P.size() ? P[l] : 0u;
-  const int bitsP = (int)std::ceil(crt_bits(D));
   switch (a.m) {
-    case 2: return launch_crt_combine_m<2>(a, F, bitsP, s);
-    case 4: return launch_crt_combine_m<4>(a, F, bitsP, s);
+    case 2: return launch_crt_combine_m<2>(a, F, s);
+    case 4: return launch_crt_combine_m<4>(a, F, s);
   }
   return fail(MW_EUNSUPPORTED, "residue form: m = %d (2 or 4)", a.m);
 }

@@ -17,7 +17,7 @@ def test_moduli_table(mw):
     ps = mw.crt_moduli()
     assert len(ps) >= 90 and len(set(ps)) == len(ps)
     assert crt.pairwise_coprime(ps)
-    assert all(2 < p <= 513 for p in ps)
+    assert all(2 < p <= 513 and p % 2 == 1 for p in ps)   # odd: no halfway sums
     # every balanced residue is an integer bfloat16 holds exactly
     assert max(p // 2 for p in ps) <= 256
     # the bits a plan can reach with the whole table
