@@ -283,6 +283,10 @@ TRAFFIC = {
     "qd4096": {"bytes": 181198118656 + 2540828672, "digest": "c15848e119b2e400"},
     # 2,000 of the 20,000 products captured (the whole batch holds ~100 GB), x10
     "od_batch": {"bytes": 10 * (4056931840 + 2792728320), "digest": "c15848e119b2e400"},
+    # residue form, captured at 2048^3 (quad double 69 moduli, double double 40) and
+    # scaled by 4: residue planes and planes of sums both grow with N^2
+    "qd4096_crt": {"bytes": 4 * (1159775000 + 1120246000), "digest": "152b7e1f240e2e73"},
+    "dd4096_crt": {"bytes": 4 * (672518400 + 631561216), "digest": "152b7e1f240e2e73"},
 }
 
 
