@@ -21,6 +21,9 @@ Parts, each a plain and slow restatement of what the paper defines:
                   4): the same fixed-point integers multiplied exactly through
                   residues modulo pairwise coprime moduli and the Chinese
                   remainder theorem, then rounded greedily.
+* ``series``   -- products of truncated power series (Section 1's
+                  application): every coefficient c_i = sum_{k<=i} a_k b_{i-k}
+                  exactly, its bound, and its error-free summation.
 * ``textbook`` -- the "ordinary" m-double product of Table 2: multiply-add in
                   m-double arithmetic with two-sum and Dekker two-product, in C
                   (``textbook.c``) for timing and in Python for operation counts
