@@ -76,7 +76,7 @@ def parse():
                     help="od_batch: number of products (20,000 is the benchmark; fewer for profiling)")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "qd1024", "dd4096", "qd4096", "od_batch", "adjoint",
-                             "table2"],
+                             "table2", "series"],
                     help="headline (default): the benchmark line, quad and double double at "
                          "4096^3; the others measure one configuration of the method each")
     return ap.parse_args()
@@ -883,6 +883,70 @@ def run_table2(args, mw, torch, dist, rank, world, dev):
     return line
 
 
+def run_series(args, mw, torch, dist, rank, world, dev):
+    """Products of truncated power series: count pairs of octo-double series of
+    degree 127 (n = 128 coefficients, entries U[-1,1) with lower words
+    x2^-53 U[-1,1), seed 3), every coefficient c_i = sum_{k<=i} a_k b_(i-k) in one
+    mw_convolve_batched call.  m-double flops: 2 sum_i (i+1) = n (n+1) a pair."""
+    import synthetic
+    m, n, count = 8, 128, args.count if args.count != 20000 else 2000
+    rng = synthetic.SplitMix64(3)
+    A = synthetic.uniform_mdouble(rng, m, count, n)
+    B = synthetic.uniform_mdouble(rng, m, count, n)
+    tA, tB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    plan = mw.plan_convolve(tA, tB)
+    C = torch.empty((m, count, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flops = float(count) * n * (n + 1)
+
+    def step():
+        mw.mw_convolve_batched(tA, tB, plan, C=C, check=False)
+
+    for _ in range(args.warmup):
+        step()
+    mw.check_status()
+    torch.cuda.synchronize()
+    step_ms, _, clk = timed(step, args.steps, flush, mw, dist, dev, phase=False)
+    value, t_step = aggregate(sum(step_ms) / 1e3, flops, args.steps, dist, dev)
+    e2e = None
+    e2e_steps = e2e_count(args)
+    if e2e_steps > 0:
+        hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+        e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB],
+                              lambda d: [mw.mw_convolve_batched(d[0], d[1], plan, check=False)])
+        e2e = {"value": aggregate(e2e_s, flops, 1, dist, dev)[0], "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
+               "d2h_bytes_per_step": int(m * count * n * 8), "how": E2E_HOW}
+        mw.check_status()
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_of(m, "24-bit integer digits, int64 sums"), "data": "synthetic",
+            "config": {"workload": f"{count} products of octo-double power series of degree "
+                                   f"{n - 1}, entries U[-1,1) with lower words x2^-53 U[-1,1), "
+                                   "seed 3, one mw_convolve_batched call",
+                       "m": m, "count": count, "n": n, "plan": plan.as_dict(),
+                       "flop_per_step": flops,
+                       "l2": "flushed (256 MiB write) before every timed step"},
+            "roofline": None, "clocks": clk, "e2e": e2e, "gpu_launches": args.steps}
+    if rank == 0 and not args.no_cpu:
+        from oracle import textbook
+        tc = textbook.TextbookC()
+        sample = min(count, 40)
+        t0 = time.perf_counter()
+        for s in range(sample):
+            for i in range(n):
+                a = np.ascontiguousarray(A[:, s:s + 1, :i + 1])
+                b = np.ascontiguousarray(B[:, s, i::-1][:, :, None])
+                tc.gemm(a, b, threads=1)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sample * n * (n + 1) / dt / 1e9, "unit": "GFLOP/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"{sample} of the {count} series products, one thread, "
+                                          f"{dt:.2f} s"}
+    return line
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -901,6 +965,8 @@ def main():
         line = run_adjoint(args, mw, torch, dist, rank, world, dev)
     elif args.workload == "table2":
         line = run_table2(args, mw, torch, dist, rank, world, dev)
+    elif args.workload == "series":
+        line = run_series(args, mw, torch, dist, rank, world, dev)
     else:
         line = run_single(args, args.workload, mw, torch, dist, rank, world, dev)
     if rank == 0:

@@ -231,6 +231,24 @@ int mw_dot_batched(const mw_plan *plan, int64_t count, int64_t K, const double *
                    int64_t plane_stride_a, const double *B, int64_t ldb, int64_t plane_stride_b,
                    double *C, int64_t plane_stride_c, mw_stream_t stream);
 
+/* Products of truncated power series with m-double coefficients (Section 1's
+ * application; Section 2's diagonal sums s_i are these convolutions):
+ *   c_si = sum_{k=0..i} a_sk b_s(i-k)   for every series s < count, i < n,
+ * each coefficient the inner product of a_s0..a_si with b_si..b_s0, summed
+ * error-free as in mw_dot_batched with the plan's pieces.  Plan it as one inner
+ * product of length 1 (mw_plan_gemm(m, MW_DOT, 1, 1, 1, ...): the shortest
+ * product needs the most bits), so that every coefficient meets
+ * |c_si - exact| <= 2 (i+1) 2^(-52m) sum_k |a_sk| |b_s(i-k)|.  Series s of A is
+ * row s (coefficient k at A[j * plane_stride_a + s * lda + k], word plane j),
+ * likewise B; c_si goes to C[j * plane_stride_c + s * ldc + i].  One CTA per
+ * coefficient; no workspace, asynchronous.  MW_EINVAL for bad arguments,
+ * MW_EUNSUPPORTED for n beyond the kernel's int64 sums; device status bits as
+ * for mw_dot_batched. */
+int mw_convolve_batched(const mw_plan *plan, int64_t count, int64_t n, const double *A,
+                        int64_t lda, int64_t plane_stride_a, const double *B, int64_t ldb,
+                        int64_t plane_stride_b, double *C, int64_t ldc, int64_t plane_stride_c,
+                        mw_stream_t stream);
+
 /* ---- batches of independent products (power-series coefficient convolutions,
  * Section 1, come as many small products of uneven sizes) -------------------- */
 

@@ -99,6 +99,7 @@ def _load():
         "mw_dot_batched": [pp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, vp],
         "mw_selftest_timeout": [ctypes.c_uint, vp],
         "mw_crt_moduli": [ip, i32],
+        "mw_convolve_batched": [pp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp],
         "mw_set_phase_events": [ctypes.POINTER(ctypes.c_void_p), i32],
     }
     for name, args in sig.items():
@@ -118,7 +119,7 @@ EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_works
             "mw_version", "mw_set_phase_events", "mw_gemm_noalloc", "mw_batch_describe",
             "mw_gemm_batched_workspace_size", "mw_measure_spread_batched",
             "mw_measure_spread_batched_workspace_size", "mw_gemm_batched",
-            "mw_dot_batched", "mw_selftest_timeout", "mw_crt_moduli")
+            "mw_dot_batched", "mw_selftest_timeout", "mw_crt_moduli", "mw_convolve_batched")
 
 
 def _check(rc: int, what: str):
@@ -513,6 +514,37 @@ def mw_dot_batched(A: torch.Tensor, B: torch.Tensor, plan: mw_plan | None = None
     _check(_lib.mw_dot_batched(ctypes.byref(plan), count, K, pa, lda, psa, pb, ldb, psb,
                                ctypes.c_void_p(C.data_ptr()), C.stride(0), _stream()),
            "mw_dot_batched")
+    if check:
+        check_status()
+    return C
+
+
+def plan_convolve(A: torch.Tensor, B: torch.Tensor) -> mw_plan:
+    """MW_DOT plan for the products of the series in the rows of A and B, both
+    (m, count, n): one inner product of length 1 (the shortest coefficient needs
+    the most bits) with the exponent spreads of whole rows (a coefficient's
+    vectors span no more), measured on the GPU (synchronizes)."""
+    m = A.shape[0]
+    ra, rb = mw_measure_spread(A, B, False, True)
+    return mw_plan_gemm(m, "dot", 1, 1, 1, ra, rb)
+
+
+def mw_convolve_batched(A: torch.Tensor, B: torch.Tensor, plan: mw_plan | None = None,
+                        C: torch.Tensor | None = None, check: bool = True) -> torch.Tensor:
+    """Products of truncated power series: C[:, s, i] = sum_{k<=i} A[:, s, k] B[:, s, i-k]
+    in m-double precision; A and B are (m, count, n), the result (m, count, n)."""
+    if A.dim() != 3 or B.shape != A.shape:
+        raise MWError("A and B must be (m, count, n) tensors of one shape")
+    m, count, n = A.shape
+    if plan is None:
+        plan = plan_convolve(A, B)
+    if C is None:
+        C = torch.empty((m, count, n), dtype=torch.float64, device=A.device)
+    pa, lda, psa = _mat(A, "A")
+    pb, ldb, psb = _mat(B, "B")
+    pc, ldc, psc = _mat(C, "C")
+    _check(_lib.mw_convolve_batched(ctypes.byref(plan), count, n, pa, lda, psa, pb, ldb, psb,
+                                    pc, ldc, psc, _stream()), "mw_convolve_batched")
     if check:
         check_status()
     return C

@@ -17,9 +17,16 @@
 //      X 2^(E_a + E_b + 4 - w (D+1)) into m words (greedy, ties to even).
 // S is a template parameter (digit positions known at compile time); the
 // planner picks the smallest instance that covers the error analysis.
+//
+// The same kernel multiplies truncated power series (mw_convolve_batched):
+// coefficient i of the product of series s, c_i = sum_{k<=i} a_k b_{i-k}, is the
+// inner product of a_0..a_i with b_i..b_0, so product u = (s, i) reads a forward
+// from a_0 and b backward from b_i, over i + 1 terms (Section 2's s_i are these
+// convolutions).
 #include <cuda.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "mw_column.cuh"
 #include "mw_device.cuh"
@@ -41,6 +48,10 @@ struct DotArgs {
   int64_t count, K;
   int D, range_A, range_B;
   unsigned int *status;
+  // power series: count series of n = K coefficients, product u = (s, i) for
+  // u < count * n, output at C[s * ldc + i]
+  int conv;
+  int64_t ldc;
 };
 
 // bits 24k + 23 for k = 0 .. S-2 (the bias that makes the low digits bytes-like)
@@ -147,14 +158,19 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
   const int D = a.D;
   if (tid == 0) red_flag[0] = red_flag[1] = red_flag[2] = 0;
   __syncthreads();
-  for (int64_t i = blockIdx.x; i < a.count; i += gridDim.x) {
-    const double *pa = a.A + i * a.lda;
-    const double *pb = a.B + i * a.ldb;
+  const int64_t nprod = a.conv ? a.count * a.K : a.count;
+  for (int64_t i = blockIdx.x; i < nprod; i += gridDim.x) {
+    // product i: inner product of length Ki of a (forward) and b (step bs)
+    const int64_t s_idx = a.conv ? i / a.K : i, c_idx = a.conv ? i - s_idx * a.K : 0;
+    const int64_t Ki = a.conv ? c_idx + 1 : a.K;
+    const int64_t bs = a.conv ? -1 : 1;
+    const double *pa = a.A + s_idx * a.lda;
+    const double *pb = a.B + s_idx * a.ldb + c_idx;
     // 1. shared exponents from the leading words (an m-double's largest word is
     // its first), one read of 1/m of the data
     int ea = kExpZero, eb = kExpZero;
-    for (int64_t k = tid; k < a.K; k += kDotThreads) {
-      const int u = exp_plus1(pa[k]), v = exp_plus1(pb[k]);
+    for (int64_t k = tid; k < Ki; k += kDotThreads) {
+      const int u = exp_plus1(pa[k]), v = exp_plus1(pb[k * bs]);
       if (u != kExpNonFinite) ea = max(ea, u);
       if (v != kExpNonFinite) eb = max(eb, v);
     }
@@ -185,7 +201,7 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
 #pragma unroll
       for (int j = 0; j < MW; ++j) {
         cp_async8(slot(buf, j), pa + j * a.psa + k);
-        cp_async8(slot(buf, MW + j), pb + j * a.psb + k);
+        cp_async8(slot(buf, MW + j), pb + j * a.psb + k * bs);
       }
     };
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -196,10 +212,10 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
 #pragma unroll
       for (int t = 0; t < DC; ++t) s[t] = 0;
       int buf = 0;
-      if (tid < a.K) fetch(tid, 0);
+      if (tid < Ki) fetch(tid, 0);
       cp_async_commit();
-      for (int64_t k = tid; k < a.K; k += kDotThreads, buf ^= 1) {
-        if (k + kDotThreads < a.K) fetch(k + kDotThreads, buf ^ 1);
+      for (int64_t k = tid; k < Ki; k += kDotThreads, buf ^= 1) {
+        if (k + kDotThreads < Ki) fetch(k + kDotThreads, buf ^ 1);
         cp_async_commit();
         cp_async_wait<1>();
         double xa[MW], xb[MW];
@@ -315,7 +331,7 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const DotArgs a) {
       }
       uint32_t U[2 * NLF];
       to_limbs32<NLF>(X, U);
-      double *c = a.C + i;
+      double *c = a.C + (a.conv ? s_idx * a.ldc + c_idx : i);
       const int64_t psc = a.psc;
       // exps: the exponents of the last cut (the same on both cuts but for input
       // that is not normalised)
@@ -341,7 +357,7 @@ int launch_dot_s(const DotArgs &a, cudaStream_t st) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)std::min<int64_t>(a.count, (int64_t)nsm * 8);
+  const int grid = (int)std::min<int64_t>(a.conv ? a.count * a.K : a.count, (int64_t)nsm * 8);
   constexpr size_t smem = 2 * 2 * MW * kDotThreads * sizeof(double) +
                          (MW >= 8 ? (size_t)(S + 3) * kDotThreads * sizeof(uint32_t) : 0);
   static bool attr_set = false;   // once per instance
@@ -378,6 +394,31 @@ int dot_pieces_range(int m, int *lo, int *hi) {
   }
 }
 
+namespace {
+
+int check_dot_plan(const mw_plan *plan) {
+  if (!plan) return fail(MW_EINVAL, "plan is NULL");
+  const mw_plan &p = *plan;
+  if (p.mode != MW_DOT) return fail(MW_EINVAL, "plan mode must be MW_DOT");
+  if (p.m != 2 && p.m != 4 && p.m != 8 && p.m != 16)
+    return fail(MW_EINVAL, "m must be 2, 4, 8 or 16");
+  if (p.w != kDotW || p.S_A != p.S_B || p.S_A < 1)
+    return fail(MW_EINVAL, "MW_DOT plans have w = 24 and S_A = S_B");
+  if (p.D < 1 || p.D > p.S_A + kDotExtraD || p.D > 2 * p.S_A - 1)
+    return fail(MW_EINVAL, "MW_DOT plans keep at most S + %d diagonals", kDotExtraD);
+  return MW_OK;
+}
+
+int launch_dot(const mw_plan &p, const DotArgs &a, cudaStream_t st) {
+  switch (p.m) {
+    case 2: return launch_dot_range<2, DotS<2>::lo>(a, p.S_A, st);
+    case 4: return launch_dot_range<4, DotS<4>::lo>(a, p.S_A, st);
+    case 8: return launch_dot_range<8, DotS<8>::lo>(a, p.S_A, st);
+    default: return launch_dot_range<16, DotS<16>::lo>(a, p.S_A, st);
+  }
+}
+
+}  // namespace
 }  // namespace mw
 
 using namespace mw;
@@ -387,34 +428,49 @@ extern "C" {
 int mw_dot_batched(const mw_plan *plan, int64_t count, int64_t K, const double *A, int64_t lda,
                    int64_t plane_stride_a, const double *B, int64_t ldb, int64_t plane_stride_b,
                    double *C, int64_t plane_stride_c, mw_stream_t stream) {
-  if (!plan) return fail(MW_EINVAL, "plan is NULL");
+  int rc = check_dot_plan(plan);
+  if (rc) return rc;
   const mw_plan &p = *plan;
-  if (p.mode != MW_DOT) return fail(MW_EINVAL, "plan mode must be MW_DOT");
-  if (p.m != 2 && p.m != 4 && p.m != 8 && p.m != 16)
-    return fail(MW_EINVAL, "m must be 2, 4, 8 or 16");
   if (count < 1 || K < 1) return fail(MW_EINVAL, "count and K must be positive");
   if (!A || !B || !C) return fail(MW_EINVAL, "NULL operand");
   if (lda < K || ldb < K) return fail(MW_EINVAL, "lda and ldb must be >= K");
   if (plane_stride_a < lda * (count - 1) + K || plane_stride_b < ldb * (count - 1) + K ||
       plane_stride_c < count)
     return fail(MW_EINVAL, "plane strides overlap");
-  if (p.w != kDotW || p.S_A != p.S_B || p.S_A < 1)
-    return fail(MW_EINVAL, "MW_DOT plans have w = 24 and S_A = S_B");
-  if (p.D < 1 || p.D > p.S_A + kDotExtraD || p.D > 2 * p.S_A - 1)
-    return fail(MW_EINVAL, "MW_DOT plans keep at most S + %d diagonals", kDotExtraD);
   DotArgs a{};
   a.A = A; a.B = B; a.C = C;
   a.lda = lda; a.psa = plane_stride_a; a.ldb = ldb; a.psb = plane_stride_b;
   a.psc = plane_stride_c;
   a.count = count; a.K = K; a.D = p.D; a.range_A = p.range_A; a.range_B = p.range_B;
   a.status = status_ptr();
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (p.m) {
-    case 2: return launch_dot_range<2, DotS<2>::lo>(a, p.S_A, st);
-    case 4: return launch_dot_range<4, DotS<4>::lo>(a, p.S_A, st);
-    case 8: return launch_dot_range<8, DotS<8>::lo>(a, p.S_A, st);
-    default: return launch_dot_range<16, DotS<16>::lo>(a, p.S_A, st);
-  }
+  return launch_dot(p, a, (cudaStream_t)stream);
+}
+
+int mw_convolve_batched(const mw_plan *plan, int64_t count, int64_t n, const double *A,
+                        int64_t lda, int64_t plane_stride_a, const double *B, int64_t ldb,
+                        int64_t plane_stride_b, double *C, int64_t ldc, int64_t plane_stride_c,
+                        mw_stream_t stream) {
+  int rc = check_dot_plan(plan);
+  if (rc) return rc;
+  const mw_plan &p = *plan;
+  if (count < 1 || n < 1) return fail(MW_EINVAL, "count and n must be positive");
+  if (!A || !B || !C) return fail(MW_EINVAL, "NULL operand");
+  if (lda < n || ldb < n || ldc < n) return fail(MW_EINVAL, "lda, ldb and ldc must be >= n");
+  if (plane_stride_a < lda * (count - 1) + n || plane_stride_b < ldb * (count - 1) + n ||
+      plane_stride_c < ldc * (count - 1) + n)
+    return fail(MW_EINVAL, "plane strides overlap");
+  if (count > ((int64_t)1 << 40) / n) return fail(MW_EINVAL, "count * n too large");
+  // a thread's int64 diagonal sums take ceil(n / 256) products below 2^46 each
+  if ((double)p.S_A * std::ceil((double)n / kDotThreads) > 65536.0)
+    return fail(MW_EUNSUPPORTED, "n = %lld too long for the inner-product kernel", (long long)n);
+  DotArgs a{};
+  a.A = A; a.B = B; a.C = C;
+  a.lda = lda; a.psa = plane_stride_a; a.ldb = ldb; a.psb = plane_stride_b;
+  a.psc = plane_stride_c; a.ldc = ldc;
+  a.count = count; a.K = n; a.D = p.D; a.range_A = p.range_A; a.range_B = p.range_B;
+  a.status = status_ptr();
+  a.conv = 1;
+  return launch_dot(p, a, (cudaStream_t)stream);
 }
 
 }  // extern "C"
