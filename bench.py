@@ -63,7 +63,7 @@ def parse():
                     help="single products: launch each step directly instead of replaying a graph")
     ap.add_argument("--forms", default="ozaki,crt", type=lambda s: s.split(","),
                     help="headline: Ozaki forms to time (ozaki = digit slices, crt = residues)")
-    ap.add_argument("--mode", default="crt", choices=["ozaki", "crt"],
+    ap.add_argument("--mode", default="crt", choices=["ozaki", "crt", "textbook"],
                     help="single workloads: the form to time")
     ap.add_argument("--size", type=int, default=0,
                     help="single workloads: M = N = K (0 = the workload's own size; smaller "
@@ -359,7 +359,9 @@ def count_pairs(plan):
     return sum(1 for t in range(plan.D) for p in range(plan.S_A) if 0 <= t - p < plan.S_B)
 
 
-FORMS = {"ozaki": "Ozaki slices: bf16 integer digits on tcgen05, every kept pair of digit "
+FORMS = {"textbook": "textbook ('ordinary') m-double product on the FP64 pipe: two_prod, "
+                     "two_sum and m-word renormalisation per term, k in order",
+         "ozaki": "Ozaki slices: bf16 integer digits on tcgen05, every kept pair of digit "
                   "matrices, fp32 drained to integers, exact fusion",
          "crt": "Ozaki residues (scheme II): balanced residues modulo pairwise coprime moduli "
                 "on tcgen05, one product per modulus, Chinese-remainder reconstruction"}
@@ -431,7 +433,7 @@ def measure_single(args, mw, torch, dist, rank, dev, A, B, workload, mode="ozaki
     ws = torch.empty(mw.workspace_size(plan, M, N, K), dtype=torch.uint8, device=dev)
     C = torch.empty((m, M, N), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    pairs = count_pairs(plan)
+    pairs = count_pairs(plan) if mode != "textbook" else 0
 
     def call():
         mw.mw_gemm(tA, tB, plan, C=C, ws=ws, check=False)
@@ -466,7 +468,8 @@ def measure_single(args, mw, torch, dist, rank, dev, A, B, workload, mode="ozaki
            "tensor_products_per_launch": pairs, "form": FORMS[mode],
            "launch": "one mw_gemm call captured in a CUDA graph, replayed per step"
                      if g is not None else "direct mw_gemm calls",
-           "roofline": roofline_of(pairs, flops, kern_ms, workload_key(m, M, N, K, mode)),
+           "roofline": roofline_of(pairs, flops, kern_ms, workload_key(m, M, N, K, mode))
+                       if mode != "textbook" else None,
            "clocks": clk, "gpu_launches": KERNELS_PER_STEP * args.steps}
     del g
     extras(args, mw, torch, dist, rank, dev, A, B, tA, tB, plan, rec, plain_steps, e2e_steps,

@@ -36,6 +36,11 @@
  *             which step 4 rounds as in MW_OZAKI.  n grows with the bits of
  *             T_A + T_B, where MW_OZAKI's pair count grows with their square
  *             (m = 2 and 4).
+ * and a reference form without error-free summation:
+ *   MW_TEXTBOOK the "ordinary" product Table 2 compares against: every term an
+ *             m-double multiplication and addition (two_sum, two_prod, m-word
+ *             renormalisation) on the FP64 pipe, k in order (m = 2, 4, 8; no
+ *             workspace beyond 256 bytes; the plan fixes only m and the form).
  * Inner products (mw_dot_batched, the workload of Table 2) use a fourth form:
  *   MW_DOT    pieces are 24-bit integers, products summed in int64 on the
  *             integer units (no operand reuse, so no tensor cores); exact
@@ -80,7 +85,7 @@ enum {
 };
 
 /* forms of the product */
-enum { MW_PLAIN = 0, MW_OZAKI = 1, MW_DOT = 2, MW_CRT = 3 };
+enum { MW_PLAIN = 0, MW_OZAKI = 1, MW_DOT = 2, MW_CRT = 3, MW_TEXTBOOK = 4 };
 
 /* digit formats written by mw_split */
 enum { MW_DIGITS_BF16 = 0, MW_DIGITS_F64 = 1 };

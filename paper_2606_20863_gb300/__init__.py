@@ -26,9 +26,10 @@ _LIB_PATH = os.path.join(_HERE, "libmw.so")
 
 MW_OK, MW_EINVAL, MW_ERANGE, MW_ENONFINITE, MW_ECUDA, MW_ETIMEOUT, MW_ENOSPC, MW_WRANGE = (
     0, 1, 2, 4, 8, 16, 32, 64)
-MW_PLAIN, MW_OZAKI, MW_DOT, MW_CRT = 0, 1, 2, 3
+MW_PLAIN, MW_OZAKI, MW_DOT, MW_CRT, MW_TEXTBOOK = 0, 1, 2, 3, 4
 MW_DIGITS_BF16, MW_DIGITS_F64 = 0, 1
-_MODES = {"plain": MW_PLAIN, "ozaki": MW_OZAKI, "dot": MW_DOT, "crt": MW_CRT}
+_MODES = {"plain": MW_PLAIN, "ozaki": MW_OZAKI, "dot": MW_DOT, "crt": MW_CRT,
+          "textbook": MW_TEXTBOOK}
 STATUS_NAMES = {MW_ERANGE: "ERANGE", MW_ENONFINITE: "ENONFINITE", MW_ETIMEOUT: "ETIMEOUT",
                 MW_WRANGE: "WRANGE"}
 

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmw.so")
 SOURCES = ["mw_capi.cu", "mw_split.cu", "mw_plain.cu", "mw_ozaki.cu", "mw_noalloc.cu", "mw_batched.cu",
-           "mw_dot.cu", "mw_combine.cu", "mw_crt.cu"]
+           "mw_dot.cu", "mw_combine.cu", "mw_crt.cu", "mw_textbook.cu"]
 HEADERS = ["mw_device.cuh", "mw_internal.h", "mw_pieces.cuh", "mw_tc.cuh", "mw_column.cuh", "mw_fuse.cuh", "mw_work.cuh", os.path.join("..", "..", "include", "mw.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]

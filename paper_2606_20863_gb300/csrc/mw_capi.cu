@@ -84,6 +84,10 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 Layout layout(const mw_plan &p, int64_t M, int64_t N, int64_t K) {
   Layout L{};
   L.Kp = round_up(K, 64);
+  if (p.mode == MW_TEXTBOOK) {       // no pieces, no partial sums
+    L.total = 256;
+    return L;
+  }
   const size_t elem = p.mode == MW_PLAIN ? 8 : 2;
   // planes of pieces: S_A / S_B digits, or D residues in the residue form
   const size_t planesA = p.mode == MW_CRT ? p.D : p.S_A, planesB = p.mode == MW_CRT ? p.D : p.S_B;
@@ -107,7 +111,8 @@ int check_plan(const mw_plan *p, int64_t M, int64_t N, int64_t K) {
   if (!p) return fail(MW_EINVAL, "plan is NULL");
   if (!valid_m(p->m)) return fail(MW_EINVAL, "m = %d, must be 2, 4, 8 or 16", p->m);
   if (M <= 0 || N <= 0 || K <= 0) return fail(MW_EINVAL, "dimensions must be positive");
-  if (p->S_A < 1 || p->S_B < 1 || p->D < 1) return fail(MW_EINVAL, "S_A, S_B, D must be >= 1");
+  if (p->mode != MW_TEXTBOOK && (p->S_A < 1 || p->S_B < 1 || p->D < 1))
+    return fail(MW_EINVAL, "S_A, S_B, D must be >= 1");
   if (p->mode == MW_OZAKI) {
     if (p->w < 2 || p->w > 8) return fail(MW_EINVAL, "Ozaki piece width w must be 2..8");
     if (p->group < 1 || p->chunk < 64) return fail(MW_EINVAL, "bad group/chunk");
@@ -115,6 +120,9 @@ int check_plan(const mw_plan *p, int64_t M, int64_t N, int64_t K) {
     const int gmax = group_size(S_min, K, p->w);
     if (gmax < 1 || p->group > gmax)
       return fail(MW_EINVAL, "group %d exceeds the int64 limit %d", p->group, gmax);
+  } else if (p->mode == MW_TEXTBOOK) {
+    if (p->m != 2 && p->m != 4 && p->m != 8)
+      return fail(MW_EUNSUPPORTED, "the textbook form (MW_TEXTBOOK) takes m = 2, 4 and 8");
   } else if (p->mode == MW_CRT) {
     if (p->m != 2 && p->m != 4)
       return fail(MW_EUNSUPPORTED, "the residue form (MW_CRT) takes m = 2 and 4");
@@ -134,7 +142,7 @@ int check_plan(const mw_plan *p, int64_t M, int64_t N, int64_t K) {
     const double bits = std::log2((double)S_min * (double)K) + 2.0 * p->w - 2.0;
     if (bits > 53.0) return fail(MW_EINVAL, "plain plan not exact: pairs*K*2^(2w-2) > 2^53");
   } else {
-    return fail(MW_EINVAL, "mode must be MW_PLAIN, MW_OZAKI or MW_CRT");
+    return fail(MW_EINVAL, "mode must be MW_PLAIN, MW_OZAKI, MW_CRT or MW_TEXTBOOK");
   }
   return MW_OK;
 }
@@ -270,6 +278,10 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
     if (w < 4) return fail(MW_EUNSUPPORTED, "K = %lld too long for exact FP64 sums", (long long)K);
     p.group = 1;
     p.chunk = 0;
+  } else if (mode == MW_TEXTBOOK) {
+    if (m != 2 && m != 4 && m != 8)
+      return fail(MW_EUNSUPPORTED, "the textbook form (MW_TEXTBOOK) takes m = 2, 4 and 8");
+    p.w = p.S_A = p.S_B = p.D = p.group = p.chunk = 0;
   } else if (mode == MW_CRT) {
     // fixed-point bits as for the slice form's digits (w = 1: no rounding up to
     // whole digits); no products are dropped, so the moduli only have to hold
@@ -308,7 +320,7 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
     p.group = 1;
     p.chunk = 0;
   } else {
-    return fail(MW_EINVAL, "mode must be MW_PLAIN, MW_OZAKI, MW_CRT or MW_DOT");
+    return fail(MW_EINVAL, "mode must be MW_PLAIN, MW_OZAKI, MW_CRT, MW_TEXTBOOK or MW_DOT");
   }
   *plan = p;
   return MW_OK;
@@ -453,6 +465,14 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
   if (!ws || ws_bytes < L.total)
     return fail(MW_ENOSPC, "workspace %zu bytes, need %zu", ws_bytes, L.total);
   cudaStream_t s = (cudaStream_t)stream;
+  if (p.mode == MW_TEXTBOOK) {
+    phase(0, s);
+    phase(1, s);
+    rc = launch_textbook(p.m, transA, transB, M, N, K, A, lda, psa, B, ldb, psb, C, ldc, psc, s);
+    phase(2, s);
+    phase(3, s);
+    return rc;
+  }
   phase(0, s);
   cudaError_t e = cudaMemsetAsync(ops_in(ws, M, N).maxsp, 0, 2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "mw_gemm memset");

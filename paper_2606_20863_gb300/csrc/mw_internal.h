@@ -86,6 +86,11 @@ bool narrow_partials(int S_A, int S_B, int w, int64_t max_K);
 size_t ozaki_partials_planes_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 
+// ---- textbook form (mw_textbook.cu) ---------------------------------------------
+int launch_textbook(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,
+                    const double *A, int64_t lda, int64_t psa, const double *B, int64_t ldb,
+                    int64_t psb, double *C, int64_t ldc, int64_t psc, cudaStream_t s);
+
 // ---- residue form (mw_crt.cu) -------------------------------------------------
 constexpr int kCrtMaxModuli = 96;   // capacity of the moduli tables
 constexpr int kCrtMaxLimbs = 24;    // 32-bit limbs of the largest modulus product
