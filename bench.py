@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--size", type=int, default=0,
                     help="single workloads: M = N = K (0 = the workload's own size; smaller "
                          "sizes of the same recipe are for profiling)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="headline: leave out the autotuner's timing of every admissible plan")
     ap.add_argument("--no-secondary", action="store_true",
                     help="headline: leave out the quad-double 1024^3 sub-record")
     ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8, 16],
@@ -564,6 +566,21 @@ def run_single(args, name, mw, torch, dist, rank, world, dev):
     return line
 
 
+def autotune_record(mw, torch, tA, tB):
+    """The autotuner's measured choice for these operands: every admissible
+    (form, width, chunk) timed with CUDA events (mean of 3 after one untimed
+    call, L2 not flushed), cached in a temporary file unless MW_AUTOTUNE_CACHE
+    names one."""
+    import tempfile
+    from paper_2606_20863_gb300 import autotune
+    path = os.environ.get("MW_AUTOTUNE_CACHE") or os.path.join(tempfile.mkdtemp(), "tune.json")
+    tuner = autotune.Autotuner(path)
+    choice, times = tuner.tune(tA, tB)
+    torch.cuda.empty_cache()
+    return {"choice": choice.as_dict(), "ms": {k: round(v, 3) for k, v in times.items()},
+            "cache": "MW_AUTOTUNE_CACHE" if os.environ.get("MW_AUTOTUNE_CACHE") else "temporary"}
+
+
 def run_headline(args, mw, torch, dist, rank, world, dev):
     """The benchmark line: quad double (value) and double double at 4096^3, each
     in both Ozaki forms (digit slices and residues) on the same operands and the
@@ -572,7 +589,7 @@ def run_headline(args, mw, torch, dist, rank, world, dev):
     import synthetic
     pipes = measure_pipes(torch, dev)
     cpu_s = 0.0 if args.no_cpu else args.cpu_seconds
-    recs, best = {}, {}
+    recs, best, tuned = {}, {}, {}
     for name, m in (("qd4096", 4), ("dd4096", 2)):
         A, B = synthetic.ozaki_4096(m)
         forms = {f: measure_single(args, mw, torch, dist, rank, dev, A, B, name, mode=f,
@@ -581,6 +598,8 @@ def run_headline(args, mw, torch, dist, rank, world, dev):
         tA, tB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
         extras(args, mw, torch, dist, rank, dev, A, B, tA, tB, mw.plan_for(tA, tB, win),
                forms[win], args.plain_steps, e2e_count(args), cpu_s, pipes)
+        if not args.no_autotune:
+            tuned[name] = autotune_record(mw, torch, tA, tB)
         if "plain" in forms[win]:
             for f in forms:
                 forms[f]["speedup_vs_plain"] = forms[f]["value"] / forms[win]["plain"]["value"]
@@ -614,6 +633,7 @@ def run_headline(args, mw, torch, dist, rank, world, dev):
                        "int8_peak_tops_measured": pipes[1],
                        "error_bound": "|C - C_exact| <= 2K 2^(-52m) (|A||B|) componentwise, "
                                       "every form (checked by the GPU tests)",
+                       "autotune": tuned,
                        "records": recs},
             "roofline": qd["roofline"], "clocks": qd["clocks"], "e2e": qd.get("e2e"),
             "gpu_launches": qd["gpu_launches"]}

@@ -196,6 +196,12 @@ def crt_moduli(n: int | None = None) -> list[int]:
     return list(buf[:n])
 
 
+def mw_crt_moduli_product_bits(n: int) -> float:
+    """log2 of the product of the first n moduli of the residue form."""
+    import math
+    return sum(math.log2(p) for p in crt_moduli(n))
+
+
 def mw_plan_gemm(m: int, mode: str | int, M: int, N: int, K: int, range_A: int,
                  range_B: int, w: int = 0) -> mw_plan:
     p = mw_plan()
