@@ -102,7 +102,7 @@ Layout layout(const mw_plan &p, int64_t M, int64_t N, int64_t K) {
     off = align256(off + ozaki_partials_bytes(M, N, p.D, p.group,
                                               narrow_partials(p.S_A, p.S_B, p.w, L.Kp)));
   else if (p.mode == MW_CRT)
-    off = align256(off + ozaki_partials_bytes(M, N, p.D, 1, true));
+    off = align256(off + crt_partials_bytes(M, N, p.D));
   L.total = off;
   return L;
 }
@@ -194,8 +194,11 @@ int mw_selftest_timeout(unsigned int limit_us, mw_stream_t stream) {
   return cuda_fail(cudaGetLastError(), "self-test launch");
 }
 
+#define MW_STR2(x) #x
+#define MW_STR(x) MW_STR2(x)
 const char *mw_version(void) {
-  return "mw 0.2 (sm_103a, tcgen05 bf16 slices and residues, fp64 pieces)";
+  return "mw 0.3 (sm_103a, tcgen05 bf16 slices and residues, fp64 pieces; residue blocks of "
+         MW_STR(MW_CRT_J) " columns)";
 }
 
 int mw_crt_moduli(int *moduli, int n) {

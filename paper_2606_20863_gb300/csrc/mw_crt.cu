@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -117,11 +118,6 @@ __device__ __forceinline__ float balanced_f(float z, int t) {
 // significant bits): its top 16 bits.
 __device__ __forceinline__ uint16_t bf16_bits_small(float r) {
   return (uint16_t)(__float_as_uint(r) >> 16);
-}
-
-// The float of an integer |d| <= 2^22 without a conversion instruction.
-__device__ __forceinline__ float small_int_float(int d) {
-  return __uint_as_float(0x4B400000u + (uint32_t)d) - 12582912.0f;
 }
 
 // T in [-2^(L-1), 2^(L-1)): every bit from L-1 up equals the sign.
@@ -373,251 +369,264 @@ int launch_residues_nl(const SplitArgs &a, cudaStream_t s) {
 }
 
 // ---- reconstruction on the tensor cores ----------------------------------------------
-// With r_t the balanced residue of Y_t mod p_t and Q'_t = inv_t (P / p_t), where
-// inv_t = (P / p_t)^(-1) mod p_t, X' = sum_t r_t Q'_t = X mod P and
-// X'/P = sum_t r_t inv_t / p_t, so X = X' - k P with k = round(sum_t r_t inv_t / p_t)
-// (|X| < P/8 leaves that sum within 1/8 of k; its float evaluation errs by less
-// than 0.13 for D <= 96, |r_t| <= 256).  Modulo 2^(32 NL32) (enough for |X| < P/8)
-// X' = sum_n z_n 2^(8n) with z_n = sum_t r_t b_tn, b_tn the balanced bytes of
-// Q'_t mod 2^(32 NL32): one MMA per tile of 128 outputs, A (128 x D) the residues
-// written by the threads, B (D x 4 NL32) the bytes; |z_n| <= 96 2^15 < 2^22, exact
-// in fp32.  The epilogue joins the z_n into 32-bit limbs (Horner, as the slice
-// form's fusion joins its diagonal sums), subtracts k P and rounds into m words.
+// The product kernel leaves r_t, the balanced residue of the exact sum mod p_t,
+// for every output and modulus (bfloat16).  With Q'_t = inv_t (P / p_t),
+// inv_t = (P / p_t)^(-1) mod p_t, the integer X' = sum_t r_t Q'_t is congruent to
+// X mod P, so X = X' - k P with k = round(X' / P) (|X| < P/8).  X' is exact:
+// Q'_t = sum_n b_tn 2^(8n) in balanced bytes (P < 2^(32 top - 2): no carry out of
+// byte 4 top - 1), so X' = sum_n z_n 2^(8n) with z_n = sum_t r_t b_tn, one MMA
+// per tile of 128 outputs (A: 128 x D residues, B: D x 4 NL bytes), |z_n| <= 96
+// 2^15 < 2^22.  A column of ones against a row of 1.5 2^23 adds that bias to
+// every z_n in the fp32 accumulator (all partial sums are integers below 2^24:
+// exact), so the accumulator's bits are 0x4B400000 + z_n.  Horner joins them into
+// 32-bit limbs, k comes from the limbs top-2..top of X' (|X'| < D 2^8 P), and
+// X = X' + |k| (P or 2^(32 NL) - P) mod 2^(32 NL) is rounded greedily into m words.
 struct CrtFuse {
-  int D, nlimb;
-  uint32_t p[kCrtMaxModuli], m32[kCrtMaxModuli], c31[kCrtMaxModuli];
-  float rk[kCrtMaxModuli];                         // inv_t / p_t
+  int D, top;                                      // moduli; limbs of X' below its sign
+  float c64, c32;                                  // 2^(32(top - 1)) / P, 2^(32(top - 2)) / P
   int8_t qb[kCrtMaxModuli][4 * kCrtMaxLimbs];      // balanced bytes of Q'_t
-  uint32_t P[kCrtMaxLimbs];
+  uint32_t P[kCrtMaxLimbs], nP[kCrtMaxLimbs];      // P and 2^(32 NL) - P
 };
 
-template <int NL32>
-struct FuseSizes {
-  static constexpr int NB = 4 * NL32;              // byte positions, N of the MMA
-  // moduli a thread loads: a product of 32 NL32 bits needs at most 5 NL32 of the
-  // table's moduli (every modulus has more than 6.4 bits), at most 96
-  static constexpr int DMAX = 5 * NL32 < 96 ? (5 * NL32 + 7) / 8 * 8 : 96;
+template <int NL>
+struct FuseShape {
+  static constexpr int NB = 4 * NL;                // byte positions: N of the MMA
+  static constexpr uint32_t TCOLS = 2 * NB <= 128 ? 128u : 256u;   // two accumulators
 };
 
-template <int MW, int NL32>
+// Bytes of shared memory the reconstruction kernel uses for D moduli and NL limbs.
+inline size_t fuse_smem(int D, int NL) {
+  const int D8 = (D + 7) & ~7, KM = (D8 + 1 + 15) & ~15, kc = (KM + 63) / 64;
+  return 1024 + (size_t)256 * D8 + (size_t)kc * 16384 + (size_t)kc * 4 * NL * 128 +
+         (size_t)(NL + 1) * 512 + 32;
+}
+
+template <int MW, int NL>
 __global__ void __launch_bounds__(128, 2)
-    crt_fuse_mma_kernel(const int32_t *__restrict__ partials, const int32_t *eA,
-                        const int32_t *eB, int64_t M, int64_t N, int ex0, double *C, int64_t ldc,
-                        int64_t psc, unsigned int *status, const __grid_constant__ CrtFuse F) {
-  constexpr int NB = FuseSizes<NL32>::NB, DMAX = FuseSizes<NL32>::DMAX;
+    crt_fuse_kernel(const __grid_constant__ CUtensorMap map, const int32_t *eA, const int32_t *eB,
+                    int64_t M, int64_t N, int ex0, double *C, int64_t ldc, int64_t psc,
+                    unsigned int *status, const __grid_constant__ CrtFuse F) {
+  constexpr int NB = FuseShape<NL>::NB;
+  constexpr uint32_t TCOLS = FuseShape<NL>::TCOLS;
+  const int D = F.D, D8 = (D + 7) & ~7, kb = D8;   // kb: the column of ones
+  const int KM = (kb + 1 + 15) & ~15, kc = (KM + 63) / 64;
   extern __shared__ uint8_t smem_raw[];
-  const int kc = (F.D + 63) / 64;                  // K chunks of 64 moduli
-  uint8_t *sA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);  // 2 x kc tiles
-  uint8_t *sB = sA + 2 * kc * kTileBytes;          // kc chunks of NB rows x 64
-  uint32_t *col = (uint32_t *)(sB + (size_t)kc * NB * 128);   // [NL32][128] rounding columns
-  uint64_t *bar = (uint64_t *)(col + NL32 * 128);
-  uint32_t *holder = (uint32_t *)(bar + 2);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  // residues of a tile as TMA leaves them (two 64-output halves, D8 rows of 128 B,
+  // swizzled), the MMA's A (128 rows, K-major) and B (NB rows), Horner columns
+  uint8_t *stage = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = stage + 256 * D8;
+  uint8_t *sB = sA + kc * 16384;
+  uint32_t *col = (uint32_t *)(sB + kc * NB * 128);          // [NL + 1][128]
+  uint64_t *bar = (uint64_t *)(col + (NL + 1) * 128);        // residues, accumulators 0, 1
+  uint32_t *holder = (uint32_t *)(bar + 3);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int idx = tid; idx < kc * 64 * NB; idx += 128) {
     const int t = idx / NB, n = idx - t * NB;
-    const int b = t < F.D ? F.qb[t][n] : 0;
-    *reinterpret_cast<uint16_t *>(sB + (t >> 6) * (NB * 128) + sw128_offset(n, t & 63)) =
-        small_int_bf16(b);
+    const uint16_t v = t < D ? small_int_bf16(F.qb[t][n]) : (t == kb ? (uint16_t)0x4B40 : 0);
+    *reinterpret_cast<uint16_t *>(sB + (t >> 6) * (NB * 128) + sw128_offset(n, t & 63)) = v;
   }
+  for (int t = D8; t < kc * 64; ++t)               // row tid of A past the residues
+    *reinterpret_cast<uint16_t *>(sA + (t >> 6) * 16384 + sw128_offset(tid, t & 63)) =
+        t == kb ? (uint16_t)0x3F80 : (uint16_t)0;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
     fence_barrier_init();
+    prefetch_map(&map);
   }
-  if (warp == 0) tmem_alloc(holder, 256);          // two regions of 128 columns (NB <= 96)
+  if (warp == 0) tmem_alloc(holder, TCOLS);
   fence_proxy_async_smem();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *holder;
   const uint32_t idesc = idesc_bf16(128, NB);
-  const int64_t itiles = (M + 127) / 128;
-  const int64_t ntiles = itiles * N;
-  const int64_t plane = M * N;
+  const int64_t itiles = (M + 127) / 128, ntiles = itiles * N;
+  const uint32_t stage_bytes = 256u * D8;
   volatile int abort_flag = 0;
 
-  struct Out {
-    int64_t i, j;
-    bool valid;
-    float kf;
+  auto issue = [&](int64_t tile) {                // one thread: the tile's residues
+    const int64_t j = tile / itiles, i0 = (tile - j * itiles) * 128;
+    const int jj = (int)(j % kCrtJ), jb = (int)(j / kCrtJ);
+    mbar_arrive_expect_tx(&bar[0], stage_bytes);
+    tma_load_4d(smem_u32(stage), &map, (int)i0, jj, 0, jb, smem_u32(&bar[0]));
+    tma_load_4d(smem_u32(stage + 128 * D8), &map, (int)i0 + 64, jj, 0, jb, smem_u32(&bar[0]));
   };
-  auto fetch = [&](int64_t tile, Out &o, int32_t (&Y)[DMAX]) {
-    o.valid = false;
-    o.i = o.j = 0;
-    if (tile < ntiles) {
-      o.j = tile / itiles;
-      o.i = (tile - o.j * itiles) * 128 + tid;
-      o.valid = o.i < M;
-    }
-    const int32_t *y = partials + o.j * M + (o.valid ? o.i : 0);
-#pragma unroll
-    for (int t = 0; t < DMAX; ++t) Y[t] = (o.valid && t < F.D) ? y[t * plane] : 0;
-  };
-  // balanced residues of the Y_t into row tid of A tile `slot`, then the MMA
-  auto stage = [&](int slot, Out &o, const int32_t (&Y)[DMAX]) {
-    uint8_t *a = sA + slot * kc * kTileBytes;
-    float kf = 0.f;
-#pragma unroll
-    for (int t0 = 0; t0 < 128; t0 += 8) {
-      if (t0 >= kc * 64) break;
-      uint32_t w[4];
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        int rr[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int t = t0 + u + e;
-          rr[e] = 0;
-          if (t < DMAX && t < F.D) {
-            const uint32_t p = F.p[t];
-            int r = (int)mod_u32((uint32_t)Y[t < DMAX ? t : 0] ^ 0x80000000u, p, F.m32[t]) -
-                    (int)F.c31[t];
-            if (r < 0) r += (int)p;
-            rr[e] = balanced((uint32_t)r, p);
-            kf = fmaf(small_int_float(rr[e]), F.rk[t], kf);
-          }
-        }
-        w[u >> 1] = (uint32_t)small_int_bf16(rr[0]) | ((uint32_t)small_int_bf16(rr[1]) << 16);
-      }
-      *reinterpret_cast<uint4 *>(a + (t0 >> 6) * kTileBytes + sw128_offset(tid, t0 & 63)) =
-          make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    o.kf = kf;
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      for (int c = 0; c < kc; ++c) {
-        const uint64_t ad = sw128_desc(smem_u32(a + c * kTileBytes));
-        const uint64_t bd = sw128_desc(smem_u32(sB + c * NB * 128));
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          tc_mma(tmem + slot * 128, ad + 2 * kk, bd + 2 * kk, idesc, (c | kk) ? 1u : 0u);
-      }
-      tc_commit(&bar[slot]);
+  // staged residues (rows t, outputs along the row) into A (rows = outputs):
+  // warp w moves outputs 32w..32w+31, eight moduli per step
+  auto transpose = [&]() {
+    const int c = 4 * warp + (lane >> 3), rho = lane & 7;
+    const uint32_t src = smem_u32(stage) + (c >> 3) * (128 * D8) + rho * 128 + (((c & 7) ^ rho) << 4);
+    const uint32_t dst = smem_u32(sA) + (8 * c + rho) * 128;
+    for (int tau = 0; tau < D8 / 8; ++tau) {
+      uint32_t r[4];
+      ldsm_x4_trans(src + tau * 1024, r);
+      stsm_x4(dst + (tau >> 3) * 16384 + (((tau & 7) ^ rho) << 4), r);
     }
   };
-  // X' from the byte sums, X = X' - k P, greedy words
-  auto drain = [&](int slot, uint32_t parity, const Out &o) -> bool {
-    if (!__syncthreads_and(mbar_wait(&bar[slot], parity, status, &abort_flag))) return false;
+  uint32_t fph = 0, mph[2] = {0u, 0u};
+  // X' from the accumulator of `tile`, k, X, greedy words
+  auto drain = [&](int64_t tile, int s) -> bool {
+    if (!__syncthreads_and(mbar_wait(&bar[1 + s], mph[s], status, &abort_flag))) return false;
+    mph[s] ^= 1;
     tc_fence_after();
-    uint32_t z[NB];
-    const uint32_t ta = tmem + slot * 128 + ((uint32_t)(warp * 32) << 16);
+    const uint32_t ta = tmem + s * NB + ((uint32_t)(warp * 32) << 16);
+    constexpr uint64_t K0 = 0x4B400000ull * 0x01010101ull;   // the bias in a limb's four bytes
+    uint32_t U[NL];
+    int64_t rc = 0;
 #pragma unroll
-    for (int h = 0; h < NB / 32; ++h)
-      tc_ld32(ta + 32 * h, *reinterpret_cast<uint32_t(*)[32]>(z + 32 * h));
-    if constexpr (NB % 32) tc_ld16(ta + NB / 32 * 32, z + NB / 32 * 32);
-    tc_wait_ld();
-    tc_fence_before();
-    // X' mod 2^(32 NL32) in 32-bit limbs: limb l = sum of z_(4l+u) 2^(8u) plus the carry
-    uint32_t U[NL32];
-    int64_t Rc = 0;
+    for (int h = 0; h < (NB + 31) / 32; ++h) {
+      uint32_t z[32];
+      if (32 * h + 32 <= NB) tc_ld32(ta + 32 * h, z);
+      else tc_ld16(ta + 32 * h, z);
+      tc_wait_ld();
 #pragma unroll
-    for (int l = 0; l < NL32; ++l) {
-      int64_t V = (int32_t)(__float_as_uint(__uint_as_float(z[4 * l + 3]) + 12582912.0f) -
-                            0x4B400000u);
-#pragma unroll
-      for (int u = 2; u >= 0; --u)
-        V = V * 256 + (int32_t)(__float_as_uint(__uint_as_float(z[4 * l + u]) + 12582912.0f) -
-                                0x4B400000u);
-      Rc += V;
-      U[l] = (uint32_t)Rc;
-      Rc >>= 32;
-    }
-    const int k = (int)rintf(o.kf);                // X = X' - k P (mod 2^(32 NL32))
-    const uint32_t ak = (uint32_t)(k < 0 ? -k : k);
-    uint64_t mc = 0;
-    uint32_t cb = 0;
-#pragma unroll
-    for (int l = 0; l < NL32; ++l) {
-      const uint64_t kp = (uint64_t)ak * F.P[l] + mc;
-      mc = kp >> 32;
-      const uint32_t lo = (uint32_t)kp;
-      if (k >= 0) {
-        const uint64_t d = (uint64_t)U[l] - lo - cb;
-        U[l] = (uint32_t)d;
-        cb = (uint32_t)(d >> 63);
-      } else {
-        const uint64_t s2 = (uint64_t)U[l] + lo + cb;
-        U[l] = (uint32_t)s2;
-        cb = (uint32_t)(s2 >> 32);
+      for (int q = 0; q < 8; ++q) {
+        if (32 * h + 4 * q >= NB) break;
+        const int64_t acc = rc - (int64_t)K0 + (int64_t)z[4 * q] + ((int64_t)z[4 * q + 1] << 8) +
+                            ((int64_t)z[4 * q + 2] << 16) + ((int64_t)z[4 * q + 3] << 24);
+        U[8 * h + q] = (uint32_t)acc;
+        rc = acc >> 32;
       }
     }
-    if (o.valid) {
-      double *c = C + o.i * ldc + o.j;
-      round_column<MW, NL32>(U, col + tid, 128, eA[o.i] + eB[o.j] + ex0,
-                             [&](int wd, double v) { c[wd * psc] = v; });
+    tc_fence_before();
+    const int64_t j = tile / itiles, i = (tile - j * itiles) * 128 + tid;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) col[l * 128 + tid] = U[l];
+    col[NL * 128 + tid] = (uint32_t)rc;
+    const int top = F.top;
+    const uint64_t hi = ((uint64_t)col[top * 128 + tid] << 32) | col[(top - 1) * 128 + tid];
+    const float kf = fmaf((float)(int64_t)hi, F.c64, (float)col[(top - 2) * 128 + tid] * F.c32);
+    const int k = (int)(__float_as_uint(kf + 12582912.0f) - 0x4B400000u);
+    const bool pos = k > 0;
+    const uint32_t ak = (uint32_t)(pos ? k : -k);
+    uint64_t cy = 0;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const uint64_t v = (uint64_t)ak * (pos ? F.nP[l] : F.P[l]) + U[l] + cy;
+      U[l] = (uint32_t)v;
+      cy = v >> 32;
+    }
+    if (i < M) {
+      double *c = C + i * ldc + j;
+      round_column<MW, NL>(U, col + tid, 128, eA[i] + eB[j] + ex0,
+                           [&](int wd, double v) { c[wd * psc] = v; });
     }
     return true;
   };
 
-  // two tiles in flight, the partial sums of the tile after them loaded before
-  // each drain
-  int64_t cur = blockIdx.x;
-  if (cur < ntiles) {
-    Out oc, on;
-    int32_t Y[DMAX];
-    fetch(cur, oc, Y);
-    stage(0, oc, Y);
-    fetch(cur + gridDim.x, on, Y);
-    uint32_t ph0 = 0, ph1 = 0;
-    int slot = 0;
-    for (;;) {
-      const int64_t nxt = cur + gridDim.x;
-      if (nxt < ntiles) stage(slot ^ 1, on, Y);
-      Out o2;
-      fetch(nxt + gridDim.x, o2, Y);
-      if (!drain(slot, slot ? ph1 : ph0, oc)) break;
-      if (slot) ph1 ^= 1; else ph0 ^= 1;
-      if (nxt >= ntiles) break;
-      oc = on;
-      on = o2;
-      cur = nxt;
-      slot ^= 1;
+  // the next tile's residues load while this tile is moved and the previous
+  // tile drains; its product runs during that drain
+  int64_t cur = blockIdx.x, prev = -1;
+  int slot = 0;
+  bool ok = true, tma_out = false;
+  uint32_t mma_out = 0;                            // accumulators with a product in flight
+  if (tid == 0 && cur < ntiles) {
+    issue(cur);
+    tma_out = true;
+  }
+  while (ok && (cur < ntiles || prev >= 0)) {
+    const bool have = cur < ntiles;
+    if (have) {
+      ok = __syncthreads_and(mbar_wait(&bar[0], fph, status, &abort_flag));
+      if (!ok) break;
+      fph ^= 1;
+      tma_out = false;
+      // the previous product has read A before A is rewritten
+      if (prev >= 0 && !__syncthreads_and(mbar_wait(&bar[1 + (slot ^ 1)], mph[slot ^ 1], status,
+                                                    &abort_flag))) {
+        ok = false;
+        break;
+      }
+      transpose();
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        if (cur + gridDim.x < ntiles) {
+          issue(cur + gridDim.x);
+          tma_out = true;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + slot * NB;
+        for (int cc = 0; cc < kc; ++cc) {
+          const uint64_t ad = sw128_desc(smem_u32(sA + cc * 16384));
+          const uint64_t bd = sw128_desc(smem_u32(sB + cc * NB * 128));
+          for (int kk = 0; kk < 4 && 64 * cc + 16 * kk < KM; ++kk)
+            tc_mma(d, ad + 2 * kk, bd + 2 * kk, idesc, (cc | kk) ? 1u : 0u);
+        }
+        tc_commit(&bar[1 + slot]);
+      }
+      mma_out |= 1u << slot;
     }
+    if (prev >= 0) {
+      ok = drain(prev, slot ^ 1);
+      if (!ok) break;
+      mma_out &= ~(1u << (slot ^ 1));
+    }
+    prev = have ? cur : -1;
+    if (have) cur += gridDim.x;
+    slot ^= 1;
+  }
+  // after a wait that gave up: let the copies and products in flight finish
+  // (bounded) before the tensor memory is released
+  if (!ok && tid == 0) {
+    volatile int never = 0;
+    if (tma_out) mbar_wait(&bar[0], fph, status, &never);
+    for (int s = 0; s < 2; ++s)
+      if (mma_out & (1u << s)) mbar_wait(&bar[1 + s], mph[s], status, &never);
   }
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_free(tmem, 256);
+    tmem_free(tmem, TCOLS);
   }
 }
 
-template <int MW, int NL32>
-int launch_crt_combine_t(const OzakiArgs &a, const CrtFuse &F, cudaStream_t s) {
-  constexpr int NB = FuseSizes<NL32>::NB;
-  if (F.D > FuseSizes<NL32>::DMAX)
-    return fail(MW_EUNSUPPORTED, "residue form: %d moduli for %d limbs", F.D, NL32);
-  const int kc = (F.D + 63) / 64;
-  const size_t smem = 1024 + kc * (2 * kTileBytes + NB * 128) + NL32 * 128 * 4 + 32;
+template <int MW, int NL>
+int launch_crt_fuse_t(const OzakiArgs &a, const CrtFuse &F, const CUtensorMap &map,
+                      cudaStream_t s) {
+  const size_t smem = fuse_smem(F.D, NL);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(crt_fuse_mma_kernel<MW, NL32>,
+    cudaError_t e = cudaFuncSetAttribute(crt_fuse_kernel<MW, NL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         1024 + 2 * (2 * kTileBytes + 96 * 128) + 24 * 128 * 4 + 32);
+                                         (int)fuse_smem(kCrtMaxModuli, NL));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(crt_fuse_kernel<MW, NL>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return cuda_fail(e, "reconstruction smem attribute");
     attr = true;
   }
-  int dev = 0, nsm = 0;
+  int dev = 0, nsm = 0, smem_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, crt_fuse_kernel<MW, NL>);
+  if (e != cudaSuccess) return cuda_fail(e, "reconstruction attributes");
+  // resident CTAs: what shared memory (1 KB reserved per CTA), registers and the
+  // tensor memory (512 columns) hold
+  const int by_smem = smem_sm / (int)(smem + 1024);
+  const int by_regs = 65536 / (std::max(fa.numRegs, 1) * 128);
+  const int by_tmem = (int)(512 / FuseShape<NL>::TCOLS);
+  const int per_sm = std::max(1, std::min({by_smem, by_regs, by_tmem}));
   const int64_t ntiles = (a.M + 127) / 128 * a.N;
-  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, 2 * (int64_t)nsm);
-  crt_fuse_mma_kernel<MW, NL32><<<grid, 128, smem, s>>>(
-      static_cast<const int32_t *>(a.partials), a.eA, a.eB, a.M, a.N, 4 - a.S_A - a.S_B, a.C,
-      a.ldc, a.psc, status_ptr(), F);
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
+  crt_fuse_kernel<MW, NL><<<grid, 128, smem, s>>>(map, a.eA, a.eB, a.M, a.N, 4 - a.S_A - a.S_B,
+                                                  a.C, a.ldc, a.psc, status_ptr(), F);
   return cuda_fail(cudaGetLastError(), "residue reconstruction launch");
 }
 
 template <int MW>
-int launch_crt_combine_m(const OzakiArgs &a, const CrtFuse &F, cudaStream_t s) {
-  switch (F.nlimb) {
-    case 8: return launch_crt_combine_t<MW, 8>(a, F, s);
-    case 12: return launch_crt_combine_t<MW, 12>(a, F, s);
-    case 16: return launch_crt_combine_t<MW, 16>(a, F, s);
-    case 20: return launch_crt_combine_t<MW, 20>(a, F, s);
-    case 24: return launch_crt_combine_t<MW, 24>(a, F, s);
+int launch_crt_fuse_m(const OzakiArgs &a, const CrtFuse &F, int NL, const CUtensorMap &map,
+                      cudaStream_t s) {
+  switch (NL) {
+    case 8: return launch_crt_fuse_t<MW, 8>(a, F, map, s);
+    case 12: return launch_crt_fuse_t<MW, 12>(a, F, map, s);
+    case 16: return launch_crt_fuse_t<MW, 16>(a, F, map, s);
+    case 20: return launch_crt_fuse_t<MW, 20>(a, F, map, s);
+    case 24: return launch_crt_fuse_t<MW, 24>(a, F, map, s);
   }
-  return fail(MW_EUNSUPPORTED, "residue form: %d limbs", F.nlimb);
+  return fail(MW_EUNSUPPORTED, "residue form: %d limbs", NL);
 }
 
 // ---- host arithmetic on the constants ------------------------------------------
@@ -681,38 +690,63 @@ int launch_residues(const SplitArgs &a, cudaStream_t s) {
 int launch_crt_combine(const OzakiArgs &a, cudaStream_t s) {
   const int D = a.D;
   if (D < 1 || D > kNumModuli) return fail(MW_EINVAL, "residue form: %d moduli", D);
-  const int bitsP = (int)std::ceil(crt_bits(D));
-  CrtFuse F{};
-  F.D = D;
-  F.nlimb = 0;
-  for (int n : {8, 12, 16, 20, 24})
-    if (!F.nlimb && 32 * n >= bitsP) F.nlimb = n;    // |X| < P/8 with its sign fits
-  if (!F.nlimb) return fail(MW_EUNSUPPORTED, "residue form: modulus product of %d bits", bitsP);
   Big P{1};
   for (int t = 0; t < D; ++t) big_mul_small(P, kModuli[t]);
+  int hb = 31;                                       // bit length of P: bl
+  while (!(P.back() >> hb)) --hb;
+  const int bl = 32 * (int)(P.size() - 1) + hb + 1;
+  // X' = sum_t r_t Q'_t with Q'_t < P < 2^(32 top - 2); limbs of X' up to `top`
+  const int top = std::max(2, (bl + 2 + 31) / 32);
+  const int NL = std::max(8, (top + 3) / 4 * 4);   // limbs computed (N of the MMA / 4)
+  if (NL > kCrtMaxLimbs) return fail(MW_EUNSUPPORTED, "residue form: modulus product of %d bits", bl);
+  CrtFuse F{};
+  F.D = D;
+  F.top = top;
   for (int t = 0; t < D; ++t) {
     const uint32_t p = kModuli[t];
     Big Q;
     big_div_small(P, p, &Q);                         // P / p_t
     const uint32_t inv = inverse_mod(big_div_small(Q, p, nullptr), p);
-    big_mul_small(Q, inv);                           // Q'_t = inv_t P / p_t
-    F.p[t] = p;
-    F.m32[t] = (uint32_t)((1ull << 32) / p);
-    F.c31[t] = (uint32_t)((1ull << 31) % p);
-    F.rk[t] = (float)((double)inv / (double)p);
-    // balanced bytes of Q'_t mod 2^(32 nlimb), least significant first
-    int carry = 0;
-    for (int n = 0; n < 4 * F.nlimb; ++n) {
+    big_mul_small(Q, inv);                           // Q'_t = inv_t P / p_t < P
+    int carry = 0;                                   // balanced bytes, least significant first
+    for (int n = 0; n < 4 * NL; ++n) {
       const int byte = (size_t)(n / 4) < Q.size() ? (int)((Q[n / 4] >> (8 * (n % 4))) & 0xFF) : 0;
-      int x = byte + carry;
+      const int x = byte + carry;
       carry = x >= 128;
       F.qb[t][n] = (int8_t)(x - 256 * carry);
+      if (n >= 4 * top && F.qb[t][n]) return fail(MW_EUNSUPPORTED, "residue form: Q' past its limbs");
     }
+    if (carry) return fail(MW_EUNSUPPORTED, "residue form: Q' past its limbs");
   }
-  for (int l = 0; l < kCrtMaxLimbs; ++l) F.P[l] = l < (int)P.size() ? P[l] : 0u;
+  uint64_t borrow = 0;                               // nP = 2^(32 NL) - P
+  for (int l = 0; l < NL; ++l) {
+    const uint32_t pl = (size_t)l < P.size() ? P[l] : 0u;
+    F.P[l] = pl;
+    const uint64_t d = (uint64_t)0 - pl - borrow;
+    F.nP[l] = (uint32_t)d;
+    borrow = (pl | borrow) ? 1 : 0;
+  }
+  // P ~ Pd 2^e from its top limbs
+  double Pd = 0;
+  const int lo = std::max(0, (int)P.size() - 3);
+  for (int l = (int)P.size() - 1; l >= lo; --l) Pd = Pd * 4294967296.0 + (double)P[l];
+  const int e = 32 * lo;
+  F.c64 = (float)std::ldexp(1.0 / Pd, 32 * (top - 1) - e);
+  F.c32 = (float)std::ldexp(1.0 / Pd, 32 * (top - 2) - e);
+  // residues: bf16 [j / J][t][j % J][i], leading dimension crt_ld(M); boxes of 64
+  // outputs x every modulus of one column (moduli past D, outputs past M: zeros)
+  alignas(64) CUtensorMap map;
+  const int64_t ld = crt_ld(a.M);
+  const uint64_t dims[4] = {(uint64_t)a.M, (uint64_t)kCrtJ, (uint64_t)D,
+                            (uint64_t)(crt_cols(a.N) / kCrtJ)};
+  const uint64_t strides[3] = {(uint64_t)ld * 2, (uint64_t)kCrtJ * ld * 2,
+                               (uint64_t)D * kCrtJ * ld * 2};
+  const uint32_t box[4] = {64, 1, (uint32_t)((D + 7) & ~7), 1};
+  int rc = make_map_bf16(&map, a.partials, 4, dims, strides, box);
+  if (rc) return rc;
   switch (a.m) {
-    case 2: return launch_crt_combine_m<2>(a, F, s);
-    case 4: return launch_crt_combine_m<4>(a, F, s);
+    case 2: return launch_crt_fuse_m<2>(a, F, NL, map, s);
+    case 4: return launch_crt_fuse_m<4>(a, F, NL, map, s);
   }
   return fail(MW_EUNSUPPORTED, "residue form: m = %d (2 or 4)", a.m);
 }

@@ -85,6 +85,26 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
 bool narrow_partials(int S_A, int S_B, int w, int64_t max_K);
 size_t ozaki_partials_planes_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
+// Residue form: the product kernel stores the balanced residue of every sum as
+// bfloat16 in blocks of kCrtJ columns, each block holding its columns of every
+// modulus: entry (i, j) of modulus t at ((j / J) D J + t J + j % J) crt_ld(M) + i,
+// crt_ld(M) a multiple of 8 (tensor-map strides are multiples of 16 bytes).
+// Then the 8-byte work counter.
+#ifndef MW_CRT_J
+#define MW_CRT_J 1
+#endif
+constexpr int kCrtJ = MW_CRT_J;
+static_assert(kCrtJ >= 1 && kCrtJ <= 32 && (kCrtJ & (kCrtJ - 1)) == 0,
+              "columns per residue block: a power of two up to 32 (divides every drain's columns)");
+__host__ __device__ inline int64_t crt_ld(int64_t M) { return (M + 7) & ~(int64_t)7; }
+inline int64_t crt_cols(int64_t N) { return (N + kCrtJ - 1) / kCrtJ * kCrtJ; }
+size_t crt_residue_planes_bytes(int64_t M, int64_t N, int D);
+size_t crt_partials_bytes(int64_t M, int64_t N, int D);
+// Tensor map of `rank` dimensions over a bfloat16 array (dims innermost first,
+// strides in bytes of dimensions 1.., box in elements), 128-byte swizzle, zeros
+// outside the array.  map points to a CUtensorMap (64-byte aligned).
+int make_map_bf16(void *map, const void *base, int rank, const uint64_t *dims,
+                  const uint64_t *strides, const uint32_t *box);
 
 // ---- textbook form (mw_textbook.cu) ---------------------------------------------
 int launch_textbook(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,

@@ -92,9 +92,12 @@ struct PParams {
   unsigned long long *next_item;  // work counter, zero before the launch
   unsigned int *status;
   int gorder[MAX_GROUPS]; // diagonal groups, most expensive first
-  // residue form: per modulus t, k-blocks per drain and the modulus
+  // residue form: per modulus t, k-blocks per drain, the modulus, floor(2^32 / p),
+  // the offset B_t >= 2^31 with B_t = (p - 1) / 2 mod p, and 1.5 2^23 + (p - 1) / 2
   uint8_t crt_chunk_kb[MAX_GROUPS];
   uint16_t crt_p[MAX_GROUPS];
+  uint32_t crt_m32[MAX_GROUPS], crt_off[MAX_GROUPS];
+  float crt_cf[MAX_GROUPS];
   BInfo single;
 };
 
@@ -394,6 +397,26 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
                   ++j;
                 }
               }
+            } else if constexpr (CRT) {
+              // the balanced residue of each sum S, as bfloat16 (|r| <= 256): with
+              // u = S + B_t in [0, 2^32) (|S| < 2^31 - 2^22 + p), u mod p by the
+              // reciprocal (the quotient estimate is exact or one short), then
+              // r = u mod p - (p - 1) / 2 as a float from its bits
+              constexpr int J = kCrtJ;                    // divides c0 and COLS
+              const int64_t ldy = crt_ld(x.M), blk = (int64_t)P.D * J * ldy;
+              uint16_t *dst = static_cast<uint16_t *>(P.partials) + (c0 / J) * blk +
+                              (int64_t)t * J * ldy + r;
+              const uint32_t pm = P.crt_p[t], m32 = P.crt_m32[t], off = P.crt_off[t];
+              const float cf = P.crt_cf[t];
+#pragma unroll
+              for (int i = 0; i < COLS; ++i)
+                if (c0 + i < x.N) {
+                  const uint32_t u = acc[i] - bias + off;
+                  const uint32_t r0 = u - __umulhi(u, m32) * pm;
+                  const uint32_t rr = min(r0, r0 - pm);
+                  dst[(i / J) * blk + (i % J) * ldy] =
+                      (uint16_t)(__float_as_uint(__uint_as_float(0x4B400000u + rr) - cf) >> 16);
+                }
             } else {
               int32_t *dst = static_cast<int32_t *>(P.partials) + x.part + (int64_t)t * x.N * x.M + r;
 #pragma unroll
@@ -473,6 +496,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // 2D map over a bf16 array of `rows` rows of `pitch` elements; boxes of 64 x 128,
 // 128-byte swizzle (the layout sw128_desc describes).
 int make_map_2d(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows, int box_rows) {
+  const uint64_t dims[2] = {(uint64_t)pitch, (uint64_t)rows};
+  const uint64_t strides[1] = {(uint64_t)pitch * 2};
+  const uint32_t box[2] = {BK, (uint32_t)box_rows};
+  return make_map_bf16(map, base, 2, dims, strides, box);
+}
+
+}  // namespace
+
+int make_map_bf16(void *map, const void *base, int rank, const uint64_t *dims,
+                  const uint64_t *strides, const uint32_t *box) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -483,18 +516,22 @@ int make_map_2d(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows,
       fn = (EncodeTiledFn)p;
   }
   if (!fn) return fail(MW_ECUDA, "cuTensorMapEncodeTiled not available");
-  cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
-  cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (rank < 1 || rank > 5) return fail(MW_EINVAL, "tensor map rank %d", rank);
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], estr[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    bx[i] = box[i];
+    estr[i] = 1;
+    if (i + 1 < rank) st[i] = strides[i];
+  }
+  CUresult r = fn(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank,
+                  const_cast<void *>(base), d, st, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(MW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return MW_OK;
 }
-
-}  // namespace
 
 int launch_product(const ProductLaunch &a, cudaStream_t s) {
   const int G = n_groups(a.D, a.group);
@@ -524,8 +561,12 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   P.chunk_kb = a.crt ? 1 : a.chunk / BK;
   if (a.crt)
     for (int t = 0; t < a.D; ++t) {
+      const uint32_t p = (uint32_t)crt_modulus(t), h = (p - 1) / 2;
       P.crt_chunk_kb[t] = (uint8_t)(crt_chunk(t) / BK);
-      P.crt_p[t] = (uint16_t)crt_modulus(t);
+      P.crt_p[t] = (uint16_t)p;
+      P.crt_m32[t] = (uint32_t)((1ull << 32) / p);
+      P.crt_off[t] = (uint32_t)((1ull << 31) + (h + p - (uint32_t)((1ull << 31) % p)) % p);
+      P.crt_cf[t] = 12582912.0f + (float)h;
     }
   P.partials = a.partials;
   P.next_item = a.next_item;
@@ -619,6 +660,14 @@ size_t ozaki_partials_planes_bytes(int64_t M, int64_t N, int D, int group, bool 
   return (narrow ? (size_t)D * 4 : (size_t)n_groups(D, group) * 8) * M * N;
 }
 
+size_t crt_residue_planes_bytes(int64_t M, int64_t N, int D) {
+  return (size_t)D * crt_cols(N) * crt_ld(M) * 2;
+}
+
+size_t crt_partials_bytes(int64_t M, int64_t N, int D) {
+  return ((crt_residue_planes_bytes(M, N, D) + 255) & ~(size_t)255) + 256;
+}
+
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow) {
   // partial sums, then the 8-byte work counter at the next 256-byte boundary
   const size_t planes = ozaki_partials_planes_bytes(M, N, D, group, narrow);
@@ -644,7 +693,8 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
   L.M = a.M; L.N = a.N; L.K = a.Kp;
   L.partials = a.partials;
   L.narrow = narrow;
-  const size_t planes = ozaki_partials_planes_bytes(a.M, a.N, a.D, a.group, narrow);
+  const size_t planes = a.crt ? crt_residue_planes_bytes(a.M, a.N, a.D)
+                              : ozaki_partials_planes_bytes(a.M, a.N, a.D, a.group, narrow);
   L.next_item = reinterpret_cast<unsigned long long *>(
       reinterpret_cast<uint8_t *>(a.partials) + ((planes + 255) & ~(size_t)255));
   int rc = launch_product(L, s);

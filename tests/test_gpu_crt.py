@@ -21,6 +21,12 @@ def bf16_to_int(x):
     return x.float().cpu().numpy().astype(np.int64)
 
 
+def residue_block_columns(mw):
+    """Columns per block of the stored residues (the library's version string)."""
+    import re
+    return int(re.search(r"residue blocks of (\d+) columns", mw.version()).group(1))
+
+
 def run_crt(mw, dev, A, B, plan, transA=False, transB=False):
     tA, tB = to_dev(A, dev), to_dev(B, dev)
     m, M, N, K = mw._dims(tA, tB, transA, transB)
@@ -52,13 +58,16 @@ def check_crt(mw, dev, A, B, plan=None, transA=False, transB=False, rows=None, c
         ra, rb = bf16_to_int(RA[:, rows, :K]), bf16_to_int(RB[:, cols, :K])
         assert np.array_equal(ra, rp.A.residues) and np.array_equal(rb, rp.B.residues)
         assert not bf16_to_int(RA[:, rows, K:]).any() and not bf16_to_int(RB[:, cols, K:]).any()
-        Y = ws[off[3]:off[3] + 4 * D * M * N].view(torch.int32).cpu().numpy().astype(np.int64)
-        Y = Y.reshape(D, N, M).transpose(0, 2, 1)[:, rows][:, :, cols]     # column-major planes
-        if all(K * (p // 2) ** 2 < 2 ** 31 for p in moduli):
-            assert np.array_equal(Y, rp.Y)
-        else:
-            for i, p in enumerate(moduli):
-                assert not ((Y[i] - rp.Y[i]) % p).any(), p
+        # the product kernel leaves the balanced residue of every exact sum Y_p,
+        # bfloat16 [j / J][t][j % J][i], leading dimension M rounded up to 8
+        J = residue_block_columns(mw)
+        ld, nb = -(-M // 8) * 8, -(-N // J)
+        R = ws[off[3]:off[3] + 2 * D * nb * J * ld].view(torch.bfloat16).reshape(nb, D, J, ld)
+        R = bf16_to_int(R[..., :M]).transpose(1, 3, 0, 2).reshape(D, M, nb * J)[:, :, :N]
+        R = R[:, rows][:, :, cols]
+        for i, p in enumerate(moduli):
+            h = p // 2
+            assert np.array_equal(R[i], (rp.Y[i] + h) % p - h), p
     assert np.array_equal(C[:, rows][:, :, cols], rp.result())
     ratio = exact.ExactProduct(A if not transA else np.ascontiguousarray(A.transpose(0, 2, 1)),
                                B if not transB else np.ascontiguousarray(B.transpose(0, 2, 1)),
@@ -77,6 +86,8 @@ def check_crt(mw, dev, A, B, plan=None, transA=False, transB=False, rows=None, c
     (4, 129, 300, 65, -20, 20),       # 256-column tiles with a ragged second tile
     (2, 300, 520, 100, -6, 6),
     (4, 33, 20, 700, None, None),
+    (4, 64, 33, 300, -45, 45),        # 81 moduli, 20 limbs of X'
+    (4, 50, 40, 300, -60, 60),        # 88 moduli, 24 limbs of X'
 ])
 def test_crt_bit_exact(mw, cuda, m, M, N, K, lo, hi):
     rng = SplitMix64(1000 + m + M + K)
@@ -111,8 +122,8 @@ def test_crt_paper_pattern_and_zeros(mw, cuda):
 
 def test_crt_long_k_reduces_mod_p(mw, cuda):
     """K = 40,000 quad doubles: the moduli above 363 drain every 64 products and
-    reduce their int32 sums mod p every 511 drains; the sums stay congruent to
-    the oracle's exact ones and the words stay bit-exact."""
+    reduce their int32 sums mod p every 511 drains; the stored residues equal
+    those of the oracle's exact sums and the words stay bit-exact."""
     rng = SplitMix64(1030)
     K = 40000
     A, B = loguniform_mdouble(rng, 4, 3, K, -4, 4), loguniform_mdouble(rng, 4, K, 3, -4, 4)
