@@ -143,7 +143,8 @@ __device__ __forceinline__ bool in_range_bits(const uint64_t (&T)[NL], int L) {
 // threads; B (64 x n) the constants c_qt, built once per CTA, zero for q >= S;
 // both in fp16 (exact for integers up to 2048).  The fp32 sums
 // |sum_q d_q c_qt| <= 64 2^15 = 2^21 are exact, and the epilogue reduces them
-// mod p_t (balanced_f) into the bfloat16 residue planes.
+// mod p_t (balanced_f) into a shared tile of bfloat16 residues that one TMA
+// store writes to the residue planes.
 // Digits from bytes: with H = 128 (1 + 2^8 + ... + 2^(8(S-2))), byte q of T + H
 // is d_q + 128 for q < S-1; the fp16 number with exponent field 0x64 and that
 // byte as low mantissa bits is 1024 + byte, so one byte permute and one packed
@@ -154,9 +155,14 @@ __device__ __forceinline__ bool in_range_bits(const uint64_t (&T)[NL], int L) {
 // may hold anything finite.
 // TRANS = false: a tile is 128 consecutive k of one row r; TRANS = true (the
 // operand stored K x R): 4 consecutive r x 32 consecutive k, so that the loads
-// along r and the stores along k both fill whole sectors.
+// along r fill whole sectors.
 constexpr int kResTile = 128;
-constexpr uint32_t kTileBytes = 128 * 128;        // 128 rows x 64 bf16
+constexpr uint32_t kTileBytes = 128 * 128;        // 128 rows x 64 fp16
+
+// Bytes of shared memory of the residue split for npad constants rows.
+inline size_t residue_smem(int npad) {
+  return 1024 + kTileBytes + (size_t)npad * 128 + (size_t)npad * 256 + 32;
+}
 
 template <int MW>
 struct SplitEntry {      // one thread's entry of a tile: position and words
@@ -165,16 +171,33 @@ struct SplitEntry {      // one thread's entry of a tile: position and words
   double x[MW];
 };
 
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int c0, int c1, int c2,
+                                             uint32_t src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          (uint64_t)map),
+      "r"(c0), "r"(c1), "r"(c2), "r"(src)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 template <int MW, int NL, bool TRANS>
-__global__ void __launch_bounds__(kResTile, 2)
-    residues_mma_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t ld,
-                        int64_t ps, int L, int S, int nmod, int npad, __nv_bfloat16 *res,
-                        int64_t dld, const int *E, unsigned int *status) {
+__global__ void __launch_bounds__(kResTile, 4)
+    residues_mma_kernel(const __grid_constant__ CUtensorMap omap, const double *__restrict__ X,
+                        int64_t R, int64_t K, int64_t ld, int64_t ps, int L, int S, int nmod,
+                        int npad, int64_t dld, const int *E, unsigned int *status) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *sA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);  // 2 tiles
-  uint8_t *sB = sA + 2 * kTileBytes;               // npad rows x 64
-  uint64_t *bar = (uint64_t *)(sB + (size_t)npad * 128);
-  uint32_t *holder = (uint32_t *)(bar + 2);
+  uint8_t *sA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sB = sA + kTileBytes;                   // npad rows x 64 constants
+  uint8_t *stage = sB + (size_t)npad * 128;        // npad rows of 128 residues (256 B)
+  uint64_t *bar = (uint64_t *)(stage + (size_t)npad * 256);
+  uint32_t *holder = (uint32_t *)(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int idx = tid; idx < npad * 64; idx += kResTile) {
     const int t = idx >> 6, qc = idx & 63;
@@ -190,11 +213,10 @@ __global__ void __launch_bounds__(kResTile, 2)
   }
   if (tid == 0) {
     mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
     fence_barrier_init();
+    prefetch_map(&omap);
   }
-  // two accumulator regions, one per tile in flight
-  const uint32_t ncols = npad <= 64 ? 128u : 256u, region = ncols / 2;
+  const uint32_t ncols = npad <= 64 ? 64u : 128u;
   if (warp == 0) tmem_alloc(holder, ncols);
   fence_proxy_async_smem();
   __syncthreads();
@@ -203,7 +225,10 @@ __global__ void __launch_bounds__(kResTile, 2)
   const uint32_t idesc = idesc_f16(128, npad);
   const int64_t ktiles = TRANS ? (dld + 31) / 32 : (dld + 127) / 128;
   const int64_t ntiles = (TRANS ? (R + 3) / 4 : R) * ktiles;
-  const int64_t plane = R * dld;
+  // this thread's slot in a row of the shared residue tile: the box is 128 k of
+  // one row, or 4 rows x 32 k
+  const uint32_t slot = TRANS ? (uint32_t)((tid & 3) * 32 + (tid >> 2)) : (uint32_t)tid;
+  uint16_t *mine = reinterpret_cast<uint16_t *>(stage) + slot;
   volatile int abort_flag = 0;
 
   auto fetch = [&](int64_t tile, SplitEntry<MW> &e) {
@@ -220,98 +245,88 @@ __global__ void __launch_bounds__(kResTile, 2)
     for (int j = 0; j < MW; ++j)
       e.x[j] = in ? (TRANS ? X[j * ps + e.k * ld + e.r] : X[j * ps + e.r * ld + e.k]) : 0.0;
   };
-  // digits of the entry into row tid of A tile `slot`, then the tile's MMA
-  auto stage = [&](int slot, const SplitEntry<MW> &e) {
-    uint64_t T[NL];
-    fixed_point<MW, NL>(e.x, e.valid ? L - 2 - E[e.r] : 0, T);
-    if (e.valid && !in_range_bits<NL>(T, L)) raise_status(status, MW_ERANGE);
-    const bool neg = add_bias_w8<NL>(T, S);
-    uint8_t *a = sA + slot * kTileBytes;
+
+  SplitEntry<MW> ec, en;
+  uint32_t ph = 0;
+  bool ok = true;
+  int64_t cur = blockIdx.x;
+  fetch(cur, ec);
+  for (; cur < ntiles; cur += gridDim.x) {
+    // digits of the entry into row tid of A
+    {
+      uint64_t T[NL];
+      fixed_point<MW, NL>(ec.x, ec.valid ? L - 2 - E[ec.r] : 0, T);
+      if (ec.valid && !in_range_bits<NL>(T, L)) raise_status(status, MW_ERANGE);
+      const bool neg = add_bias_w8<NL>(T, S);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {               // 16-byte chunk c: digits 8c .. 8c+7
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
-      if (c < NL) {
+      for (int c = 0; c < 8; ++c) {               // 16-byte chunk c: digits 8c .. 8c+7
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (c < NL) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t word = (uint32_t)(T[c < NL ? c : 0] >> (32 * h));
-          uint32_t lo, hi;
-          asm("prmt.b32 %0, %1, %2, 0x5140;" : "=r"(lo) : "r"(word), "r"(0x64646464u));
-          asm("prmt.b32 %0, %1, %2, 0x7362;" : "=r"(hi) : "r"(word), "r"(0x64646464u));
-          asm("add.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * h]) : "r"(lo), "r"(0xE480E480u));
-          asm("add.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * h + 1]) : "r"(hi), "r"(0xE480E480u));
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t word = (uint32_t)(T[c < NL ? c : 0] >> (32 * h));
+            uint32_t lo, hi;
+            asm("prmt.b32 %0, %1, %2, 0x5140;" : "=r"(lo) : "r"(word), "r"(0x64646464u));
+            asm("prmt.b32 %0, %1, %2, 0x7362;" : "=r"(hi) : "r"(word), "r"(0x64646464u));
+            asm("add.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * h]) : "r"(lo), "r"(0xE480E480u));
+            asm("add.rn.f16x2 %0, %1, %2;" : "=r"(w[2 * h + 1]) : "r"(hi), "r"(0xE480E480u));
+          }
         }
+        if (c == 7) w[3] = neg ? 0xD8000000u : 0x58000000u;   // column 63: -128 / +128 in fp16
+        *reinterpret_cast<uint4 *>(sA + sw128_offset(tid, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
-      if (c == 7) w[3] = neg ? 0xD8000000u : 0x58000000u;   // column 63: -128 / +128 in fp16
-      *reinterpret_cast<uint4 *>(a + sw128_offset(tid, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     fence_proxy_async_smem();
+    if (tid == 0) bulk_wait_read();                // the previous tile's store has read its tile
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint64_t ad = sw128_desc(smem_u32(a)), bd = sw128_desc(smem_u32(sB));
+      const uint64_t ad = sw128_desc(smem_u32(sA)), bd = sw128_desc(smem_u32(sB));
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        tc_mma(tmem + slot * region, ad + 2 * kk, bd + 2 * kk, idesc, kk ? 1u : 0u);
-      tc_commit(&bar[slot]);
+      for (int kk = 0; kk < 4; ++kk) tc_mma(tmem, ad + 2 * kk, bd + 2 * kk, idesc, kk ? 1u : 0u);
+      tc_commit(&bar[0]);
     }
-  };
-  // wait for the tile's MMA, reduce every sum mod p_t and store the residues
-  auto drain = [&](int slot, uint32_t parity, const SplitEntry<MW> &e) -> bool {
-    if (!__syncthreads_and(mbar_wait(&bar[slot], parity, status, &abort_flag))) return false;
+    fetch(cur + gridDim.x, en);                    // the next tile's words load meanwhile
+    ok = __syncthreads_and(mbar_wait(&bar[0], ph, status, &abort_flag));
+    if (!ok) break;
+    ph ^= 1;
     tc_fence_after();
-    const uint32_t ta = tmem + slot * region + ((uint32_t)(warp * 32) << 16);
-    uint16_t *dst = reinterpret_cast<uint16_t *>(res + e.r * dld + e.k);
+    // every sum reduced mod p_t into row t of the shared tile
+    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-    for (int h = 0; h < 3; ++h) {               // 32 moduli at a time
+    for (int h = 0; h < 3; ++h) {                 // 32 moduli at a time
       if (32 * h >= npad) break;
       uint32_t v[32];
       if (32 * h + 32 <= npad) tc_ld32(ta + 32 * h, v);
       else tc_ld16(ta + 32 * h, v);
       tc_wait_ld();
-      if (e.valid) {
-        if (32 * h + 32 <= nmod) {              // a whole chunk: no bound per modulus
+      if (32 * h + 32 <= nmod) {                  // a whole chunk: no bound per modulus
 #pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            *dst = bf16_bits_small(balanced_f(__uint_as_float(v[u]), 32 * h + u));
-            dst += plane;
-          }
-        } else {
+        for (int u = 0; u < 32; ++u)
+          mine[(32 * h + u) * 128] = bf16_bits_small(balanced_f(__uint_as_float(v[u]), 32 * h + u));
+      } else {
 #pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            if (32 * h + u >= nmod) break;
-            *dst = bf16_bits_small(balanced_f(__uint_as_float(v[u]), 32 * h + u));
-            dst += plane;
-          }
+        for (int u = 0; u < 32; ++u) {
+          if (32 * h + u >= nmod) break;
+          mine[(32 * h + u) * 128] = bf16_bits_small(balanced_f(__uint_as_float(v[u]), 32 * h + u));
         }
       }
     }
     tc_fence_before();
-    return true;
-  };
-
-  // two tiles in flight: the next tile's MMA runs while this one drains, and
-  // the words of the tile after it are loaded before this drain
-  int64_t cur = blockIdx.x;
-  if (cur < ntiles) {
-    SplitEntry<MW> ec, en, e2;
-    fetch(cur, ec);
-    stage(0, ec);
-    fetch(cur + gridDim.x, en);
-    uint32_t ph0 = 0, ph1 = 0;
-    int slot = 0;
-    for (;;) {
-      const int64_t nxt = cur + gridDim.x;
-      if (nxt < ntiles) stage(slot ^ 1, en);
-      fetch(nxt + gridDim.x, e2);
-      if (!drain(slot, slot ? ph1 : ph0, ec)) break;
-      if (slot) ph1 ^= 1; else ph0 ^= 1;
-      if (nxt >= ntiles) break;
-      ec = en;
-      en = e2;
-      cur = nxt;
-      slot ^= 1;
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {                                // entries past R or dld are clipped
+      const int64_t rt = cur / ktiles, kt = cur - rt * ktiles;
+      if (TRANS) tma_store_3d(&omap, (int)(kt * 32), (int)(rt * 4), 0, smem_u32(stage));
+      else tma_store_3d(&omap, (int)(kt * 128), (int)rt, 0, smem_u32(stage));
     }
+    ec = en;
   }
+  if (!ok && tid == 0) {                           // a wait gave up: let the product finish
+    volatile int never = 0;
+    mbar_wait(&bar[0], ph, status, &never);
+  }
+  if (tid == 0) bulk_wait_all();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
@@ -321,41 +336,50 @@ __global__ void __launch_bounds__(kResTile, 2)
 
 template <int MW, int NL>
 int launch_residues_t(const SplitArgs &a, cudaStream_t s) {
-  auto *res = static_cast<__nv_bfloat16 *>(a.digits);
   const int S = (a.S + 7) / 8;                     // base-256 digits of an L-bit T
   const int npad = (a.nmod + 15) / 16 * 16;
   if (S > 8 * NL || S > 48 || NL > 6 || npad > 96)
     return fail(MW_EUNSUPPORTED, "residue split: %d digits, %d moduli", S, a.nmod);
-  const size_t smem = 1024 + 2 * kTileBytes + (size_t)npad * 128 + 32;
-  int dev = 0, nsm = 0;
+  if (a.digit_ld % 8 || a.R > 0x7fffffffLL || a.digit_ld > 0x7fffffffLL)
+    return fail(MW_EUNSUPPORTED, "residue split: planes of %lld x %lld", (long long)a.R,
+                (long long)a.digit_ld);
+  // residue planes [t][r][k] of dld columns; boxes of one row x 128 k, or 4 rows
+  // x 32 k, every modulus; no swizzle (the shared tile is dense)
+  alignas(64) CUtensorMap map;
+  const uint64_t dims[3] = {(uint64_t)a.digit_ld, (uint64_t)a.R, (uint64_t)a.nmod};
+  const uint64_t strides[2] = {(uint64_t)a.digit_ld * 2, (uint64_t)a.R * a.digit_ld * 2};
+  const uint32_t box[3] = {a.trans ? 32u : 128u, a.trans ? 4u : 1u, (uint32_t)a.nmod};
+  int rc = make_map_bf16(&map, a.digits, 3, dims, strides, box, false);
+  if (rc) return rc;
+  const size_t smem = residue_smem(npad);
+  auto kern = a.trans ? residues_mma_kernel<MW, NL, true> : residues_mma_kernel<MW, NL, false>;
+  static bool attr[2] = {false, false};
+  if (!attr[a.trans ? 1 : 0]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)residue_smem(96));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return cuda_fail(e, "residue split smem attribute");
+    attr[a.trans ? 1 : 0] = true;
+  }
+  int dev = 0, nsm = 0, smem_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return cuda_fail(e, "residue split attributes");
+  // resident CTAs: shared memory (1 KB reserved per CTA), registers, tensor memory
+  const int by_smem = smem_sm / (int)(smem + 1024);
+  const int by_regs = 65536 / (std::max(fa.numRegs, 1) * kResTile);
+  const int by_tmem = npad <= 64 ? 8 : 4;
+  const int per_sm = std::max(1, std::min({by_smem, by_regs, by_tmem}));
   const int64_t ktiles = a.trans ? (a.digit_ld + 31) / 32 : (a.digit_ld + 127) / 128;
   const int64_t ntiles = (a.trans ? (a.R + 3) / 4 : a.R) * ktiles;
-  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, 2 * (int64_t)nsm);
-  if (a.trans) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(residues_mma_kernel<MW, NL, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 49152);
-      if (e != cudaSuccess) return cuda_fail(e, "residue split smem attribute");
-      attr = true;
-    }
-    residues_mma_kernel<MW, NL, true><<<grid, kResTile, smem, s>>>(
-        a.X, a.R, a.K, a.ld, a.plane_stride, a.S, S, a.nmod, npad, res, a.digit_ld, a.exps,
-        status_ptr());
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(residues_mma_kernel<MW, NL, false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 49152);
-      if (e != cudaSuccess) return cuda_fail(e, "residue split smem attribute");
-      attr = true;
-    }
-    residues_mma_kernel<MW, NL, false><<<grid, kResTile, smem, s>>>(
-        a.X, a.R, a.K, a.ld, a.plane_stride, a.S, S, a.nmod, npad, res, a.digit_ld, a.exps,
-        status_ptr());
-  }
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
+  kern<<<grid, kResTile, smem, s>>>(map, a.X, a.R, a.K, a.ld, a.plane_stride, a.S, S, a.nmod,
+                                    npad, a.digit_ld, a.exps, status_ptr());
   return cuda_fail(cudaGetLastError(), "residue split launch");
 }
 

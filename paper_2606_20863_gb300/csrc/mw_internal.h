@@ -101,10 +101,10 @@ inline int64_t crt_cols(int64_t N) { return (N + kCrtJ - 1) / kCrtJ * kCrtJ; }
 size_t crt_residue_planes_bytes(int64_t M, int64_t N, int D);
 size_t crt_partials_bytes(int64_t M, int64_t N, int D);
 // Tensor map of `rank` dimensions over a bfloat16 array (dims innermost first,
-// strides in bytes of dimensions 1.., box in elements), 128-byte swizzle, zeros
-// outside the array.  map points to a CUtensorMap (64-byte aligned).
+// strides in bytes of dimensions 1.., box in elements), 128-byte swizzle or
+// none, zeros outside the array.  map points to a CUtensorMap (64-byte aligned).
 int make_map_bf16(void *map, const void *base, int rank, const uint64_t *dims,
-                  const uint64_t *strides, const uint32_t *box);
+                  const uint64_t *strides, const uint32_t *box, bool swizzle128 = true);
 
 // ---- textbook form (mw_textbook.cu) ---------------------------------------------
 int launch_textbook(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,

@@ -505,7 +505,7 @@ int make_map_2d(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows,
 }  // namespace
 
 int make_map_bf16(void *map, const void *base, int rank, const uint64_t *dims,
-                  const uint64_t *strides, const uint32_t *box) {
+                  const uint64_t *strides, const uint32_t *box, bool swizzle128) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -527,7 +527,8 @@ int make_map_bf16(void *map, const void *base, int rank, const uint64_t *dims,
   }
   CUresult r = fn(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank,
                   const_cast<void *>(base), d, st, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(MW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return MW_OK;
