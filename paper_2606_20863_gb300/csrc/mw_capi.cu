@@ -194,11 +194,8 @@ int mw_selftest_timeout(unsigned int limit_us, mw_stream_t stream) {
   return cuda_fail(cudaGetLastError(), "self-test launch");
 }
 
-#define MW_STR2(x) #x
-#define MW_STR(x) MW_STR2(x)
 const char *mw_version(void) {
-  return "mw 0.3 (sm_103a, tcgen05 bf16 slices and residues, fp64 pieces; residue blocks of "
-         MW_STR(MW_CRT_J) " columns)";
+  return "mw 0.3 (sm_103a, tcgen05 bf16 slices and residues, fp64 pieces)";
 }
 
 int mw_crt_moduli(int *moduli, int n) {

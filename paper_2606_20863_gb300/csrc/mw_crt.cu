@@ -435,8 +435,9 @@ __global__ void __launch_bounds__(128, 2)
   const int D = F.D, D8 = (D + 7) & ~7, kb = D8;   // kb: the column of ones
   const int KM = (kb + 1 + 15) & ~15, kc = (KM + 63) / 64;
   extern __shared__ uint8_t smem_raw[];
-  // residues of a tile as TMA leaves them (two 64-output halves, D8 rows of 128 B,
-  // swizzled), the MMA's A (128 rows, K-major) and B (NB rows), Horner columns
+  // residues of a tile (128 outputs of one row) as TMA leaves them (two halves of
+  // 64, D8 rows of 128 B, swizzled), the MMA's A (128 rows, K-major) and B (NB
+  // rows), Horner columns
   uint8_t *stage = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = stage + 256 * D8;
   uint8_t *sB = sA + kc * 16384;
@@ -463,16 +464,15 @@ __global__ void __launch_bounds__(128, 2)
   tc_fence_after();
   const uint32_t tmem = *holder;
   const uint32_t idesc = idesc_bf16(128, NB);
-  const int64_t itiles = (M + 127) / 128, ntiles = itiles * N;
+  const int64_t jtiles = (N + 127) / 128, ntiles = jtiles * M;   // a tile: 128 j of one row i
   const uint32_t stage_bytes = 256u * D8;
   volatile int abort_flag = 0;
 
   auto issue = [&](int64_t tile) {                // one thread: the tile's residues
-    const int64_t j = tile / itiles, i0 = (tile - j * itiles) * 128;
-    const int jj = (int)(j % kCrtJ), jb = (int)(j / kCrtJ);
+    const int64_t i = tile / jtiles, j0 = (tile - i * jtiles) * 128;
     mbar_arrive_expect_tx(&bar[0], stage_bytes);
-    tma_load_4d(smem_u32(stage), &map, (int)i0, jj, 0, jb, smem_u32(&bar[0]));
-    tma_load_4d(smem_u32(stage + 128 * D8), &map, (int)i0 + 64, jj, 0, jb, smem_u32(&bar[0]));
+    tma_load_3d(smem_u32(stage), &map, (int)j0, (int)i, 0, smem_u32(&bar[0]));
+    tma_load_3d(smem_u32(stage + 128 * D8), &map, (int)j0 + 64, (int)i, 0, smem_u32(&bar[0]));
   };
   // staged residues (rows t, outputs along the row) into A (rows = outputs):
   // warp w moves outputs 32w..32w+31, eight moduli per step
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(128, 2)
       }
     }
     tc_fence_before();
-    const int64_t j = tile / itiles, i = (tile - j * itiles) * 128 + tid;
+    const int64_t i = tile / jtiles, j = (tile - i * jtiles) * 128 + tid;
 #pragma unroll
     for (int l = 0; l < NL; ++l) col[l * 128 + tid] = U[l];
     col[NL * 128 + tid] = (uint32_t)rc;
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(128, 2)
       U[l] = (uint32_t)v;
       cy = v >> 32;
     }
-    if (i < M) {
+    if (j < N) {
       double *c = C + i * ldc + j;
       round_column<MW, NL>(U, col + tid, 128, eA[i] + eB[j] + ex0,
                            [&](int wd, double v) { c[wd * psc] = v; });
@@ -633,7 +633,7 @@ int launch_crt_fuse_t(const OzakiArgs &a, const CrtFuse &F, const CUtensorMap &m
   const int by_regs = 65536 / (std::max(fa.numRegs, 1) * 128);
   const int by_tmem = (int)(512 / FuseShape<NL>::TCOLS);
   const int per_sm = std::max(1, std::min({by_smem, by_regs, by_tmem}));
-  const int64_t ntiles = (a.M + 127) / 128 * a.N;
+  const int64_t ntiles = (a.N + 127) / 128 * a.M;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
   crt_fuse_kernel<MW, NL><<<grid, 128, smem, s>>>(map, a.eA, a.eB, a.M, a.N, 4 - a.S_A - a.S_B,
                                                   a.C, a.ldc, a.psc, status_ptr(), F);
@@ -757,16 +757,14 @@ int launch_crt_combine(const OzakiArgs &a, cudaStream_t s) {
   const int e = 32 * lo;
   F.c64 = (float)std::ldexp(1.0 / Pd, 32 * (top - 1) - e);
   F.c32 = (float)std::ldexp(1.0 / Pd, 32 * (top - 2) - e);
-  // residues: bf16 [j / J][t][j % J][i], leading dimension crt_ld(M); boxes of 64
-  // outputs x every modulus of one column (moduli past D, outputs past M: zeros)
+  // residues: bf16 planes [t][i][j], rows of crt_ld(N); boxes of 64 outputs of
+  // one row x every modulus (moduli past D, outputs past N: zeros)
   alignas(64) CUtensorMap map;
-  const int64_t ld = crt_ld(a.M);
-  const uint64_t dims[4] = {(uint64_t)a.M, (uint64_t)kCrtJ, (uint64_t)D,
-                            (uint64_t)(crt_cols(a.N) / kCrtJ)};
-  const uint64_t strides[3] = {(uint64_t)ld * 2, (uint64_t)kCrtJ * ld * 2,
-                               (uint64_t)D * kCrtJ * ld * 2};
-  const uint32_t box[4] = {64, 1, (uint32_t)((D + 7) & ~7), 1};
-  int rc = make_map_bf16(&map, a.partials, 4, dims, strides, box);
+  const int64_t ld = crt_ld(a.N);
+  const uint64_t dims[3] = {(uint64_t)a.N, (uint64_t)a.M, (uint64_t)D};
+  const uint64_t strides[2] = {(uint64_t)ld * 2, (uint64_t)a.M * ld * 2};
+  const uint32_t box[3] = {64, 1, (uint32_t)((D + 7) & ~7)};
+  int rc = make_map_bf16(&map, a.partials, 3, dims, strides, box);
   if (rc) return rc;
   switch (a.m) {
     case 2: return launch_crt_fuse_m<2>(a, F, NL, map, s);

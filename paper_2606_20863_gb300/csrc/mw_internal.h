@@ -86,18 +86,10 @@ bool narrow_partials(int S_A, int S_B, int w, int64_t max_K);
 size_t ozaki_partials_planes_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow);
 // Residue form: the product kernel stores the balanced residue of every sum as
-// bfloat16 in blocks of kCrtJ columns, each block holding its columns of every
-// modulus: entry (i, j) of modulus t at ((j / J) D J + t J + j % J) crt_ld(M) + i,
-// crt_ld(M) a multiple of 8 (tensor-map strides are multiples of 16 bytes).
-// Then the 8-byte work counter.
-#ifndef MW_CRT_J
-#define MW_CRT_J 1
-#endif
-constexpr int kCrtJ = MW_CRT_J;
-static_assert(kCrtJ >= 1 && kCrtJ <= 32 && (kCrtJ & (kCrtJ - 1)) == 0,
-              "columns per residue block: a power of two up to 32 (divides every drain's columns)");
-__host__ __device__ inline int64_t crt_ld(int64_t M) { return (M + 7) & ~(int64_t)7; }
-inline int64_t crt_cols(int64_t N) { return (N + kCrtJ - 1) / kCrtJ * kCrtJ; }
+// bfloat16 in row-major planes: entry (i, j) of modulus t at (t M + i) crt_ld(N)
+// + j, crt_ld(N) a multiple of 8 (rows start on 16-byte boundaries and
+// tensor-map strides are multiples of 16 bytes).  Then the 8-byte work counter.
+__host__ __device__ inline int64_t crt_ld(int64_t N) { return (N + 7) & ~(int64_t)7; }
 size_t crt_residue_planes_bytes(int64_t M, int64_t N, int D);
 size_t crt_partials_bytes(int64_t M, int64_t N, int D);
 // Tensor map of `rank` dimensions over a bfloat16 array (dims innermost first,

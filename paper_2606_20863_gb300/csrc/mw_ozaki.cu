@@ -401,22 +401,34 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
               // the balanced residue of each sum S, as bfloat16 (|r| <= 256): with
               // u = S + B_t in [0, 2^32) (|S| < 2^31 - 2^22 + p), u mod p by the
               // reciprocal (the quotient estimate is exact or one short), then
-              // r = u mod p - (p - 1) / 2 as a float from its bits
-              constexpr int J = kCrtJ;                    // divides c0 and COLS
-              const int64_t ldy = crt_ld(x.M), blk = (int64_t)P.D * J * ldy;
-              uint16_t *dst = static_cast<uint16_t *>(P.partials) + (c0 / J) * blk +
-                              (int64_t)t * J * ldy + r;
+              // r = u mod p - (p - 1) / 2 as a float from its bits.  The row's
+              // COLS residues are contiguous: 16-byte stores of eight
               const uint32_t pm = P.crt_p[t], m32 = P.crt_m32[t], off = P.crt_off[t];
               const float cf = P.crt_cf[t];
+              auto resid = [&](uint32_t a) -> uint32_t {   // bf16 bits in the high half
+                const uint32_t u = a - bias + off;
+                const uint32_t r0 = u - __umulhi(u, m32) * pm;
+                const uint32_t rr = min(r0, r0 - pm);
+                return __float_as_uint(__uint_as_float(0x4B400000u + rr) - cf);
+              };
+              uint16_t *dst = static_cast<uint16_t *>(P.partials) +
+                              ((int64_t)t * x.M + r) * crt_ld(x.N) + c0;
+              if (c0 + COLS <= x.N) {
 #pragma unroll
-              for (int i = 0; i < COLS; ++i)
-                if (c0 + i < x.N) {
-                  const uint32_t u = acc[i] - bias + off;
-                  const uint32_t r0 = u - __umulhi(u, m32) * pm;
-                  const uint32_t rr = min(r0, r0 - pm);
-                  dst[(i / J) * blk + (i % J) * ldy] =
-                      (uint16_t)(__float_as_uint(__uint_as_float(0x4B400000u + rr) - cf) >> 16);
+                for (int g = 0; g < COLS / 8; ++g) {
+                  uint32_t w[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e)
+                    asm("prmt.b32 %0, %1, %2, 0x7632;"
+                        : "=r"(w[e])
+                        : "r"(resid(acc[8 * g + 2 * e])), "r"(resid(acc[8 * g + 2 * e + 1])));
+                  *reinterpret_cast<uint4 *>(dst + 8 * g) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
+              } else {
+#pragma unroll
+                for (int i = 0; i < COLS; ++i)
+                  if (c0 + i < x.N) dst[i] = (uint16_t)(resid(acc[i]) >> 16);
+              }
             } else {
               int32_t *dst = static_cast<int32_t *>(P.partials) + x.part + (int64_t)t * x.N * x.M + r;
 #pragma unroll
@@ -662,7 +674,7 @@ size_t ozaki_partials_planes_bytes(int64_t M, int64_t N, int D, int group, bool 
 }
 
 size_t crt_residue_planes_bytes(int64_t M, int64_t N, int D) {
-  return (size_t)D * crt_cols(N) * crt_ld(M) * 2;
+  return (size_t)D * M * crt_ld(N) * 2;
 }
 
 size_t crt_partials_bytes(int64_t M, int64_t N, int D) {

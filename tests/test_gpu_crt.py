@@ -21,12 +21,6 @@ def bf16_to_int(x):
     return x.float().cpu().numpy().astype(np.int64)
 
 
-def residue_block_columns(mw):
-    """Columns per block of the stored residues (the library's version string)."""
-    import re
-    return int(re.search(r"residue blocks of (\d+) columns", mw.version()).group(1))
-
-
 def run_crt(mw, dev, A, B, plan, transA=False, transB=False):
     tA, tB = to_dev(A, dev), to_dev(B, dev)
     m, M, N, K = mw._dims(tA, tB, transA, transB)
@@ -59,12 +53,10 @@ def check_crt(mw, dev, A, B, plan=None, transA=False, transB=False, rows=None, c
         assert np.array_equal(ra, rp.A.residues) and np.array_equal(rb, rp.B.residues)
         assert not bf16_to_int(RA[:, rows, K:]).any() and not bf16_to_int(RB[:, cols, K:]).any()
         # the product kernel leaves the balanced residue of every exact sum Y_p,
-        # bfloat16 [j / J][t][j % J][i], leading dimension M rounded up to 8
-        J = residue_block_columns(mw)
-        ld, nb = -(-M // 8) * 8, -(-N // J)
-        R = ws[off[3]:off[3] + 2 * D * nb * J * ld].view(torch.bfloat16).reshape(nb, D, J, ld)
-        R = bf16_to_int(R[..., :M]).transpose(1, 3, 0, 2).reshape(D, M, nb * J)[:, :, :N]
-        R = R[:, rows][:, :, cols]
+        # bfloat16 row-major planes [t][i][j], rows of N rounded up to 8
+        ld = -(-N // 8) * 8
+        R = ws[off[3]:off[3] + 2 * D * M * ld].view(torch.bfloat16).reshape(D, M, ld)[:, :, :N]
+        R = bf16_to_int(R)[:, rows][:, :, cols]
         for i, p in enumerate(moduli):
             h = p // 2
             assert np.array_equal(R[i], (rp.Y[i] + h) % p - h), p
