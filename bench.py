@@ -280,15 +280,15 @@ def timed(step, steps, flush, mw, dist, dev, phase=True):
 # is captured again.
 KERNEL_SOURCES = ("mw_ozaki.cu", "mw_tc.cuh", "mw_device.cuh", "mw_work.cuh")
 TRAFFIC = {
-    "qd1024": {"bytes": 395363328 + 91096832, "digest": "c15848e119b2e400"},
-    "dd4096": {"bytes": 47455044352 + 1611938048, "digest": "c15848e119b2e400"},
-    "qd4096": {"bytes": 181198118656 + 2540828672, "digest": "c15848e119b2e400"},
+    "qd1024": {"bytes": 399605760 + 90630912, "digest": "81eb59a545940bfc"},
+    "dd4096": {"bytes": 44345757440 + 1610460160, "digest": "81eb59a545940bfc"},
+    "qd4096": {"bytes": 125931728640 + 2540127232, "digest": "81eb59a545940bfc"},
     # 2,000 of the 20,000 products captured (the whole batch holds ~100 GB), x10
-    "od_batch": {"bytes": 10 * (4056931840 + 2792728320), "digest": "c15848e119b2e400"},
+    "od_batch": {"bytes": 10 * (4059287808 + 2794346240), "digest": "81eb59a545940bfc"},
     # residue form, captured at 2048^3 (quad double 69 moduli, double double 40) and
-    # scaled by 4: residue planes and planes of sums both grow with N^2
-    "qd4096_crt": {"bytes": 4 * (1159775000 + 1120246000), "digest": "152b7e1f240e2e73"},
-    "dd4096_crt": {"bytes": 4 * (672518400 + 631561216), "digest": "152b7e1f240e2e73"},
+    # scaled by 4: residue planes in and residues out both grow with N^2
+    "qd4096_crt": {"bytes": 4 * (1158942976 + 549663488), "digest": "81eb59a545940bfc"},
+    "dd4096_crt": {"bytes": 4 * (673336320 + 306032384), "digest": "81eb59a545940bfc"},
 }
 
 
