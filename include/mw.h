@@ -285,7 +285,7 @@ int mw_gemm_batched_workspace_size(const mw_plan *plan, const mw_batch *batch, s
 
 /* Bytes of device workspace mw_measure_spread_batched needs for this batch
  * (host only; at most 8192 + 256 count + 16 (sum_M + sum_N) + sum_MN / 32).
- * MW_EINVAL for m outside {2, 4, 8} or a bad batch summary.
+ * MW_EINVAL for m outside {2, 4, 8, 16} or a bad batch summary.
  * No counterpart in the paper (device memory sizing). */
 int mw_measure_spread_batched_workspace_size(int m, const mw_batch *batch, size_t *bytes);
 
@@ -298,8 +298,9 @@ int mw_measure_spread_batched(int m, const mw_batch *batch, const mw_problem *pr
                               void *ws, size_t ws_bytes, int *range_A, int *range_B,
                               mw_stream_t stream);
 
-/* C_i = A_i B_i for every problem of the batch in the Ozaki form, one plan for
- * all (plan it with the smallest K of the batch for the error bound; its group
+/* C_i = A_i B_i for every problem of the batch in the Ozaki form (m = 2, 4, 8
+ * or 16), one plan for all (plan it with the smallest K of the batch for the
+ * error bound; its group
  * must also fit the largest K).  problems: device array of batch->count
  * descriptors.  Launches a short prologue (offsets of every problem's pieces
  * and partial sums, computed on the GPU from the descriptors), one split of all

@@ -4,7 +4,7 @@ Argument marshalling only: every step of the product runs in the CUDA kernels
 of ``libmw.so`` (C interface ``include/mw.h``); PyTorch supplies device memory
 and the current stream.  An m-double matrix is a float64 tensor of shape
 (m, rows, cols) whose last dimension is contiguous; plane j holds word j of
-every entry (m = 2, 4 or 8).
+every entry (m = 2, 4, 8 or 16).
 
 The functions keep the names of the C entry points: ``mw_plan_gemm``,
 ``mw_split``, ``mw_gemm``, ``mw_gemm_backward``; ``MWGemm`` is the

@@ -592,7 +592,8 @@ int grid_for(int per_sm) {
 int check_batch(const mw_plan *p, const mw_batch *b) {
   if (!p || !b) return fail(MW_EINVAL, "plan/batch is NULL");
   if (p->mode != MW_OZAKI) return fail(MW_EUNSUPPORTED, "batches run in the Ozaki form");
-  if (p->m != 2 && p->m != 4 && p->m != 8) return fail(MW_EINVAL, "batches take m = 2, 4 or 8");
+  if (p->m != 2 && p->m != 4 && p->m != 8 && p->m != 16)
+    return fail(MW_EINVAL, "batches take m = 2, 4, 8 or 16");
   if (b->count < 1 || b->sum_M < 1 || b->sum_N < 1 || b->max_K < 1)
     return fail(MW_EINVAL, "empty batch");
   if (p->w < 2 || p->w > 8 || (int64_t)p->chunk << (2 * p->w - 2) > (1 << 22) || p->chunk % 64)
@@ -663,12 +664,14 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
   }
   const int bits = p.w * std::max(p.S_A, p.S_B) + 3;
   int nl = bits <= 128 ? 2 : bits <= 256 ? 4 : bits <= 384 ? 6 : bits <= 512 ? 8 : bits <= 640 ? 10 : 0;
+  if (p.m == 16) nl = bits <= 896 ? 14 : bits <= 1024 ? 16 : 0;   // 52 x 16 bits and more
   if (!nl) return fail(MW_EUNSUPPORTED, "w*S too large");
 #define MW_SPLIT_CASE(MWV, NLV) \
   if (p.m == MWV && nl == NLV) { int rc = launch_split_nl<MWV, NLV>(info, hdr, b, p, w8, L, exps_only, s); if (rc) return rc; }
   MW_SPLIT_CASE(2, 2) MW_SPLIT_CASE(2, 4) MW_SPLIT_CASE(2, 6) MW_SPLIT_CASE(2, 8) MW_SPLIT_CASE(2, 10)
   MW_SPLIT_CASE(4, 2) MW_SPLIT_CASE(4, 4) MW_SPLIT_CASE(4, 6) MW_SPLIT_CASE(4, 8) MW_SPLIT_CASE(4, 10)
   MW_SPLIT_CASE(8, 2) MW_SPLIT_CASE(8, 4) MW_SPLIT_CASE(8, 6) MW_SPLIT_CASE(8, 8) MW_SPLIT_CASE(8, 10)
+  MW_SPLIT_CASE(16, 14) MW_SPLIT_CASE(16, 16)
 #undef MW_SPLIT_CASE
   return cuda_fail(cudaGetLastError(), "batch split launch");
 }
@@ -689,9 +692,28 @@ void launch_combine_b(const BInfo *info, const BHeader *hdr, const mw_batch &b,
 }
 
 template <int MW>
+int combine_nl_small(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
+                     uint8_t *w8, const Layout &L, cudaStream_t s, int bits);
+
+template <int MW>
 int combine_nl(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
                uint8_t *w8, const Layout &L, cudaStream_t s) {
   const int bits = 64 + p.w * (p.D - 1) + 1;
+  if constexpr (MW == 16) {          // at least 52 x 16 bits: 14 to 17 limbs
+    if (bits <= 896) launch_combine_b<MW, 14>(info, hdr, b, p, w8, L, s);
+    else if (bits <= 960) launch_combine_b<MW, 15>(info, hdr, b, p, w8, L, s);
+    else if (bits <= 1024) launch_combine_b<MW, 16>(info, hdr, b, p, w8, L, s);
+    else if (bits <= 1088) launch_combine_b<MW, 17>(info, hdr, b, p, w8, L, s);
+    else return fail(MW_EUNSUPPORTED, "too many diagonals for the fusion");
+    return cuda_fail(cudaGetLastError(), "batch combine launch");
+  } else {
+    return combine_nl_small<MW>(info, hdr, b, p, w8, L, s, bits);
+  }
+}
+
+template <int MW>
+int combine_nl_small(const BInfo *info, const BHeader *hdr, const mw_batch &b, const mw_plan &p,
+                     uint8_t *w8, const Layout &L, cudaStream_t s, int bits) {
   if (bits <= 256) launch_combine_b<MW, 4>(info, hdr, b, p, w8, L, s);
   else if (bits <= 320) launch_combine_b<MW, 5>(info, hdr, b, p, w8, L, s);
   else if (bits <= 384) launch_combine_b<MW, 6>(info, hdr, b, p, w8, L, s);
@@ -806,7 +828,8 @@ int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem
   switch (p.m) {
     case 2: rc = combine_nl<2>(info, hdr, b, p, w8, L, s); break;
     case 4: rc = combine_nl<4>(info, hdr, b, p, w8, L, s); break;
-    default: rc = combine_nl<8>(info, hdr, b, p, w8, L, s); break;
+    case 8: rc = combine_nl<8>(info, hdr, b, p, w8, L, s); break;
+    default: rc = combine_nl<16>(info, hdr, b, p, w8, L, s); break;
   }
   phase(3, s);
   return rc;

@@ -200,7 +200,7 @@ def test_batch_describe_sums(mw):
     assert rc == mw.MW_EINVAL
 
 
-def test_batch_workspace_grows_and_rejects_hexa_doubles(mw):
+def test_batch_workspace_grows_and_takes_hexa_doubles(mw):
     small, big = _describe(mw, [(8, 8, 8)] * 10)[1], _describe(mw, [(100, 100, 100)] * 10)[1]
     size_s, size_b = ctypes.c_size_t(0), ctypes.c_size_t(0)
     p = _ozaki_plan(mw, 8)
@@ -212,6 +212,11 @@ def test_batch_workspace_grows_and_rejects_hexa_doubles(mw):
     assert size_b.value > size_s.value and size_b.value >= 2 * 10 * 56 * 100 * 128 * 2
     p16 = _ozaki_plan(mw, 16, S=112, D=116)
     assert mw._lib.mw_gemm_batched_workspace_size(ctypes.byref(p16), ctypes.byref(small),
+                                                  ctypes.byref(size_s)) == mw.MW_OK
+    assert size_s.value >= 2 * 10 * 112 * 8 * 64 * 2      # 112 planes of the 8 x 8 problems
+    p3 = _ozaki_plan(mw, 8)
+    p3.m = 3
+    assert mw._lib.mw_gemm_batched_workspace_size(ctypes.byref(p3), ctypes.byref(small),
                                                   ctypes.byref(size_s)) == mw.MW_EINVAL
 
 
@@ -237,4 +242,4 @@ def test_batch_spread_workspace_bound(mw):
         assert rc == mw.MW_ENOSPC
     size = ctypes.c_size_t(0)
     assert mw._lib.mw_measure_spread_batched_workspace_size(
-        16, ctypes.byref(b), ctypes.byref(size)) == mw.MW_EINVAL
+        3, ctypes.byref(b), ctypes.byref(size)) == mw.MW_EINVAL

@@ -16,7 +16,7 @@ def single(mw, A, B, plan):
     return mw.mw_gemm(A, B, plan)
 
 
-@pytest.mark.parametrize("m", [2, 4, 8])
+@pytest.mark.parametrize("m", [2, 4, 8, 16])
 def test_batch_of_uneven_products(mw, cuda, m):
     rng = SplitMix64(600 + m)
     shapes = [(1, 1, 1), (8, 8, 8), (130, 7, 64), (17, 200, 65), (128, 128, 128), (3, 129, 300),
