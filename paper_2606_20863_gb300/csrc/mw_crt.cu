@@ -418,14 +418,15 @@ struct FuseShape {
   static constexpr uint32_t TCOLS = 2 * NB <= 128 ? 128u : 256u;   // two accumulators
 };
 
-// Bytes of shared memory the reconstruction kernel uses for D moduli and NL limbs.
-inline size_t fuse_smem(int D, int NL) {
+// Bytes of shared memory the reconstruction kernel uses for D moduli and NL limbs
+// (with the rounding's limb columns in shared memory unless LCOL).
+inline size_t fuse_smem(int D, int NL, bool lcol) {
   const int D8 = (D + 7) & ~7, KM = (D8 + 1 + 15) & ~15, kc = (KM + 63) / 64;
   return 1024 + (size_t)256 * D8 + (size_t)kc * 16384 + (size_t)kc * 4 * NL * 128 +
-         (size_t)(NL + 1) * 512 + 32;
+         (lcol ? 0 : (size_t)(NL + 1) * 512) + 32;
 }
 
-template <int MW, int NL>
+template <int MW, int NL, bool LCOL>
 __global__ void __launch_bounds__(128, 2)
     crt_fuse_kernel(const __grid_constant__ CUtensorMap map, const int32_t *eA, const int32_t *eB,
                     int64_t M, int64_t N, int ex0, double *C, int64_t ldc, int64_t psc,
@@ -437,12 +438,13 @@ __global__ void __launch_bounds__(128, 2)
   extern __shared__ uint8_t smem_raw[];
   // residues of a tile (128 outputs of one row) as TMA leaves them (two halves of
   // 64, D8 rows of 128 B, swizzled), the MMA's A (128 rows, K-major) and B (NB
-  // rows), Horner columns
+  // rows), then (unless LCOL: each thread's local memory, when shared memory would
+  // hold fewer CTAs than the tensor memory) the limbs the rounding reads by index
   uint8_t *stage = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = stage + 256 * D8;
   uint8_t *sB = sA + kc * 16384;
-  uint32_t *col = (uint32_t *)(sB + kc * NB * 128);          // [NL + 1][128]
-  uint64_t *bar = (uint64_t *)(col + (NL + 1) * 128);        // residues, accumulators 0, 1
+  uint32_t *colsm = (uint32_t *)(sB + kc * NB * 128);        // [NL + 1][128] unless LCOL
+  uint64_t *bar = (uint64_t *)(colsm + (LCOL ? 0 : (NL + 1) * 128));   // residues, accumulators
   uint32_t *holder = (uint32_t *)(bar + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int idx = tid; idx < kc * 64 * NB; idx += 128) {
@@ -513,12 +515,15 @@ __global__ void __launch_bounds__(128, 2)
     }
     tc_fence_before();
     const int64_t i = tile / jtiles, j = (tile - i * jtiles) * 128 + tid;
+    uint32_t lcol[LCOL ? NL + 1 : 1];              // read by index: local memory
+    uint32_t *col = LCOL ? lcol : colsm + tid;
+    constexpr int cs = LCOL ? 1 : 128;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) col[l * 128 + tid] = U[l];
-    col[NL * 128 + tid] = (uint32_t)rc;
+    for (int l = 0; l < NL; ++l) col[l * cs] = U[l];
+    col[NL * cs] = (uint32_t)rc;
     const int top = F.top;
-    const uint64_t hi = ((uint64_t)col[top * 128 + tid] << 32) | col[(top - 1) * 128 + tid];
-    const float kf = fmaf((float)(int64_t)hi, F.c64, (float)col[(top - 2) * 128 + tid] * F.c32);
+    const uint64_t hi = ((uint64_t)col[top * cs] << 32) | col[(top - 1) * cs];
+    const float kf = fmaf((float)(int64_t)hi, F.c64, (float)col[(top - 2) * cs] * F.c32);
     const int k = (int)(__float_as_uint(kf + 12582912.0f) - 0x4B400000u);
     const bool pos = k > 0;
     const uint32_t ak = (uint32_t)(pos ? k : -k);
@@ -531,7 +536,7 @@ __global__ void __launch_bounds__(128, 2)
     }
     if (j < N) {
       double *c = C + i * ldc + j;
-      round_column<MW, NL>(U, col + tid, 128, eA[i] + eB[j] + ex0,
+      round_column<MW, NL>(U, col, cs, eA[i] + eB[j] + ex0,
                            [&](int wd, double v) { c[wd * psc] = v; });
     }
     return true;
@@ -604,40 +609,51 @@ __global__ void __launch_bounds__(128, 2)
   }
 }
 
-template <int MW, int NL>
-int launch_crt_fuse_t(const OzakiArgs &a, const CrtFuse &F, const CUtensorMap &map,
+template <int MW, int NL, bool LCOL>
+int launch_crt_fuse_v(const OzakiArgs &a, const CrtFuse &F, const CUtensorMap &map, int per_sm,
                       cudaStream_t s) {
-  const size_t smem = fuse_smem(F.D, NL);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(crt_fuse_kernel<MW, NL>,
+    cudaError_t e = cudaFuncSetAttribute(crt_fuse_kernel<MW, NL, LCOL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fuse_smem(kCrtMaxModuli, NL));
+                                         (int)fuse_smem(kCrtMaxModuli, NL, LCOL));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(crt_fuse_kernel<MW, NL>,
+      e = cudaFuncSetAttribute(crt_fuse_kernel<MW, NL, LCOL>,
                                cudaFuncAttributePreferredSharedMemoryCarveout,
                                cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return cuda_fail(e, "reconstruction smem attribute");
     attr = true;
   }
-  int dev = 0, nsm = 0, smem_sm = 0;
+  int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  cudaFuncAttributes fa{};
-  cudaError_t e = cudaFuncGetAttributes(&fa, crt_fuse_kernel<MW, NL>);
-  if (e != cudaSuccess) return cuda_fail(e, "reconstruction attributes");
-  // resident CTAs: what shared memory (1 KB reserved per CTA), registers and the
-  // tensor memory (512 columns) hold
-  const int by_smem = smem_sm / (int)(smem + 1024);
-  const int by_regs = 65536 / (std::max(fa.numRegs, 1) * 128);
-  const int by_tmem = (int)(512 / FuseShape<NL>::TCOLS);
-  const int per_sm = std::max(1, std::min({by_smem, by_regs, by_tmem}));
   const int64_t ntiles = (a.N + 127) / 128 * a.M;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
-  crt_fuse_kernel<MW, NL><<<grid, 128, smem, s>>>(map, a.eA, a.eB, a.M, a.N, 4 - a.S_A - a.S_B,
-                                                  a.C, a.ldc, a.psc, status_ptr(), F);
+  crt_fuse_kernel<MW, NL, LCOL><<<grid, 128, fuse_smem(F.D, NL, LCOL), s>>>(
+      map, a.eA, a.eB, a.M, a.N, 4 - a.S_A - a.S_B, a.C, a.ldc, a.psc, status_ptr(), F);
   return cuda_fail(cudaGetLastError(), "residue reconstruction launch");
+}
+
+template <int MW, int NL>
+int launch_crt_fuse_t(const OzakiArgs &a, const CrtFuse &F, const CUtensorMap &map,
+                      cudaStream_t s) {
+  int dev = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, crt_fuse_kernel<MW, NL, false>);
+  if (e != cudaSuccess) return cuda_fail(e, "reconstruction attributes");
+  // resident CTAs: what shared memory (1 KB reserved per CTA), registers and the
+  // tensor memory (512 columns) hold; the limb columns leave shared memory only
+  // when that lets more CTAs reside
+  const int by_regs = 65536 / (std::max(fa.numRegs, 1) * 128);
+  const int by_tmem = (int)(512 / FuseShape<NL>::TCOLS);
+  const int cap = std::min(by_regs, by_tmem);
+  const int in_smem = smem_sm / (int)(fuse_smem(F.D, NL, false) + 1024);
+  const int in_local = smem_sm / (int)(fuse_smem(F.D, NL, true) + 1024);
+  if (std::min(in_local, cap) > std::min(in_smem, cap))
+    return launch_crt_fuse_v<MW, NL, true>(a, F, map, std::max(1, std::min(in_local, cap)), s);
+  return launch_crt_fuse_v<MW, NL, false>(a, F, map, std::max(1, std::min(in_smem, cap)), s);
 }
 
 template <int MW>
