@@ -43,7 +43,9 @@ constexpr int kMaxStack = 8;
 struct Layout {
   size_t header, info, eA, spA, eB, spB, rowtab, stripetab, outtab, pieceA, pieceB, items,
       partials, total;
-  int64_t Kpitch;
+  int64_t Kpitch;     // row pitch of the pieces (A when packed)
+  int64_t KpitchB;    // row pitch of B's pieces
+  bool packed;        // K-packed pieces (narrow batches, see BInfo)
   int64_t items_max;  // bound on the work items, from the batch sums
   int64_t rowsB;      // piece rows of B (bound: every problem with the most zero slices)
   int bn, rmax;       // tile width, most B slices per MMA
@@ -56,11 +58,21 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 Layout layout_of(const mw_plan &p, const mw_batch &b) {
   Layout L{};
-  L.Kpitch = round_up(b.max_K, 64);
+  L.Kpitch = L.KpitchB = round_up(b.max_K, 64);
   L.narrow = narrow_partials(p.S_A, p.S_B, p.w, b.max_K);
+  L.packed = L.narrow;
   L.bn = L.narrow ? 256 : 128;
   L.rmax = L.narrow ? std::min(kMaxStack, p.D) : 1;
   L.rowsB = (int64_t)(p.S_B + 2 * (L.rmax - 1)) * b.sum_N;
+  if (L.packed) {
+    // a row of A: S_A slices of K8 and 64 zero columns; a row of B: S_B slices,
+    // (rs - 1) K8 zero columns before them and (rs - 1) K8 + 64 (rounded up to
+    // K8, at most 63 more) after them
+    const int64_t K8 = round_up(b.max_K, 8);
+    L.Kpitch = round_up((int64_t)p.S_A * K8 + 64, 8);
+    L.KpitchB = round_up((2 * (L.rmax - 1) + p.S_B) * K8 + 128, 8);
+    L.rowsB = b.sum_N;
+  }
   size_t off = 0;
   L.header = off; off = a256(off + sizeof(BHeader));
   L.info = off;   off = a256(off + sizeof(BInfo) * (size_t)b.count);
@@ -73,8 +85,9 @@ Layout layout_of(const mw_plan &p, const mw_batch &b) {
   L.rowtab = off;    off = a256(off + 4 * (size_t)b.sum_M);
   L.stripetab = off; off = a256(off + 4 * (size_t)(b.sum_N / 32 + b.count + 1));
   L.outtab = off;    off = a256(off + 4 * (size_t)(b.sum_MN / 256 + 2));
-  L.pieceA = off; off = a256(off + 2 * (size_t)p.S_A * b.sum_M * L.Kpitch);
-  L.pieceB = off; off = a256(off + 2 * (size_t)L.rowsB * L.Kpitch);
+  L.pieceA = off;
+  off = a256(off + 2 * (size_t)(L.packed ? 1 : p.S_A) * b.sum_M * L.Kpitch);
+  L.pieceB = off; off = a256(off + 2 * (size_t)L.rowsB * L.KpitchB);
   L.planes = L.narrow ? p.D : n_groups(p.D, p.group);
   // Diagonals per work item of a problem with one B slice per MMA.  The items
   // of one tile are handed out one after another, so the CTAs at work share
@@ -86,7 +99,8 @@ Layout layout_of(const mw_plan &p, const mw_batch &b) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const double tile_bytes = 2.0 * L.Kpitch * ((double)p.S_A * BM + (double)p.S_B * L.bn);
+    const double tile_bytes = 2.0 * ((double)L.Kpitch * BM * (L.packed ? 1 : p.S_A) +
+                                     (double)L.KpitchB * L.bn * (L.packed ? 1 : p.S_B));
     const int per_tile = (int)std::min<double>(p.D, std::ceil(nsm * tile_bytes / kL2Budget));
     L.sched = (p.D + std::max(per_tile, 1) - 1) / std::max(per_tile, 1);
   } else {
@@ -133,7 +147,7 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t *sh) {
 __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs, int count,
                                                         int D, int sched, int bn, int rmax,
                                                         int planes, int S_A, int S_B,
-                                                        int64_t Kpitch, int64_t items_max,
+                                                        int packed, int64_t items_max,
                                                         mw_batch want, BInfo *info, BHeader *hdr,
                                                         unsigned int *status) {
   __shared__ int64_t sh[33];
@@ -142,18 +156,22 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
   for (int base = 0; base < count; base += 1024) {
     const int i = base + threadIdx.x;
     int64_t M = 0, N = 0, K = 0, w = 0;
-    int tm = 0, tn = 0, rs = 1, nd = 1, G = 0;
+    int tm = 0, tn = 0, rs = 1, nd = 1, G = 0, K8 = 0, Z = 0;
     mw_problem p{};
     if (i < count) {
       p = probs[i];
       M = p.M; N = p.N; K = p.K;
-      const bool ok = M > 0 && N > 0 && K > 0 && K <= Kpitch && p.A && p.B && p.C &&
+      const bool ok = M > 0 && N > 0 && K > 0 && K <= want.max_K && p.A && p.B && p.C &&
                       p.lda >= K && p.ldb >= N && p.ldc >= N;
       if (!ok) { bad = 1; M = N = K = 0; }
       tm = (int)((M + BM - 1) / BM);
       tn = (int)((N + bn - 1) / bn);
       // B slices side by side when the problem's N fits twice or more in a tile
-      rs = (rmax > 1 && N > 0) ? (int)max((int64_t)1, min((int64_t)rmax, (int64_t)bn / N)) : 1;
+      // (K-packed: column blocks of N rounded up to 8)
+      const int64_t Nb = packed ? (N + 7) & ~(int64_t)7 : N;
+      rs = (rmax > 1 && N > 0) ? (int)max((int64_t)1, min((int64_t)rmax, (int64_t)bn / Nb)) : 1;
+      K8 = (int)((K + 7) & ~(int64_t)7);
+      Z = packed ? rs - 1 : 0;
       nd = rs > 1 ? rs : sched;
       G = (D + nd - 1) / nd;
       w = (int64_t)tm * tn * G;
@@ -171,7 +189,9 @@ __global__ void __launch_bounds__(1024) prologue_kernel(const mw_problem *probs,
       b.A = p.A; b.lda = p.lda; b.psa = p.plane_stride_a;
       b.B = p.B; b.ldb = p.ldb; b.psb = p.plane_stride_b;
       b.C = p.C; b.ldc = p.ldc; b.psc = p.plane_stride_c;
-      b.rowA = (int64_t)S_A * pM; b.rowB = pRB;
+      b.rowA = packed ? pM : (int64_t)S_A * pM;
+      b.rowB = packed ? pN : pRB;
+      b.K8 = K8; b.Z = Z;
       b.eA = pM; b.eB = pN; b.part = (int64_t)planes * pMN; b.work = pW; b.outs = pMN; b.stripes = pS;
       b.tiles_m = tm; b.tiles_n = tn; b.KB = (int)((K + BK - 1) / BK);
       b.rs = rs; b.nd = nd; b.G = G;
@@ -229,7 +249,7 @@ template <int MW, int NL, bool W8>
 __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
     const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
     __nv_bfloat16 *pieceA, int32_t *eA, int32_t *spA, int32_t *max_spread, int range,
-    int exps_only, const int32_t *rowtab, unsigned int *status) {
+    int exps_only, int packed, const int32_t *rowtab, unsigned int *status) {
   if (hdr->bad) return;
   // m >= 8, w = 8: each word adds its fields into this thread's column of slots
   // (cut_column) instead of a carry chain over every limb
@@ -279,10 +299,14 @@ __global__ void __launch_bounds__(256, 4) batch_split_rows_kernel(
     };
     if (!lead) finish(E, emax == kExpZero ? 0 : emax - emin, nonfinite);
     if (exps_only) continue;
+    // slice p of entry k at dst + p plane + k: planes of M rows, or (K-packed) the
+    // row's slices back to back, K8 apart, then 64 zero columns
     __nv_bfloat16 *dst = pieceA + (b.rowA + r) * Kpitch;
-    const int64_t plane = b.M * Kpitch;
+    const int64_t plane = packed ? (int64_t)b.K8 : b.M * Kpitch;
     const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-    const int64_t Kp = (K + 63) & ~(int64_t)63;
+    const int64_t Kp = packed ? (int64_t)b.K8 : (K + 63) & ~(int64_t)63;
+    if (packed)
+      for (int c = lane; c < 64; c += 32) dst[(int64_t)S * b.K8 + c] = zero;
     for (int attempt = 0; attempt < 2; ++attempt) {
       const int F = w * S - 2 - E;
       int tmax = kExpZero, tmin = -kExpZero;       // entry exponents over every word
@@ -353,7 +377,7 @@ template <int MW, int NL, bool W8>
 __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
     const BInfo *info, const BHeader *hdr, int count, int w, int S, int64_t Kpitch,
     __nv_bfloat16 *pieceB, int32_t *eB, int32_t *spB, int32_t *max_spread, int range,
-    int exps_only, const int32_t *stripetab, unsigned int *status) {
+    int exps_only, int packed, const int32_t *stripetab, unsigned int *status) {
   extern __shared__ double tile[];              // [MW][16 k][33], then for the column
                                                 // cut the threads' slots
   __shared__ int smax[8][32], smin[8][32], sE[32];
@@ -407,9 +431,21 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
       }
     }
     __syncthreads();
+    // K-packed: the row of column j holds zk zeros, slices S-1 .. 0, zh zeros
+    const int64_t K8 = b.K8, zk = (int64_t)b.Z * K8;
+    const int64_t zh = packed ? ((int64_t)(b.rs - 1) * K8 + 64 + K8 - 1) / K8 * K8 : 0;
+    if (!exps_only && packed) {
+      const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+      const int64_t zt = zk + zh;                  // zero columns of a row
+      for (int64_t e = threadIdx.x; e < 32 * zt; e += 256) {
+        const int64_t jl = e / zt, pos = e - jl * zt;
+        if (j0 + jl < b.N)
+          pieceB[(b.rowB + j0 + jl) * Kpitch + (pos < zk ? pos : pos + (int64_t)S * K8)] = zero;
+      }
+    }
     if (!exps_only) for (int attempt = 0; attempt < 2; ++attempt) {
-      const int64_t plane = b.N * Kpitch;
-      const int64_t Kp = (K + 63) & ~(int64_t)63;
+      const int64_t plane = packed ? -K8 : b.N * Kpitch;
+      const int64_t Kp = packed ? (K8 + 15) & ~(int64_t)15 : (K + 63) & ~(int64_t)63;
       if (ty == 0) {
         tmx[tx] = kExpZero;
         tmn[tx] = -kExpZero;
@@ -442,16 +478,20 @@ __global__ void __launch_bounds__(256, 2) batch_split_cols_kernel(
           const int e = threadIdx.x + 256 * it;   // 512 entries per tile, k fastest
           const int jl = e >> 4, kl = e & 15;
           const int64_t jj = j0 + jl, k = k0 + kl;
-          if (jj >= b.N) continue;
-          // slice q of column jj at row rowB + (q + rs - 1) N + jj; the rs - 1 slices
-          // before slice 0 and after slice S - 1 are zero
-          __nv_bfloat16 *dst = pieceB + (b.rowB + (int64_t)(b.rs - 1) * b.N + jj) * Kpitch + k;
+          if (jj >= b.N || (packed && k >= K8)) continue;
+          // slice q of column jj at row rowB + (q + rs - 1) N + jj, the rs - 1 slices
+          // before slice 0 and after slice S - 1 zero; K-packed: at column
+          // (Z + S - 1 - q) K8 + k of row rowB + jj
+          __nv_bfloat16 *dst = packed
+              ? pieceB + (b.rowB + jj) * Kpitch + (zk + (int64_t)(S - 1) * K8) + k
+              : pieceB + (b.rowB + (int64_t)(b.rs - 1) * b.N + jj) * Kpitch + k;
           const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
           if (attempt == 0) {
-            for (int p = 1; p < b.rs; ++p) {
-              dst[-p * plane] = zero;
-              dst[(S - 1 + p) * plane] = zero;
-            }
+            if (!packed)
+              for (int p = 1; p < b.rs; ++p) {
+                dst[-p * plane] = zero;
+                dst[(S - 1 + p) * plane] = zero;
+              }
             if (k >= K) {
               __nv_bfloat16 *q = dst;
               for (int p = 0; p < S; ++p, q += plane) *q = zero;
@@ -616,8 +656,8 @@ int launch_split_w(const BInfo *info, const BHeader *hdr, const mw_batch &b, con
   batch_split_rows_kernel<MW, NL, W8><<<grid_for(8), 256, 0, s>>>(
       info, hdr, b.count, p.w, p.S_A, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceA),
       reinterpret_cast<int32_t *>(w8 + L.eA), reinterpret_cast<int32_t *>(w8 + L.spA),
-      h->max_spread, p.range_A, exps_only, reinterpret_cast<const int32_t *>(w8 + L.rowtab),
-      status_ptr());
+      h->max_spread, p.range_A, exps_only, L.packed ? 1 : 0,
+      reinterpret_cast<const int32_t *>(w8 + L.rowtab), status_ptr());
   // the 16-row tile, then (w = 8, m >= 8) 256 columns of (64 NL - 8) / 24 + 4 slots
   const size_t sm = (size_t)MW * 16 * 33 * sizeof(double) +
                     (W8 && MW >= 8 ? (size_t)((64 * NL - 8) / 24 + 4) * 256 * sizeof(uint32_t) : 0);
@@ -629,9 +669,9 @@ int launch_split_w(const BInfo *info, const BHeader *hdr, const mw_batch &b, con
     attr_set = true;
   }
   batch_split_cols_kernel<MW, NL, W8><<<grid_for(2), 256, sm, s>>>(
-      info, hdr, b.count, p.w, p.S_B, L.Kpitch, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceB),
+      info, hdr, b.count, p.w, p.S_B, L.KpitchB, reinterpret_cast<__nv_bfloat16 *>(w8 + L.pieceB),
       reinterpret_cast<int32_t *>(w8 + L.eB), reinterpret_cast<int32_t *>(w8 + L.spB),
-      h->max_spread + 1, p.range_B, exps_only,
+      h->max_spread + 1, p.range_B, exps_only, L.packed ? 1 : 0,
       reinterpret_cast<const int32_t *>(w8 + L.stripetab), status_ptr());
   return MW_OK;
 }
@@ -651,7 +691,8 @@ int run_front(const mw_plan &p, const mw_batch &b, const mw_problem *probs, void
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(BHeader), s);
   if (e != cudaSuccess) return cuda_fail(e, "batch header memset");
   prologue_kernel<<<1, 1024, 0, s>>>(probs, b.count, p.D, L.sched, L.bn, L.rmax, L.planes, p.S_A,
-                                     p.S_B, L.Kpitch, L.items_max, b, info, hdr, status_ptr());
+                                     p.S_B, L.packed ? 1 : 0, L.items_max, b, info, hdr,
+                                     status_ptr());
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch prologue launch");
   lookup_tables_kernel<<<(unsigned)std::min<int64_t>((b.count + 7) / 8, grid_for(4)), 256, 0, s>>>(
       info, hdr, b.count, reinterpret_cast<int32_t *>(w8 + L.rowtab),
@@ -814,7 +855,8 @@ int mw_gemm_batched(const mw_plan *plan, const mw_batch *batch, const mw_problem
   phase(1, s);
   ProductLaunch P{};
   P.pieceA = w8 + L.pieceA; P.pieceB = w8 + L.pieceB;
-  P.rowsA = (int64_t)p.S_A * b.sum_M; P.rowsB = L.rowsB; P.Kpitch = L.Kpitch;
+  P.rowsA = (int64_t)(L.packed ? 1 : p.S_A) * b.sum_M; P.rowsB = L.rowsB;
+  P.Kpitch = L.Kpitch; P.KpitchB = L.KpitchB;
   P.S_A = p.S_A; P.S_B = p.S_B; P.D = p.D; P.w = p.w; P.group = L.sched; P.chunk = p.chunk;
   P.info = w8 + L.info; P.hdr = w8 + L.header; P.count = b.count;
   P.item_problem = reinterpret_cast<const int32_t *>(w8 + L.items);

@@ -61,8 +61,8 @@ int dot_pieces_range(int m, int *lo, int *hi);
 void phase(int i, cudaStream_t s);
 
 struct ProductLaunch {
-  const void *pieceA, *pieceB;  // bf16 pieces, rows of Kpitch elements
-  int64_t rowsA, rowsB, Kpitch;
+  const void *pieceA, *pieceB;  // bf16 pieces, rows of Kpitch (A) and KpitchB (B) elements
+  int64_t rowsA, rowsB, Kpitch, KpitchB;
   int S_A, S_B, D, w, group, chunk;
   const void *info, *hdr;
   const int32_t *item_problem;    // batches: problem of every work item, or nullptr

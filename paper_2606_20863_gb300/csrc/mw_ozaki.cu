@@ -101,16 +101,22 @@ struct PParams {
   BInfo single;
 };
 
-// Tensor maps over the two piece arrays with boxes of 16, 32, 48, ..., 256 rows:
-// a tile loads only the rows its problem has, rounded up to 16 (rows past them
-// would only feed outputs that are never stored).  4 KB of kernel parameters.
-constexpr int NBOX = 16;
+// Tensor maps over the two piece arrays with boxes of 16, 32, ..., 256 rows (A)
+// and 8, 16, ..., 256 rows (B): a tile loads only the rows its problem has,
+// rounded up (rows past them would only feed outputs that are never stored).
+// 6 KB of kernel parameters.
+constexpr int NBOX = 16, NBOXB = 32;
 struct Maps {
-  CUtensorMap a[NBOX], b[NBOX];
+  CUtensorMap a[NBOX], b[NBOXB];
 };
 __host__ __device__ constexpr int box_rows(int i) { return 16 * (i + 1); }
 __device__ __forceinline__ int box_index(int64_t rows) {
   return rows <= 16 ? 0 : rows >= 256 ? NBOX - 1 : (int)((rows + 15) >> 4) - 1;
+}
+// B boxes in steps of 8 rows: a stacked block of N8 rows starts on a swizzle atom
+__host__ __device__ constexpr int box_rows_b(int i) { return 8 * (i + 1); }
+__device__ __forceinline__ int box_index_b(int64_t rows) {
+  return rows <= 8 ? 0 : rows >= 256 ? NBOXB - 1 : (int)((rows + 7) >> 3) - 1;
 }
 
 __device__ __forceinline__ const BInfo &problem(const PParams &P, int i) {
@@ -118,7 +124,7 @@ __device__ __forceinline__ const BInfo &problem(const PParams &P, int i) {
 }
 
 struct Item {
-  int i, g, t0, t1, tm, tn, KB, rs;
+  int i, g, t0, t1, tm, tn, KB, rs, K8, Z, N8;
   int64_t M, N, rowA, rowB, part;
 };
 
@@ -141,6 +147,7 @@ __device__ __forceinline__ Item decode_item(const PParams &P, int64_t u) {
   x.t1 = min(P.D, x.t0 + nd) - 1;
   x.rs = P.info ? b.rs : 1;
   x.KB = b.KB;
+  x.K8 = b.K8; x.Z = b.Z; x.N8 = (int)((b.N + 7) & ~(int64_t)7);
   x.M = b.M; x.N = b.N; x.rowA = b.rowA; x.rowB = b.rowB; x.part = b.part;
   return x;
 }
@@ -172,6 +179,18 @@ __device__ __forceinline__ int steps_of(const PParams &P, int t, int rs, int KB)
 template <bool CRT>
 __device__ __forceinline__ int chunk_of(const PParams &P, int t) {
   return CRT ? (int)P.crt_chunk_kb[t] : P.chunk_kb;
+}
+// K-packed batches: the pairs of the block of diagonals t..t+rs-1 are one
+// contiguous contraction over A columns plo K8 .. (phi + 1) K8 (the B columns move
+// with them; overhangs read zeros), in 64-wide k-blocks
+__device__ __forceinline__ int kp_steps(const PParams &P, const Item &x, int t) {
+  const int n = phi(P, t, x.rs) - plo(P, t) + 1;
+  return n > 0 ? (n * x.K8 + BK - 1) / BK : 0;
+}
+template <bool STACK, bool CRT>
+__device__ __forceinline__ int item_steps(const PParams &P, const Item &x, int t) {
+  if constexpr (STACK) return kp_steps(P, x, t);
+  else return steps_of<CRT>(P, t, x.rs, x.KB);
 }
 
 // STACK: B slices side by side (batches of small products); otherwise one
@@ -224,10 +243,8 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
     *abort = 0;
     counters[0] = counters[1] = 0;
     fence_barrier_init();
-    for (int i = 0; i < NBOX; ++i) {
-      prefetch_map(&maps.a[i]);
-      prefetch_map(&maps.b[i]);
-    }
+    for (int i = 0; i < NBOX; ++i) prefetch_map(&maps.a[i]);
+    for (int i = 0; i < NBOXB; ++i) prefetch_map(&maps.b[i]);
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -255,21 +272,50 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         Item x = decode_item(P, u);
         if constexpr (!STACK) x.rs = 1;
         const int ia = box_index(min((int64_t)BM, x.M - (int64_t)x.tm * BM));
-        const int ib = box_index(min((int64_t)BN, x.rs * x.N - (int64_t)x.tn * BN));
+        // stacked batches: one box of N8 rows per column block; otherwise one box
+        const int brows = (STACK && x.rs > 1) ? x.N8
+                                              : (int)min((int64_t)BN, x.rs * x.N - (int64_t)x.tn * BN);
+        const int ib = box_index_b(brows);
+        const int nbox = STACK ? x.rs : 1;
         // the boxes of maps.a are at most BM rows and of maps.b at most BN rows
-        const uint32_t bytes = (uint32_t)(min(box_rows(ia), BM) + min(box_rows(ib), BN)) * BK * 2;
+        const uint32_t bytes =
+            (uint32_t)(min(box_rows(ia), BM) + nbox * min(box_rows_b(ib), BN)) * BK * 2;
         for (int t = x.t0; t <= x.t1 && !*abort; t += x.rs) {
-          for (int p = pair_lo<CRT>(P, t); p <= pair_hi<CRT>(P, t, x.rs) && !*abort; ++p) {
-            const int q = CRT ? t : t - p;        // first of the rs B slices
-            const int ra = (int)(x.rowA + (int64_t)p * x.M + (int64_t)x.tm * BM);
-            const int rb = (int)(x.rowB + (int64_t)(q + x.rs - 1) * x.N + (int64_t)x.tn * BN);
-            for (int kb = 0; kb < x.KB; ++kb, ++it) {
+          if constexpr (STACK) {
+            // A columns plo K8 + 64 kb; column block jb (diagonal t + jb) reads B at
+            // (Z + S_B - 1 - t - jb) K8 further on: slice q = t + jb - p meets slice p
+            const int64_t k0 = (int64_t)plo(P, t) * x.K8;
+            const int64_t xb = k0 + (int64_t)(x.Z + P.S_B - 1 - t) * x.K8;
+            const int ra = (int)(x.rowA + (int64_t)x.tm * BM);
+            const int rb = (int)(x.rowB + (int64_t)x.tn * BN);
+            const int nst = kp_steps(P, x, t);
+            for (int kb = 0; kb < nst; ++kb, ++it) {
               const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
               if (!mbar_wait(&empty[s], ph ^ 1, P.status, abort)) break;
               mbar_arrive_expect_tx(&full[s], bytes);
-              tma_load_2d(smem_u32(sA + s * STAGE_A), &maps.a[ia], kb * BK, ra, smem_u32(&full[s]));
-              tma_load_2d(smem_u32(sB + s * STAGE_B), &maps.b[ib], kb * BK, rb, smem_u32(&full[s]));
+              tma_load_2d(smem_u32(sA + s * STAGE_A), &maps.a[ia], (int)(k0 + kb * BK), ra,
+                          smem_u32(&full[s]));
+              for (int jb = 0; jb < x.rs; ++jb)
+                tma_load_2d(smem_u32(sB + s * STAGE_B + (uint32_t)(jb * x.N8) * (BK * 2)),
+                            &maps.b[ib], (int)(xb - (int64_t)jb * x.K8 + kb * BK), rb,
+                            smem_u32(&full[s]));
               counters[0] = (int)it + 1;
+            }
+          } else {
+            for (int p = pair_lo<CRT>(P, t); p <= pair_hi<CRT>(P, t, x.rs) && !*abort; ++p) {
+              const int q = CRT ? t : t - p;        // first of the rs B slices
+              const int ra = (int)(x.rowA + (int64_t)p * x.M + (int64_t)x.tm * BM);
+              const int rb = (int)(x.rowB + (int64_t)(q + x.rs - 1) * x.N + (int64_t)x.tn * BN);
+              for (int kb = 0; kb < x.KB; ++kb, ++it) {
+                const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1, P.status, abort)) break;
+                mbar_arrive_expect_tx(&full[s], bytes);
+                tma_load_2d(smem_u32(sA + s * STAGE_A), &maps.a[ia], kb * BK, ra,
+                            smem_u32(&full[s]));
+                tma_load_2d(smem_u32(sB + s * STAGE_B), &maps.b[ib], kb * BK, rb,
+                            smem_u32(&full[s]));
+                counters[0] = (int)it + 1;
+              }
             }
           }
         }
@@ -287,10 +333,11 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         Item x = decode_item(P, u);
         if constexpr (!STACK) x.rs = 1;
         // N of the MMA: the tile's valid columns rounded up to 16
-        const int ncols = (int)min((int64_t)BN, x.rs * x.N - (int64_t)x.tn * BN);
+        const int ncols = (STACK && x.rs > 1) ? x.rs * x.N8
+                                              : (int)min((int64_t)BN, x.rs * x.N - (int64_t)x.tn * BN);
         const uint32_t idesc = idesc_bf16(BM, (ncols + 15) & ~15);
         for (int t = x.t0; t <= x.t1 && !*abort; t += x.rs) {
-          const int tot = steps_of<CRT>(P, t, x.rs, x.KB);
+          const int tot = item_steps<STACK, CRT>(P, x, t);
           const int ck = chunk_of<CRT>(P, t);
           for (int j = 0; j < tot && !*abort; ++ch) {
             const int nk = min(ck, tot - j);
@@ -346,7 +393,7 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
 #pragma unroll
           for (int i = 0; i < COLS; ++i) acc[i] = 0;
           const int ck = chunk_of<CRT>(P, t);
-          const int nch = (steps_of<CRT>(P, t, x.rs, x.KB) + ck - 1) / ck;
+          const int nch = (item_steps<STACK, CRT>(P, x, t) + ck - 1) / ck;
           int since = 0;                          // drains since the last reduction
           for (int c = 0; c < nch; ++c, ++ch) {
             const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
@@ -385,14 +432,17 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             // planes are column-major: lanes (consecutive rows) store consecutive words
             const uint32_t bias = (uint32_t)since * MAGIC_BITS;
             if constexpr (STACK) {
+              // column block j (diagonal t + j) is N8 columns wide when stacked
               const int nd = min(x.rs, x.t1 - t + 1);     // diagonals of this block to keep
-              int j = (int)(c0 / x.N);
-              int64_t col = c0 - (int64_t)j * x.N;
+              const int64_t nw = x.rs > 1 ? x.N8 : x.N;
+              int j = (int)(c0 / nw);
+              int64_t col = c0 - (int64_t)j * nw;
               int32_t *base = static_cast<int32_t *>(P.partials) + x.part + r;
 #pragma unroll
               for (int i = 0; i < COLS; ++i) {
-                if (j < nd) base[((int64_t)(t + j) * x.N + col) * x.M] = (int32_t)(acc[i] - bias);
-                if (++col == x.N) {
+                if (j < nd && col < x.N)
+                  base[((int64_t)(t + j) * x.N + col) * x.M] = (int32_t)(acc[i] - bias);
+                if (++col == nw) {
                   col = 0;
                   ++j;
                 }
@@ -606,10 +656,10 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
       std::swap(P.gorder[j], P.gorder[j - 1]);
   Maps maps;
   int rc = MW_OK;
-  for (int i = 0; i < NBOX && !rc; ++i) {
+  for (int i = 0; i < NBOX && !rc; ++i)
     rc = make_map_2d(&maps.a[i], a.pieceA, a.Kpitch, a.rowsA, std::min(box_rows(i), BM));
-    if (!rc) rc = make_map_2d(&maps.b[i], a.pieceB, a.Kpitch, a.rowsB, std::min(box_rows(i), bn));
-  }
+  for (int i = 0; i < NBOXB && !rc; ++i)
+    rc = make_map_2d(&maps.b[i], a.pieceB, a.KpitchB, a.rowsB, std::min(box_rows_b(i), bn));
   if (rc) return rc;
   static bool attr_set = false;
   if (!attr_set) {
@@ -698,7 +748,7 @@ int launch_ozaki(const OzakiArgs &a, cudaStream_t s, const std::function<void()>
   // tensor maps' extent, beyond which TMA fills zeros)
   L.rowsA = (int64_t)(a.crt ? a.D : a.S_A) * a.M;
   L.rowsB = (int64_t)(a.crt ? a.D : a.S_B) * a.N;
-  L.Kpitch = a.Kp;
+  L.Kpitch = L.KpitchB = a.Kp;
   L.S_A = a.S_A; L.S_B = a.S_B; L.D = a.D; L.w = a.w; L.chunk = a.chunk;
   L.group = a.crt ? 1 : sched_group(a.D, a.group, narrow);
   L.crt = a.crt;

@@ -27,6 +27,12 @@ struct BInfo {            // one problem, filled by the prologue
   // slice 0 and after slice S_B - 1, slice q at rowB + (q + rs - 1) N.
   // nd: diagonals per work item; G: work items per output tile.
   int32_t rs, nd, G;
+  // K-packed pieces (narrow batches): K8 = K rounded up to 8; a row of A holds its
+  // slices back to back (slice p at column p K8), a row of B (a column of B_i)
+  // its slices in descending order after Z K8 zero columns (slice q at column
+  // (Z + S_B - 1 - q) K8) and (rs - 1) K8 + 64 zeros, rounded up to K8, after
+  // them; Z = rs - 1 (the reads of stacked block j start j K8 lower).
+  int32_t K8, Z;
 };
 
 struct BHeader {          // written by the prologue

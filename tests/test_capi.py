@@ -213,7 +213,7 @@ def test_batch_workspace_grows_and_takes_hexa_doubles(mw):
     p16 = _ozaki_plan(mw, 16, S=112, D=116)
     assert mw._lib.mw_gemm_batched_workspace_size(ctypes.byref(p16), ctypes.byref(small),
                                                   ctypes.byref(size_s)) == mw.MW_OK
-    assert size_s.value >= 2 * 10 * 112 * 8 * 64 * 2      # 112 planes of the 8 x 8 problems
+    assert size_s.value >= 2 * 10 * 8 * 112 * 8 * 2       # 112 slices of every 8 x 8 problem
     p3 = _ozaki_plan(mw, 8)
     p3.m = 3
     assert mw._lib.mw_gemm_batched_workspace_size(ctypes.byref(p3), ctypes.byref(small),
