@@ -864,6 +864,15 @@ def run_table2(args, mw, torch, dist, rank, world, dev):
             "peak_source": f"{nsm} SMs x {IMAD_WIDE_PER_CLK_SM} int32 x int32 -> int64 "
                            "multiply-adds per clock x max SM clock (assumed rate)",
             "algorithmic": f"{pairs} digit pairs per entry x {K} x {count} per launch"}
+    # the same kernel against HBM: every word of both vectors read once, the words
+    # of every result written once
+    _, _, hbm_gbs, hbm_src = load_peaks()
+    bytes_alg = 2 * m * 8 * K * count + m * 8 * count
+    roof["hbm"] = {"achieved": bytes_alg / kern_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                   "frac": bytes_alg / kern_s / 1e9 / hbm_gbs,
+                   "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json)",
+                   "algorithmic": f"{bytes_alg} bytes per launch (every word of both vectors "
+                                  "read once, the results written once)"}
 
     e2e_steps = args.e2e_steps if args.e2e_steps >= 0 else max(3, args.steps // 4)
     e2e = None
