@@ -6,7 +6,7 @@ width run fastest on a given shape.  The tuner settles that by measurement:
 
 * candidates: the residue form (m = 2 and 4) and the slice form with pieces of
   w = 6, 7 and 8 bits, each with the drain chunks its width allows (a sum of
-  ``chunk`` products of w-bit balanced digits must stay below 2^22);
+  ``chunk`` products of w-bit balanced digits must stay below 2^24);
 * every candidate is checked against the bound before it runs (``admissible``:
   the truncation of either operand and the dropped diagonals within their
   shares of 2K 2^(-52m), exact fp32 drains, a residue product P > 8 K
@@ -95,7 +95,7 @@ def admissible(p: mw_plan, K: int) -> bool:
     if p.D < p.S_A + p.S_B - 1 and w * p.D < (52 * m + p.range_A + p.range_B
                                              + math.log2(min(p.S_A, p.S_B)) + 6 - lgK - 1e-9):
         return False
-    return p.chunk >= 64 and p.chunk % 64 == 0 and p.chunk * 2 ** (2 * w - 2) <= 2 ** 22
+    return p.chunk >= 64 and p.chunk % 64 == 0 and p.chunk * 2 ** (2 * w - 2) <= 2 ** 24
 
 
 def candidates(m: int, M: int, N: int, K: int, range_A: int, range_B: int) -> list[Choice]:
@@ -103,7 +103,7 @@ def candidates(m: int, M: int, N: int, K: int, range_A: int, range_B: int) -> li
     if m in (2, 4):
         out.append(Choice("crt"))
     for w in (8, 7, 6):
-        top = (1 << 22) >> (2 * w - 2)                        # largest exact chunk
+        top = (1 << 24) >> (2 * w - 2)                        # largest exact chunk
         for chunk in sorted({top, max(64, top // 4)}, reverse=True):
             out.append(Choice("ozaki", w, chunk))
     return [c for c in out

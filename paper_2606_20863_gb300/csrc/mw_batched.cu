@@ -636,7 +636,7 @@ int check_batch(const mw_plan *p, const mw_batch *b) {
     return fail(MW_EINVAL, "batches take m = 2, 4, 8 or 16");
   if (b->count < 1 || b->sum_M < 1 || b->sum_N < 1 || b->max_K < 1)
     return fail(MW_EINVAL, "empty batch");
-  if (p->w < 2 || p->w > 8 || (int64_t)p->chunk << (2 * p->w - 2) > (1 << 22) || p->chunk % 64)
+  if (p->w < 2 || p->w > 8 || (int64_t)p->chunk << (2 * p->w - 2) > (1 << 24) || p->chunk % 64)
     return fail(MW_EINVAL, "bad w/chunk");
   if (p->S_A < 1 || p->S_B < 1 || p->D < 1 || p->group < 1) return fail(MW_EINVAL, "bad plan");
   const int S_min = std::min(p->S_A, p->S_B);

@@ -262,7 +262,7 @@ int mw_plan_gemm(int m, int mode, int64_t M, int64_t N, int64_t K, int range_A, 
   if (mode == MW_OZAKI) {
     if (want_w != 0 && (want_w < 2 || want_w > 8)) return fail(MW_EINVAL, "Ozaki w must be 2..8");
     finish(want_w ? want_w : 8);
-    p.chunk = 1 << (24 - 2 * p.w);  // chunk 2^(2w-2) <= 2^22
+    p.chunk = 1 << (26 - 2 * p.w);  // chunk 2^(2w-2) <= 2^24
     const int S_min = p.S_A < p.S_B ? p.S_A : p.S_B;
     p.group = group_size(S_min, K, p.w);
     if (p.group < 1) return fail(MW_EUNSUPPORTED, "K = %lld too long for 64-bit partial sums", (long long)K);

@@ -39,9 +39,10 @@ namespace {
 // Pairwise coprime odd moduli, at most 513 (balanced residues within
 // bfloat16's exact integers; odd, so that no sum lies halfway between two
 // multiples of a modulus and the rounding of z / p below needs no correction).
-// An fp32 sum of `chunk` products of residues stays exact below 2^22 when
-// chunk floor(p/2)^2 <= 2^22: 1024 products for p <= 129, 512 for p <= 181, 256
-// for p <= 257, 128 for p <= 363, 64 for p <= 513.  A modulus costs the tensor
+// An fp32 sum of `chunk` products of residues stays exact below 2^24 when
+// chunk floor(p/2)^2 <= 2^24: 4096 products for p <= 129, 2048 for p <= 181,
+// 1024 for p <= 257, 512 for p <= 363, 256 for p <= 513.  (The table below was
+// ordered when a drain came every quarter of that.)  A modulus costs the tensor
 // cores one product of residue matrices, k-blocks of 64 at about 625 cycles a
 // 128 x 256 tile, plus one drain of its fp32 accumulators every chunk, about 775
 // cycles (both measured on GB300).  The table: greedy by log2(p) / cost at
@@ -707,9 +708,9 @@ int crt_table_size() { return kNumModuli; }
 int crt_modulus(int i) { return (i >= 0 && i < kNumModuli) ? kModuli[i] : 0; }
 int crt_chunk(int i) {
   const int64_t h = crt_modulus(i) / 2;
-  for (int c = 1024; c > 64; c /= 2)
-    if (c * h * h <= (1 << 22)) return c;
-  return 64;
+  for (int c = 4096; c > 256; c /= 2)
+    if (c * h * h <= (1 << 24)) return c;
+  return 256;
 }
 double crt_bits(int n) {
   double b = 0;

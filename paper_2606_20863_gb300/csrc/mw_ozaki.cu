@@ -5,12 +5,14 @@
 // product into matrix products of pieces, "in particular tensor cores", the
 // Ozaki scheme of Section 1.  Pieces are balanced integers |d| <= 2^(w-1),
 // w <= 8, stored in bfloat16 (exact); a product of two pieces is at most
-// 2^(2w-2) and a sum of `chunk` of them is at most 2^22, so the fp32
+// 2^(2w-2) and a sum of `chunk` of them is at most 2^24, so the fp32
 // accumulators of the tensor core hold exact integers.  After every chunk the
-// accumulator is drained from tensor memory into integer registers:
-//   v + 1.5*2^23 (one fp32 add, exact for |v| <= 2^22) has bit pattern
-//   0x4B400000 + v, which is added as an unsigned 32-bit value; the constant
-//   times the number of chunks is subtracted at the end.
+// accumulator is drained from tensor memory into integer registers (drain_parts):
+//   v = 4096 q + lo with q = round(v / 4096) by one fma against 1.5*2^23 and
+//   lo = v - 4096 q exact (|lo| <= 2048); the bit patterns 0x4B400000 + q and
+//   0x4B400000 + lo are joined as 4096 (0x4B400000 + q) + (0x4B400000 + lo) and
+//   added as an unsigned value; the constant times the number of chunks is
+//   subtracted at the end.
 // Narrow mode (every s_t fits in int32): each diagonal sum is accumulated mod
 // 2^32 and stored as an int32 plane.  Wide mode: a group of diagonals t0..t1
 // is accumulated by Horner's rule mod 2^64, V = sum_t s_t 2^(w (t1 - t)), and
@@ -54,6 +56,18 @@ namespace {
 constexpr int BM = 128, BK = 64;
 constexpr uint32_t STAGE_A = BM * BK * 2;
 constexpr uint32_t MAGIC_BITS = 0x4B400000u;  // bit pattern of 1.5 * 2^23
+constexpr uint64_t DRAIN_BIAS = (uint64_t)MAGIC_BITS * 4097u;   // what a drained value carries
+
+// An integer |v| <= 2^24 held exactly in fp32 as 4096 q + lo: h = 1.5 2^23 +
+// round(v / 4096) (one rounding: v / 4096 is exact), lo = v - 4096 q exact; hb and
+// lb are the bit patterns of 1.5 2^23 + q and 1.5 2^23 + lo, so that
+// 4096 hb + lb = v + DRAIN_BIAS.
+__device__ __forceinline__ void drain_parts(uint32_t vb, uint32_t &hb, uint32_t &lb) {
+  const float v = __uint_as_float(vb);
+  const float h = fmaf(v, 1.0f / 4096.0f, 12582912.0f);
+  hb = __float_as_uint(h);
+  lb = __float_as_uint(fmaf(h - 12582912.0f, -4096.0f, v) + 12582912.0f);
+}
 // Kernel shapes.  Tile 128 x BN (BN = 128 or 256); NBUF accumulators of BN fp32
 // columns in tensor memory (all 512 columns: with 128-column tiles four, so that
 // the MMAs of short products run up to three drains ahead).  Two drain modes.  Narrow: every diagonal sum s_t
@@ -77,8 +91,9 @@ template <int BN_, bool NARROW> struct Shape {
 constexpr int MAX_GROUPS = 128;
 static_assert(MAX_GROUPS >= kCrtMaxModuli, "a work item per modulus");
 // Residue form: drains between two reductions of the int32 accumulators mod p.
-// A drain adds at most 2^22 in magnitude, so 511 of them stay below 2^31.
-constexpr int kCrtReduceEvery = 511;
+// A drain adds at most 2^24 in magnitude, so 127 of them (and a residue) stay
+// below 2^31 - 2^24.
+constexpr int kCrtReduceEvery = 127;
 constexpr int RING = 4;   // work items the producer may run ahead
 
 struct PParams {
@@ -413,14 +428,17 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
                 if (lane == 0) mbar_arrive(&acce[b]);
               }
 #pragma unroll
-              for (int i = 0; i < 32; ++i)
-                acc[32 * h + i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
+              for (int i = 0; i < 32; ++i) {
+                uint32_t hb, lb;
+                drain_parts(v[i], hb, lb);
+                acc[32 * h + i] += (hb << 12) + lb;
+              }
             }
             ++since;
             if constexpr (CRT) {
               if (since == kCrtReduceEvery && c + 1 < nch) {
                 const int pm = P.crt_p[t];
-                const uint32_t bs = (uint32_t)since * MAGIC_BITS;
+                const uint32_t bs = (uint32_t)since * (uint32_t)DRAIN_BIAS;
 #pragma unroll
                 for (int i = 0; i < COLS; ++i) acc[i] = (uint32_t)((int32_t)(acc[i] - bs) % pm);
                 since = 0;
@@ -430,7 +448,7 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
           if (!ok) break;
           if (r < x.M) {
             // planes are column-major: lanes (consecutive rows) store consecutive words
-            const uint32_t bias = (uint32_t)since * MAGIC_BITS;
+            const uint32_t bias = (uint32_t)since * (uint32_t)DRAIN_BIAS;
             if constexpr (STACK) {
               // column block j (diagonal t + j) is N8 columns wide when stacked
               const int nd = min(x.rs, x.t1 - t + 1);     // diagonals of this block to keep
@@ -449,7 +467,7 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
               }
             } else if constexpr (CRT) {
               // the balanced residue of each sum S, as bfloat16 (|r| <= 256): with
-              // u = S + B_t in [0, 2^32) (|S| < 2^31 - 2^22 + p), u mod p by the
+              // u = S + B_t in [0, 2^32) (|S| < 2^31 - 2^24 + p), u mod p by the
               // reciprocal (the quotient estimate is exact or one short), then
               // r = u mod p - (p - 1) / 2 as a float from its bits.  The row's
               // COLS residues are contiguous: 16-byte stores of eight
@@ -499,7 +517,7 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             bias <<= P.w;
           }
           const int nch = (nsteps(P, t, 1, x.KB) + P.chunk_kb - 1) / P.chunk_kb;
-          bias += (uint64_t)nch * MAGIC_BITS;
+          bias += (uint64_t)nch * DRAIN_BIAS;
           for (int c = 0; c < nch; ++c, ++ch) {
             const uint32_t b = ch % NBUF, bph = (ch / NBUF) & 1;
             if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], bph, P.status, abort))) {
@@ -511,16 +529,22 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             tc_ld32(tbase + b * BN, v);
             tc_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              acc[i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
+            for (int i = 0; i < 32; ++i) {
+              uint32_t hb, lb;
+              drain_parts(v[i], hb, lb);
+              acc[i] += ((uint64_t)hb << 12) + lb;
+            }
             tc_ld32(tbase + b * BN + 32, v);
             tc_wait_ld();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[b]);
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              acc[32 + i] += __float_as_uint(__uint_as_float(v[i]) + 12582912.0f);
+            for (int i = 0; i < 32; ++i) {
+              uint32_t hb, lb;
+              drain_parts(v[i], hb, lb);
+              acc[32 + i] += ((uint64_t)hb << 12) + lb;
+            }
           }
         }
         if (!ok) break;
@@ -605,8 +629,8 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   } else {
     if (a.chunk < BK || a.chunk % BK)
       return fail(MW_EINVAL, "chunk must be a positive multiple of 64");
-    if (a.w < 2 || a.w > 8 || (int64_t)a.chunk << (2 * a.w - 2) > (1 << 22))
-      return fail(MW_EINVAL, "chunk * 2^(2w-2) must not exceed 2^22 (w=%d chunk=%d)", a.w,
+    if (a.w < 2 || a.w > 8 || (int64_t)a.chunk << (2 * a.w - 2) > (1 << 24))
+      return fail(MW_EINVAL, "chunk * 2^(2w-2) must not exceed 2^24 (w=%d chunk=%d)", a.w,
                   a.chunk);
   }
   if (a.rowsA > 0x7fffffffLL || a.rowsB > 0x7fffffffLL)

@@ -29,7 +29,7 @@ def test_inadmissible_plans_are_refused(mw, tuner):
     at, _ = tuner
     p = mw.mw_plan_gemm(4, "ozaki", 64, 64, 1024, 10, 10)
     assert at.admissible(p, 1024)
-    p.chunk = 2 * ((1 << 22) >> (2 * p.w - 2))          # fp32 sums no longer exact
+    p.chunk = 2 * ((1 << 24) >> (2 * p.w - 2))          # fp32 sums no longer exact
     assert not at.admissible(p, 1024)
     p = mw.mw_plan_gemm(4, "ozaki", 64, 64, 1024, 10, 10)
     p.S_A -= 2                                          # truncation beyond its share

@@ -55,7 +55,7 @@ def test_plan_constraints(mw, m, mode):
             if p.D < p.S_A + p.S_B - 1:
                 assert p.w * p.D >= 52 * m + ra + rb + math.log2(S_min) + 6 - lgK - 1e-9
             if mode == "ozaki":
-                assert p.w == 8 and p.chunk * 2 ** (2 * p.w - 2) <= 2 ** 22
+                assert p.w == 8 and p.chunk * 2 ** (2 * p.w - 2) <= 2 ** 24
                 max_s = S_min * K * 2 ** (2 * p.w - 2)
                 assert max_s * 2 ** (p.w * (p.group - 1)) * (1 + 2 ** (1 - p.w)) < 2 ** 63
             else:
