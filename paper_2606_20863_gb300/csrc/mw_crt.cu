@@ -41,20 +41,20 @@ namespace {
 // multiples of a modulus and the rounding of z / p below needs no correction).
 // An fp32 sum of `chunk` products of residues stays exact below 2^24 when
 // chunk floor(p/2)^2 <= 2^24: 4096 products for p <= 129, 2048 for p <= 181,
-// 1024 for p <= 257, 512 for p <= 363, 256 for p <= 513.  (The table below was
-// ordered when a drain came every quarter of that.)  A modulus costs the tensor
-// cores one product of residue matrices, k-blocks of 64 at about 625 cycles a
-// 128 x 256 tile, plus one drain of its fp32 accumulators every chunk, about 775
-// cycles (both measured on GB300).  The table: greedy by log2(p) / cost at
+// 1024 for p <= 257, 512 for p <= 363, 256 for p <= 513.  A modulus costs the
+// tensor cores one product of residue matrices, 64-wide k-blocks at about 625
+// cycles a 128 x 256 tile, plus per tile the store of its residues, about 6,900
+// cycles, and one drain of the fp32 accumulators every chunk, about 1,200 cycles
+// (fitted to measurements on GB300).  The table: greedy by log2(p) / cost at
 // K = 4096, each step the best odd number coprime to every one taken; a
 // product uses the first n moduli.
 constexpr uint16_t kModuli[] = {
-    129, 181, 127, 179, 125, 173, 121, 169, 119, 167, 163, 113, 157, 109, 151, 107,
-    149, 103, 101, 139, 137, 97,  257, 131, 251, 241, 239, 89,  233, 229, 227, 223,
-    83,  211, 79,  199, 197, 193, 191, 73,  71,  67,  61,  59,  53,  361, 359, 353,
-    349, 347, 337, 331, 47,  317, 313, 311, 307, 293, 283, 281, 277, 271, 269, 41,
-    263, 37,  31,  29,  23,  509, 503, 499, 491, 487, 479, 467, 463, 461, 457, 449,
-    443, 439, 433, 431, 421, 419, 409, 401, 397, 389, 383, 379, 373, 367};
+    257, 255, 253, 251, 247, 241, 239, 181, 233, 179, 229, 227, 223, 173, 359, 217,
+    353, 167, 349, 347, 211, 163, 337, 331, 157, 199, 197, 317, 193, 151, 313, 191,
+    311, 149, 307, 127, 293, 139, 283, 137, 281, 277, 271, 269, 131, 263, 113, 109,
+    107, 103, 101, 97, 509, 503, 499, 491, 487, 479, 89, 467, 463, 461, 457, 449,
+    443, 439, 83, 433, 431, 421, 419, 409, 79, 401, 397, 389, 383, 379, 373, 367,
+    73, 71, 67, 61, 59, 53, 47, 43, 41, 37, 29};
 constexpr int kNumModuli = sizeof(kModuli) / sizeof(kModuli[0]);
 static_assert(kNumModuli <= kCrtMaxModuli, "moduli table too long");
 constexpr bool all_odd() {
