@@ -97,7 +97,7 @@ enum { MW_DIGITS_BF16 = 0, MW_DIGITS_F64 = 1 };
  *   D      diagonals kept: pairs (p, q) with p < S_A, q < S_B, p + q < D
  *   group  diagonals fused into one 64-bit partial sum (MW_OZAKI)
  *   chunk  products of pieces accumulated in fp32 before a drain (MW_OZAKI;
- *          multiple of 64)
+ *          multiple of 64, chunk 2^(2w-2) <= 2^24)
  *   range_A, range_B  exponent spread (bits) the plan assumes for the rows of
  *          op(A) / columns of op(B); larger spreads raise MW_WRANGE.
  * MW_CRT reads the fields so: w = 1, S_A / S_B = fixed-point bits L_A / L_B of
