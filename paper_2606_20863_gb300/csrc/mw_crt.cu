@@ -172,22 +172,6 @@ struct SplitEntry {      // one thread's entry of a tile: position and words
   double x[MW];
 };
 
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int c0, int c1, int c2,
-                                             uint32_t src) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-          (uint64_t)map),
-      "r"(c0), "r"(c1), "r"(c2), "r"(src)
-      : "memory");
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-
 template <int MW, int NL, bool TRANS>
 __global__ void __launch_bounds__(kResTile, 4)
     residues_mma_kernel(const __grid_constant__ CUtensorMap omap, const double *__restrict__ X,

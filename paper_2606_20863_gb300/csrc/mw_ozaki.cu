@@ -42,6 +42,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "mw_device.cuh"
 #include "mw_tc.cuh"
@@ -87,6 +88,17 @@ template <int BN_, bool NARROW> struct Shape {
   static_assert(NARROW || BN == 128, "wide drain only with 128-column tiles");
   static_assert(TMEM_COLS <= 512, "tensor memory holds 512 columns");
 };
+// Residue form, 128 x 256 tiles: a 4 KB box (32 rows x 64 residues, 128-byte
+// swizzle) per drain warp, from which a tensor store writes the tile's residues.
+template <int BN, bool CRT>
+__host__ __device__ constexpr uint32_t out_stage_bytes() {
+  return (CRT && BN == 256) ? (uint32_t)Shape<256, true>::WARPS * 4096u : 0u;
+}
+template <int BN, bool NARROW, bool CRT>
+__host__ __device__ constexpr size_t kernel_smem() {
+  return Shape<BN, NARROW>::SMEM + out_stage_bytes<BN, CRT>();
+}
+static_assert(kernel_smem<256, true, true>() <= 232448, "shared memory of one CTA");
 
 constexpr int MAX_GROUPS = 128;
 static_assert(MAX_GROUPS >= kCrtMaxModuli, "a work item per modulus");
@@ -119,10 +131,11 @@ struct PParams {
 // Tensor maps over the two piece arrays with boxes of 16, 32, ..., 256 rows (A)
 // and 8, 16, ..., 256 rows (B): a tile loads only the rows its problem has,
 // rounded up (rows past them would only feed outputs that are never stored).
-// 6 KB of kernel parameters.
+// The residue form with 128 x 256 tiles also stores through a map (`out`: the
+// residue planes, boxes of 64 columns x 32 rows).  6 KB of kernel parameters.
 constexpr int NBOX = 16, NBOXB = 32;
 struct Maps {
-  CUtensorMap a[NBOX], b[NBOXB];
+  CUtensorMap a[NBOX], b[NBOXB], out;
 };
 __host__ __device__ constexpr int box_rows(int i) { return 16 * (i + 1); }
 __device__ __forceinline__ int box_index(int64_t rows) {
@@ -222,12 +235,14 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
   constexpr uint32_t STAGE_B = SH::STAGE_B;
   constexpr int NUM_DRAIN_WARPS = SH::WARPS;
   constexpr int NBUF = SH::NBUF;
+  constexpr bool OUT_TMA = out_stage_bytes<BN, CRT>() > 0;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;
   uint8_t *sB = smem + STAGES * STAGE_A;
-  uint64_t *full = (uint64_t *)(smem + STAGES * (STAGE_A + STAGE_B));
+  uint8_t *sOut = smem + STAGES * (STAGE_A + STAGE_B);   // 1024-byte aligned
+  uint64_t *full = (uint64_t *)(sOut + out_stage_bytes<BN, CRT>());
   uint64_t *empty = full + STAGES;
   uint64_t *accf = empty + STAGES;
   uint64_t *acce = accf + NBUF;
@@ -260,6 +275,7 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
     fence_barrier_init();
     for (int i = 0; i < NBOX; ++i) prefetch_map(&maps.a[i]);
     for (int i = 0; i < NBOXB; ++i) prefetch_map(&maps.b[i]);
+    if constexpr (OUT_TMA) prefetch_map(&maps.out);
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -446,7 +462,43 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             }
           }
           if (!ok) break;
-          if (r < x.M) {
+          if constexpr (OUT_TMA) {
+            // the balanced residues (see below) in pairs, column 2e in the low half;
+            // the warp writes them box by box into its staging box, one tensor store
+            // each (rows past M and columns past N are not written)
+            const uint32_t pm = P.crt_p[t], m32 = P.crt_m32[t];
+            const uint32_t offb = P.crt_off[t] - (uint32_t)since * (uint32_t)DRAIN_BIAS;
+            const float cf = P.crt_cf[t];
+            uint32_t pk[COLS / 2];
+#pragma unroll
+            for (int e = 0; e < COLS / 2; ++e) {
+              uint32_t h2[2];
+#pragma unroll
+              for (int o = 0; o < 2; ++o) {
+                const uint32_t u = acc[2 * e + o] + offb;
+                const uint32_t r0 = u - __umulhi(u, m32) * pm;
+                const uint32_t rr = min(r0, r0 - pm);
+                h2[o] = __float_as_uint(__uint_as_float(0x4B400000u + rr) - cf);
+              }
+              asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(pk[e]) : "r"(h2[0]), "r"(h2[1]));
+            }
+            uint8_t *box = sOut + (warp - 2) * 4096;
+            const int y = (int)((int64_t)x.tm * BM + quarter * 32);
+#pragma unroll
+            for (int hf = 0; hf < COLS / 64; ++hf) {
+              if (lane == 0) bulk_wait_read();     // the box's previous store has read it
+              __syncwarp();
+#pragma unroll
+              for (int g = 0; g < 8; ++g)
+                *reinterpret_cast<uint4 *>(box + lane * 128 + ((g ^ (lane & 7)) << 4)) =
+                    make_uint4(pk[32 * hf + 4 * g], pk[32 * hf + 4 * g + 1],
+                               pk[32 * hf + 4 * g + 2], pk[32 * hf + 4 * g + 3]);
+              fence_proxy_async_smem();
+              __syncwarp();
+              if (lane == 0 && y < x.M && c0 + 64 * hf < x.N)
+                tma_store_3d(&maps.out, (int)(c0 + 64 * hf), y, t, smem_u32(box));
+            }
+          } else if (r < x.M) {
             // planes are column-major: lanes (consecutive rows) store consecutive words
             const uint32_t bias = (uint32_t)since * (uint32_t)DRAIN_BIAS;
             if constexpr (STACK) {
@@ -557,6 +609,8 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
         }
       }
     }
+    if constexpr (OUT_TMA)
+      if (lane == 0) bulk_wait_all();             // the residue stores are complete
   }
 
   __syncthreads();
@@ -684,6 +738,16 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
     rc = make_map_2d(&maps.a[i], a.pieceA, a.Kpitch, a.rowsA, std::min(box_rows(i), BM));
   for (int i = 0; i < NBOXB && !rc; ++i)
     rc = make_map_2d(&maps.b[i], a.pieceB, a.KpitchB, a.rowsB, std::min(box_rows_b(i), bn));
+  if (!rc && a.crt && bn == 256) {
+    // residue planes [t][i][j], rows of crt_ld(N) elements
+    const uint64_t ld = (uint64_t)crt_ld(a.N);
+    const uint64_t dims[3] = {(uint64_t)a.N, (uint64_t)a.M, (uint64_t)a.D};
+    const uint64_t strides[2] = {ld * 2, ld * 2 * (uint64_t)a.M};
+    const uint32_t box[3] = {64, 32, 1};
+    rc = make_map_bf16(&maps.out, a.partials, 3, dims, strides, box);
+  } else {
+    memset(&maps.out, 0, sizeof maps.out);
+  }
   if (rc) return rc;
   static bool attr_set = false;
   if (!attr_set) {
@@ -705,7 +769,7 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(ozaki_kernel<256, true, false, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)Shape<256, true>::SMEM);
+                               (int)kernel_smem<256, true, true>());
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(ozaki_kernel<128, true, false, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -724,7 +788,8 @@ int launch_product(const ProductLaunch &a, cudaStream_t s) {
   using S128 = Shape<128, true>;
   using W128 = Shape<128, false>;
   if (a.crt && bn == 256)
-    ozaki_kernel<256, true, false, true><<<grid, S256::THREADS, S256::SMEM, s>>>(maps, P);
+    ozaki_kernel<256, true, false, true><<<grid, S256::THREADS, kernel_smem<256, true, true>(), s>>>(
+        maps, P);
   else if (a.crt)
     ozaki_kernel<128, true, false, true><<<grid, S128::THREADS, S128::SMEM, s>>>(maps, P);
   else if (a.narrow && bn == 256 && a.info)
