@@ -209,18 +209,31 @@ __global__ void __launch_bounds__(kResTile, 4)
   const uint32_t tmem = *holder;
   const uint32_t idesc = idesc_f16(128, npad);
   const int64_t ktiles = TRANS ? (dld + 31) / 32 : (dld + 127) / 128;
-  const int64_t ntiles = (TRANS ? (R + 3) / 4 : R) * ktiles;
+  const int64_t rtiles = TRANS ? (R + 3) / 4 : R;
+  // tile u = a * inner + b: (rt, kt) = (a, b) for rows (k contiguous), (b, a) for
+  // the operand stored K x R, so that the CTAs running together read neighbouring
+  // r of the same k rows (whole sectors); each CTA steps u by the grid size
+  const int64_t inner = TRANS ? rtiles : ktiles, outer = TRANS ? ktiles : rtiles;
+  const int64_t gq = gridDim.x / inner, gr = gridDim.x - gq * inner;
   // this thread's slot in a row of the shared residue tile: the box is 128 k of
   // one row, or 4 rows x 32 k
   const uint32_t slot = TRANS ? (uint32_t)((tid & 3) * 32 + (tid >> 2)) : (uint32_t)tid;
   uint16_t *mine = reinterpret_cast<uint16_t *>(stage) + slot;
   volatile int abort_flag = 0;
 
-  auto fetch = [&](int64_t tile, SplitEntry<MW> &e) {
+  auto step = [&](int64_t &a, int64_t &b) {
+    a += gq;
+    b += gr;
+    if (b >= inner) {
+      b -= inner;
+      ++a;
+    }
+  };
+  auto fetch = [&](int64_t ta, int64_t tb, SplitEntry<MW> &e) {
     e.valid = false;
     e.r = e.k = 0;
-    if (tile < ntiles) {
-      const int64_t rt = tile / ktiles, kt = tile - rt * ktiles;
+    if (ta < outer) {
+      const int64_t rt = TRANS ? tb : ta, kt = TRANS ? ta : tb;
       e.r = TRANS ? rt * 4 + (tid & 3) : rt;
       e.k = TRANS ? kt * 32 + (tid >> 2) : kt * 128 + tid;
       e.valid = e.r < R && e.k < dld;
@@ -234,9 +247,9 @@ __global__ void __launch_bounds__(kResTile, 4)
   SplitEntry<MW> ec, en;
   uint32_t ph = 0;
   bool ok = true;
-  int64_t cur = blockIdx.x;
-  fetch(cur, ec);
-  for (; cur < ntiles; cur += gridDim.x) {
+  int64_t ca = blockIdx.x / inner, cb = blockIdx.x - (blockIdx.x / inner) * inner;
+  fetch(ca, cb, ec);
+  for (; ca < outer; step(ca, cb)) {
     // digits of the entry into row tid of A
     {
       uint64_t T[NL];
@@ -271,7 +284,11 @@ __global__ void __launch_bounds__(kResTile, 4)
       for (int kk = 0; kk < 4; ++kk) tc_mma(tmem, ad + 2 * kk, bd + 2 * kk, idesc, kk ? 1u : 0u);
       tc_commit(&bar[0]);
     }
-    fetch(cur + gridDim.x, en);                    // the next tile's words load meanwhile
+    {
+      int64_t na = ca, nb = cb;
+      step(na, nb);
+      fetch(na, nb, en);                           // the next tile's words load meanwhile
+    }
     ok = __syncthreads_and(mbar_wait(&bar[0], ph, status, &abort_flag));
     if (!ok) break;
     ph ^= 1;
@@ -301,9 +318,8 @@ __global__ void __launch_bounds__(kResTile, 4)
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {                                // entries past R or dld are clipped
-      const int64_t rt = cur / ktiles, kt = cur - rt * ktiles;
-      if (TRANS) tma_store_3d(&omap, (int)(kt * 32), (int)(rt * 4), 0, smem_u32(stage));
-      else tma_store_3d(&omap, (int)(kt * 128), (int)rt, 0, smem_u32(stage));
+      if (TRANS) tma_store_3d(&omap, (int)(ca * 32), (int)(cb * 4), 0, smem_u32(stage));
+      else tma_store_3d(&omap, (int)(cb * 128), (int)ca, 0, smem_u32(stage));
     }
     ec = en;
   }
@@ -385,9 +401,9 @@ int launch_residues_nl(const SplitArgs &a, cudaStream_t s) {
 // Q'_t = sum_n b_tn 2^(8n) in balanced bytes (P < 2^(32 top - 2): no carry out of
 // byte 4 top - 1), so X' = sum_n z_n 2^(8n) with z_n = sum_t r_t b_tn, one MMA
 // per tile of 128 outputs (A: 128 x D residues, B: D x 4 NL bytes), |z_n| <= 96
-// 2^15 < 2^22.  A column of ones against a row of 1.5 2^23 adds that bias to
-// every z_n in the fp32 accumulator (all partial sums are integers below 2^24:
-// exact), so the accumulator's bits are 0x4B400000 + z_n.  Horner joins them into
+// 2^15 < 2^22.  The accumulators start at 1.5 2^23 (written into tensor memory
+// before each product), so every partial sum is an integer in [2^23, 2^24) (exact)
+// and the accumulator's bits are 0x4B400000 + z_n.  Horner joins them into
 // 32-bit limbs, k comes from the limbs top-2..top of X' (|X'| < D 2^8 P), and
 // X = X' + |k| (P or 2^(32 NL) - P) mod 2^(32 NL) is rounded greedily into m words.
 struct CrtFuse {
@@ -406,7 +422,7 @@ struct FuseShape {
 // Bytes of shared memory the reconstruction kernel uses for D moduli and NL limbs
 // (with the rounding's limb columns in shared memory unless LCOL).
 inline size_t fuse_smem(int D, int NL, bool lcol) {
-  const int D8 = (D + 7) & ~7, KM = (D8 + 1 + 15) & ~15, kc = (KM + 63) / 64;
+  const int D8 = (D + 7) & ~7, KM = (D8 + 15) & ~15, kc = (KM + 63) / 64;
   return 1024 + (size_t)256 * D8 + (size_t)kc * 16384 + (size_t)kc * 4 * NL * 128 +
          (lcol ? 0 : (size_t)(NL + 1) * 512) + 32;
 }
@@ -418,8 +434,8 @@ __global__ void __launch_bounds__(128, 2)
                     unsigned int *status, const __grid_constant__ CrtFuse F) {
   constexpr int NB = FuseShape<NL>::NB;
   constexpr uint32_t TCOLS = FuseShape<NL>::TCOLS;
-  const int D = F.D, D8 = (D + 7) & ~7, kb = D8;   // kb: the column of ones
-  const int KM = (kb + 1 + 15) & ~15, kc = (KM + 63) / 64;
+  const int D = F.D, D8 = (D + 7) & ~7;
+  const int KM = (D8 + 15) & ~15, kc = (KM + 63) / 64;
   extern __shared__ uint8_t smem_raw[];
   // residues of a tile (128 outputs of one row) as TMA leaves them (two halves of
   // 64, D8 rows of 128 B, swizzled), the MMA's A (128 rows, K-major) and B (NB
@@ -434,12 +450,11 @@ __global__ void __launch_bounds__(128, 2)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int idx = tid; idx < kc * 64 * NB; idx += 128) {
     const int t = idx / NB, n = idx - t * NB;
-    const uint16_t v = t < D ? small_int_bf16(F.qb[t][n]) : (t == kb ? (uint16_t)0x4B40 : 0);
+    const uint16_t v = t < D ? small_int_bf16(F.qb[t][n]) : (uint16_t)0;
     *reinterpret_cast<uint16_t *>(sB + (t >> 6) * (NB * 128) + sw128_offset(n, t & 63)) = v;
   }
   for (int t = D8; t < kc * 64; ++t)               // row tid of A past the residues
-    *reinterpret_cast<uint16_t *>(sA + (t >> 6) * 16384 + sw128_offset(tid, t & 63)) =
-        t == kb ? (uint16_t)0x3F80 : (uint16_t)0;
+    *reinterpret_cast<uint16_t *>(sA + (t >> 6) * 16384 + sw128_offset(tid, t & 63)) = 0;
   if (tid == 0) {
     for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
     fence_barrier_init();
@@ -450,6 +465,20 @@ __global__ void __launch_bounds__(128, 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *holder;
+  // the bias 1.5 2^23 into this warp's lanes of both accumulators
+  auto bias_fill = [&](int s) {
+    const uint32_t ta = tmem + s * NB + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int h = 0; h < (NB + 31) / 32; ++h) {
+      if (32 * h + 32 <= NB) tc_fill32(ta + 32 * h, 0x4B400000u);
+      else tc_fill16(ta + 32 * h, 0x4B400000u);
+    }
+  };
+  bias_fill(0);
+  bias_fill(1);
+  tc_wait_st();
+  tc_fence_before();
+  __syncthreads();
   const uint32_t idesc = idesc_bf16(128, NB);
   const int64_t jtiles = (N + 127) / 128, ntiles = jtiles * M;   // a tile: 128 j of one row i
   const uint32_t stage_bytes = 256u * D8;
@@ -498,6 +527,8 @@ __global__ void __launch_bounds__(128, 2)
         rc = acc >> 32;
       }
     }
+    bias_fill(s);                                  // for the accumulator's next product
+    tc_wait_st();
     tc_fence_before();
     const int64_t i = tile / jtiles, j = (tile - i * jtiles) * 128 + tid;
     uint32_t lcol[LCOL ? NL + 1 : 1];              // read by index: local memory
@@ -564,7 +595,7 @@ __global__ void __launch_bounds__(128, 2)
           const uint64_t ad = sw128_desc(smem_u32(sA + cc * 16384));
           const uint64_t bd = sw128_desc(smem_u32(sB + cc * NB * 128));
           for (int kk = 0; kk < 4 && 64 * cc + 16 * kk < KM; ++kk)
-            tc_mma(d, ad + 2 * kk, bd + 2 * kk, idesc, (cc | kk) ? 1u : 0u);
+            tc_mma(d, ad + 2 * kk, bd + 2 * kk, idesc, 1u);   // onto the bias
         }
         tc_commit(&bar[1 + slot]);
       }

@@ -433,21 +433,23 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
               break;
             }
             tc_fence_after();
+            // 16 columns per load: with 32 the accumulators and the loaded values
+            // no longer fit in the registers of a thread (10 warps per CTA)
 #pragma unroll
-            for (int h = 0; h < COLS / 32; ++h) {
-              uint32_t v[32];
-              tc_ld32(tbase + b * BN + 32 * h, v);
+            for (int h = 0; h < COLS / 16; ++h) {
+              uint32_t v[16];
+              tc_ld16(tbase + b * BN + 16 * h, v);
               tc_wait_ld();
-              if (h == COLS / 32 - 1) {
+              if (h == COLS / 16 - 1) {
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce[b]);
               }
 #pragma unroll
-              for (int i = 0; i < 32; ++i) {
+              for (int i = 0; i < 16; ++i) {
                 uint32_t hb, lb;
                 drain_parts(v[i], hb, lb);
-                acc[32 * h + i] += (hb << 12) + lb;
+                acc[16 * h + i] += (hb << 12) + lb;
               }
             }
             ++since;
