@@ -7,7 +7,7 @@
 // w <= 8, stored in bfloat16 (exact); a product of two pieces is at most
 // 2^(2w-2) and a sum of `chunk` of them is at most 2^24, so the fp32
 // accumulators of the tensor core hold exact integers.  After every chunk the
-// accumulator is drained from tensor memory into integer registers (drain_parts):
+// accumulator is drained from tensor memory into integer registers (drain_parts2):
 //   v = 4096 q + lo with q = round(v / 4096) by one fma against 1.5*2^23 and
 //   lo = v - 4096 q exact (|lo| <= 2048); the bit patterns 0x4B400000 + q and
 //   0x4B400000 + lo are joined as 4096 (0x4B400000 + q) + (0x4B400000 + lo) and
@@ -59,15 +59,41 @@ constexpr uint32_t STAGE_A = BM * BK * 2;
 constexpr uint32_t MAGIC_BITS = 0x4B400000u;  // bit pattern of 1.5 * 2^23
 constexpr uint64_t DRAIN_BIAS = (uint64_t)MAGIC_BITS * 4097u;   // what a drained value carries
 
+// Packed fp32 arithmetic, two values per instruction (fma / add .f32x2: each
+// element rounded as the scalar operation would round it).
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(uint32_t lo, uint32_t hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t d, uint32_t &lo, uint32_t &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(d));
+}
+constexpr uint64_t kF2Magic = 0x4B4000004B400000ull;      // 1.5 2^23 twice
+constexpr uint64_t kF2NegMagic = 0xCB400000CB400000ull;   // -1.5 2^23
+constexpr uint64_t kF2Inv4096 = 0x3980000039800000ull;    // 2^-12
+constexpr uint64_t kF2Neg4096 = 0xC5800000C5800000ull;    // -2^12
+
 // An integer |v| <= 2^24 held exactly in fp32 as 4096 q + lo: h = 1.5 2^23 +
 // round(v / 4096) (one rounding: v / 4096 is exact), lo = v - 4096 q exact; hb and
 // lb are the bit patterns of 1.5 2^23 + q and 1.5 2^23 + lo, so that
-// 4096 hb + lb = v + DRAIN_BIAS.
-__device__ __forceinline__ void drain_parts(uint32_t vb, uint32_t &hb, uint32_t &lb) {
-  const float v = __uint_as_float(vb);
-  const float h = fmaf(v, 1.0f / 4096.0f, 12582912.0f);
-  hb = __float_as_uint(h);
-  lb = __float_as_uint(fmaf(h - 12582912.0f, -4096.0f, v) + 12582912.0f);
+// 4096 hb + lb = v + DRAIN_BIAS.  Two values v0, v1 at a time: hb and lb of
+// each packed, v0's in the low half.
+__device__ __forceinline__ void drain_parts2(uint32_t v0, uint32_t v1, uint64_t &hb,
+                                             uint64_t &lb) {
+  const uint64_t v = f2_pack(v0, v1);
+  hb = f2_fma(v, kF2Inv4096, kF2Magic);
+  lb = f2_add(f2_fma(f2_add(hb, kF2NegMagic), kF2Neg4096, v), kF2Magic);
 }
 // Kernel shapes.  Tile 128 x BN (BN = 128 or 256); NBUF accumulators of BN fp32
 // columns in tensor memory (all 512 columns: with 128-column tiles four, so that
@@ -446,10 +472,14 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
                 if (lane == 0) mbar_arrive(&acce[b]);
               }
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                uint32_t hb, lb;
-                drain_parts(v[i], hb, lb);
-                acc[16 * h + i] += (hb << 12) + lb;
+              for (int i = 0; i < 16; i += 2) {
+                uint64_t hb, lb;
+                drain_parts2(v[i], v[i + 1], hb, lb);
+                uint32_t h0, h1, l0, l1;
+                f2_unpack(hb, h0, h1);
+                f2_unpack(lb, l0, l1);
+                acc[16 * h + i] += (h0 << 12) + l0;
+                acc[16 * h + i + 1] += (h1 << 12) + l1;
               }
             }
             ++since;
@@ -471,18 +501,20 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             const uint32_t pm = P.crt_p[t], m32 = P.crt_m32[t];
             const uint32_t offb = P.crt_off[t] - (uint32_t)since * (uint32_t)DRAIN_BIAS;
             const float cf = P.crt_cf[t];
+            const uint64_t ncf = f2_pack(__float_as_uint(-cf), __float_as_uint(-cf));
             uint32_t pk[COLS / 2];
 #pragma unroll
             for (int e = 0; e < COLS / 2; ++e) {
-              uint32_t h2[2];
+              uint32_t rb[2];
 #pragma unroll
               for (int o = 0; o < 2; ++o) {
                 const uint32_t u = acc[2 * e + o] + offb;
                 const uint32_t r0 = u - __umulhi(u, m32) * pm;
-                const uint32_t rr = min(r0, r0 - pm);
-                h2[o] = __float_as_uint(__uint_as_float(0x4B400000u + rr) - cf);
+                rb[o] = 0x4B400000u + min(r0, r0 - pm);
               }
-              asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(pk[e]) : "r"(h2[0]), "r"(h2[1]));
+              uint32_t f0, f1;
+              f2_unpack(f2_add(f2_pack(rb[0], rb[1]), ncf), f0, f1);
+              asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(pk[e]) : "r"(f0), "r"(f1));
             }
             uint8_t *box = sOut + (warp - 2) * 4096;
             const int y = (int)((int64_t)x.tm * BM + quarter * 32);
@@ -583,10 +615,11 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             tc_ld32(tbase + b * BN, v);
             tc_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              uint32_t hb, lb;
-              drain_parts(v[i], hb, lb);
-              acc[i] += ((uint64_t)hb << 12) + lb;
+            for (int i = 0; i < 32; i += 2) {
+              uint64_t hb, lb;
+              drain_parts2(v[i], v[i + 1], hb, lb);
+              acc[i] += ((uint64_t)(uint32_t)hb << 12) + (uint32_t)lb;
+              acc[i + 1] += ((hb >> 32) << 12) + (lb >> 32);
             }
             tc_ld32(tbase + b * BN + 32, v);
             tc_wait_ld();
@@ -594,10 +627,11 @@ __global__ void __launch_bounds__(Shape<BN_, NARROW>::THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[b]);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              uint32_t hb, lb;
-              drain_parts(v[i], hb, lb);
-              acc[32 + i] += ((uint64_t)hb << 12) + lb;
+            for (int i = 0; i < 32; i += 2) {
+              uint64_t hb, lb;
+              drain_parts2(v[i], v[i + 1], hb, lb);
+              acc[32 + i] += ((uint64_t)(uint32_t)hb << 12) + (uint32_t)lb;
+              acc[32 + i + 1] += ((hb >> 32) << 12) + (lb >> 32);
             }
           }
         }
