@@ -37,6 +37,17 @@ HEADLINE = ("m-double GEMM C=A*B, M=N=K=4096, quad double (value) and double dou
             "words 2^U[-20,20) random sign, lower words x2^-53 U[-1,1), seed 2; Ozaki form next "
             "to the plain FP64 form at the same error bound")
 KERNELS_PER_STEP = 8   # per operand: exponent, finalize, pieces (x2); product; combine
+LEAD_MIN_ENTRIES = 1 << 22   # residue form: operands this large take leading-word exponents
+
+
+def kernels_per_step(mode, M, N, K):
+    """The library's kernel launches in one product: per operand exponents,
+    finalize and pieces (the residue form's large operands: leading-word
+    exponents, finalize, residues, then the pass over every word, finalize and
+    residues again, which return at once when not needed); product; combine."""
+    if mode != "crt":
+        return KERNELS_PER_STEP
+    return sum(6 if R * K >= LEAD_MIN_ENTRIES else 3 for R in (M, N)) + 2
 WORD_NAMES = {2: "double double", 4: "quad double", 8: "octo double", 16: "hexa double"}
 
 
@@ -472,7 +483,7 @@ def measure_single(args, mw, torch, dist, rank, dev, A, B, workload, mode="ozaki
                      if g is not None else "direct mw_gemm calls",
            "roofline": roofline_of(pairs, flops, kern_ms, workload_key(m, M, N, K, mode))
                        if mode != "textbook" else None,
-           "clocks": clk, "gpu_launches": KERNELS_PER_STEP * args.steps}
+           "clocks": clk, "gpu_launches": kernels_per_step(mode, M, N, K) * args.steps}
     del g
     extras(args, mw, torch, dist, rank, dev, A, B, tA, tB, plan, rec, plain_steps, e2e_steps,
            cpu_s, pipes)

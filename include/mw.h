@@ -162,7 +162,9 @@ int mw_crt_moduli(int *moduli, int n);
 int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K, size_t *bytes);
 
 /* Where mw_gemm keeps its intermediates inside ws, for inspection and tests:
- * offsets[0] int32 exponents and spreads: E_A[M], spread_A[M], E_B[N], spread_B[N];
+ * offsets[0] int32 exponents and spreads: E_A[M], spread_A[M], E_B[N], spread_B[N],
+ *            then the two largest spreads and two flags (MW_CRT: an operand's
+ *            exponents were taken again over every word);
  * offsets[1] pieces of op(A): S_A planes of M x Kp (Kp = K rounded up to 64),
  *            bfloat16 (MW_OZAKI) or double (MW_PLAIN), layout as in mw_split;
  *            MW_CRT: D planes of balanced residues (bfloat16), plane i mod p_i;
@@ -173,8 +175,9 @@ int mw_gemm_workspace_size(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
  *            int32 s_t, t < D; otherwise int64 planes g < G holding
  *            V = sum_t s_t 2^(w (t1 - t)) over the diagonals of group g,
  *            [g*group, t1 = min(D, (g+1)*group) - 1].
- *            MW_CRT: D int32 planes, plane i congruent mod p_i to the sum of
- *            products of residues (equal to it while K (p_i/2)^2 < 2^31).
+ *            MW_CRT: D bfloat16 planes of M rows of N rounded up to 8 entries
+ *            (row-major), plane i the balanced residue mod p_i of each entry's
+ *            sum of products of residues.
  * bytes = total workspace size (same as mw_gemm_workspace_size).
  * No counterpart in the paper (device memory sizing). */
 int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t K,
@@ -185,7 +188,10 @@ int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t 
  * (A stored K x M, B stored N x K).  plan->m words per entry in A, B and C.
  * ws: device workspace of at least mw_gemm_workspace_size() bytes; it holds the
  * pieces, the exponents and the diagonal partial sums; no memory is allocated.
- * Asynchronous on `stream`.
+ * Asynchronous on `stream`.  MW_CRT takes the shared exponents from the leading
+ * words first and checks every entry while cutting it; an operand with an entry
+ * whose later word is larger (input that is not normalised), not finite or out of
+ * range is cut again with the exponents over every word.
  * Cites: Section 2 (error-free summation of pieces, the s_i) and
  * Section 4 (the matrix form, pieces of matrices on tensor cores; the Ozaki
  * scheme, whose residue form MW_CRT computes). */

@@ -92,7 +92,8 @@ Layout layout(const mw_plan &p, int64_t M, int64_t N, int64_t K) {
   // planes of pieces: S_A / S_B digits, or D residues in the residue form
   const size_t planesA = p.mode == MW_CRT ? p.D : p.S_A, planesB = p.mode == MW_CRT ? p.D : p.S_B;
   L.exps = 0;
-  size_t off = align256(sizeof(int32_t) * (2 * (size_t)M + 2 * (size_t)N + 2));
+  // exponents and spreads of both operands, the largest spreads, the redo flags
+  size_t off = align256(sizeof(int32_t) * (2 * (size_t)M + 2 * (size_t)N + 4));
   L.digA = off;
   off = align256(off + planesA * M * L.Kp * elem);
   L.digB = off;
@@ -372,7 +373,7 @@ int mw_gemm_workspace_layout(const mw_plan *plan, int64_t M, int64_t N, int64_t 
 namespace {
 
 struct Operands {
-  int32_t *eA, *spA, *eB, *spB, *maxsp;
+  int32_t *eA, *spA, *eB, *spB, *maxsp, *redo;
 };
 
 Operands ops_in(void *ws, int64_t M, int64_t N) {
@@ -383,6 +384,7 @@ Operands ops_in(void *ws, int64_t M, int64_t N) {
   o.eB = base + 2 * M;
   o.spB = base + 2 * M + N;
   o.maxsp = base + 2 * M + 2 * N;
+  o.redo = base + 2 * M + 2 * N + 2;
   return o;
 }
 
@@ -424,12 +426,14 @@ int split_both(const mw_plan &p, int transA, int transB, int64_t M, int64_t N, i
   a.trans = transA; a.R = M; a.ld = lda; a.plane_stride = psa; a.X = A; a.S = p.S_A;
   a.digits = w8 + L.digA; a.exps = o.eA; a.spread = o.spA; a.max_spread = o.maxsp;
   a.range = p.range_A;
+  a.redo = p.mode == MW_CRT ? o.redo : nullptr;
   int rc = launch_split(a, exps_only, s);
   if (!rc) {
     // op(B) used as its transpose: rows N; B stored K x N (trans 0 -> columns) or N x K
     a.trans = !transB; a.R = N; a.ld = ldb; a.plane_stride = psb; a.X = B; a.S = p.S_B;
     a.digits = w8 + L.digB; a.exps = o.eB; a.spread = o.spB; a.max_spread = o.maxsp + 1;
     a.range = p.range_B;
+    a.redo = p.mode == MW_CRT ? o.redo + 1 : nullptr;
     rc = launch_split(a, exps_only, s2);
   }
   // join the side stream whatever happened (inside a capture a fork must be joined)

@@ -176,7 +176,9 @@ template <int MW, int NL, bool TRANS>
 __global__ void __launch_bounds__(kResTile, 4)
     residues_mma_kernel(const __grid_constant__ CUtensorMap omap, const double *__restrict__ X,
                         int64_t R, int64_t K, int64_t ld, int64_t ps, int L, int S, int nmod,
-                        int npad, int64_t dld, const int *E, unsigned int *status) {
+                        int npad, int64_t dld, const int *E, unsigned int *status,
+                        int32_t *redo, const int32_t *gate) {
+  if (gate && *gate == 0) return;                  // the pass over every word is not needed
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sB = sA + kTileBytes;                   // npad rows x 64 constants
@@ -254,7 +256,27 @@ __global__ void __launch_bounds__(kResTile, 4)
     {
       uint64_t T[NL];
       fixed_point<MW, NL>(ec.x, ec.valid ? L - 2 - E[ec.r] : 0, T);
-      if (ec.valid && !in_range_bits<NL>(T, L)) raise_status(status, MW_ERANGE);
+      const bool in = in_range_bits<NL>(T, L);
+      if (redo) {
+        // exponents from the leading words: they hold for this entry when its
+        // leading word is normal and no later word has a larger exponent field, or
+        // when every word is zero; anything else (and a value out of range) sends
+        // the operand through the pass over every word
+        const uint32_t e0 = (uint32_t)(__double_as_longlong(ec.x[0]) >> 52) & 0x7ffu;
+        bool lead = e0 != 0x7ffu;
+        bool rest = false;                         // a later word is nonzero
+#pragma unroll
+        for (int j = 1; j < MW; ++j) {
+          const uint64_t b = (uint64_t)__double_as_longlong(ec.x[j]);
+          const uint32_t ej = (uint32_t)(b >> 52) & 0x7ffu;
+          lead &= ej <= e0 && ej != 0x7ffu;
+          rest |= (b << 1) != 0;
+        }
+        if (e0 == 0) lead = !rest;                 // zero or subnormal, the only nonzero word
+        if (ec.valid && !(lead && in)) atomicExch(redo, 1);
+      } else if (ec.valid && !in) {
+        raise_status(status, MW_ERANGE);
+      }
       const bool neg = add_bias_w8<NL>(T, S);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {               // 16-byte chunk c: digits 8c .. 8c+7
@@ -380,7 +402,7 @@ int launch_residues_t(const SplitArgs &a, cudaStream_t s) {
   const int64_t ntiles = (a.trans ? (a.R + 3) / 4 : a.R) * ktiles;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
   kern<<<grid, kResTile, smem, s>>>(map, a.X, a.R, a.K, a.ld, a.plane_stride, a.S, S, a.nmod,
-                                    npad, a.digit_ld, a.exps, status_ptr());
+                                    npad, a.digit_ld, a.exps, status_ptr(), a.redo, a.gate);
   return cuda_fail(cudaGetLastError(), "residue split launch");
 }
 

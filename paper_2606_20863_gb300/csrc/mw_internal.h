@@ -27,6 +27,12 @@ struct SplitArgs {
   const double *X;
   void *digits;
   int32_t *exps, *spread, *max_spread;
+  // residue form of mw_gemm: the exponents come from the leading words first; the
+  // residue split sets *redo for an entry whose later word is larger (or not
+  // finite, or out of range), and the pass over every word then runs again
+  // (kernels that read *gate == 0 return at once).  nullptr: one pass.
+  int32_t *redo;
+  const int32_t *gate;
 };
 int launch_split(const SplitArgs &a, bool exponents_only, cudaStream_t s);
 

@@ -14,6 +14,8 @@
 //   complement), then the balanced base-2^w digits from the least significant
 //   end with a carry, written as bfloat16 or double.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 #include <cstdio>
 #include <type_traits>
 
@@ -36,79 +38,105 @@ __device__ __forceinline__ void entry_exps(const double *x, int64_t plane_stride
 }
 
 // ---- pass 1 ------------------------------------------------------------------
-// trans = 0: block = 256 threads along k of one row; grid (R, ceil(K/1024)).
+// m words per entry (m = 1: the leading words only).  Kernels given a gate return
+// at once while *gate == 0; their blocks loop over the work, so that a launch
+// that turns out not to be needed costs few blocks.
+// trans = 0: block = 256 threads along 1024 k of one row; work unit (r, k chunk).
+constexpr int kRowChunk = 1024;
+// operands of at least this many entries take their exponents from the leading
+// words first (below it the extra launches cost more than the words saved)
+constexpr int64_t kLeadMinEntries = 1 << 22;
 __global__ void exps_rows_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
                                  int64_t ld, int64_t ps, int *Eb, int *eminb,
-                                 unsigned int *status) {
-  const int64_t r = blockIdx.x;
-  int emax = kExpZero, emin = -kExpZero;
+                                 unsigned int *status, const int32_t *gate) {
+  if (gate && *gate == 0) return;
+  const int64_t nkc = (K + kRowChunk - 1) / kRowChunk;
   bool bad = false;
-  for (int64_t k = blockIdx.y * (int64_t)blockDim.x * 4 + threadIdx.x;
-       k < K && k < (blockIdx.y + 1) * (int64_t)blockDim.x * 4; k += blockDim.x) {
-    int e;
-    entry_exps(X + r * ld + k, ps, m, e, bad);
-    if (e != kExpZero) {
-      emax = max(emax, e);
-      emin = min(emin, e);
-    }
-  }
-  for (int o = 16; o; o >>= 1) {
-    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
-  }
-  if (bad) raise_status(status, MW_ENONFINITE);
-  if ((threadIdx.x & 31) == 0 && emax != kExpZero) {
-    atomicMax(Eb + r, emax + kBias);
-    atomicMax(eminb + r, kBias - emin);
-  }
-}
-
-// trans = 1: block = 32 (r) x 8 (k) threads; each block covers 32 columns and
-// kRowsPerBlock rows of the stored K x R matrix.
-constexpr int kRowsPerBlock = 32;
-__global__ void exps_cols_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
-                                 int64_t ld, int64_t ps, int *Eb, int *eminb,
-                                 unsigned int *status) {
-  __shared__ int smax[8][32], smin[8][32];
-  const int64_t r = blockIdx.x * 32 + threadIdx.x;
-  const int64_t k0 = (int64_t)blockIdx.y * kRowsPerBlock;
-  int emax = kExpZero, emin = -kExpZero;
-  bool bad = false;
-  if (r < R) {
-    for (int64_t k = k0 + threadIdx.y; k < K && k < k0 + kRowsPerBlock; k += 8) {
+  for (int64_t u = blockIdx.x; u < R * nkc; u += gridDim.x) {
+    const int64_t r = u / nkc, kc = u - r * nkc;
+    int emax = kExpZero, emin = -kExpZero;
+    for (int64_t k = kc * kRowChunk + threadIdx.x; k < K && k < (kc + 1) * kRowChunk;
+         k += blockDim.x) {
       int e;
-      entry_exps(X + k * ld + r, ps, m, e, bad);
+      entry_exps(X + r * ld + k, ps, m, e, bad);
       if (e != kExpZero) {
         emax = max(emax, e);
         emin = min(emin, e);
       }
     }
-  }
-  if (bad) raise_status(status, MW_ENONFINITE);
-  smax[threadIdx.y][threadIdx.x] = emax;
-  smin[threadIdx.y][threadIdx.x] = emin;
-  __syncthreads();
-  if (threadIdx.y == 0 && r < R) {
-    for (int i = 1; i < 8; ++i) {
-      emax = max(emax, smax[i][threadIdx.x]);
-      emin = min(emin, smin[i][threadIdx.x]);
+    for (int o = 16; o; o >>= 1) {
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
     }
-    if (emax != kExpZero) {
+    if ((threadIdx.x & 31) == 0 && emax != kExpZero) {
       atomicMax(Eb + r, emax + kBias);
       atomicMax(eminb + r, kBias - emin);
     }
   }
+  if (bad) raise_status(status, MW_ENONFINITE);
 }
 
+// trans = 1: block = 32 (r) x 8 (k) threads; work unit: 32 columns x
+// kRowsPerBlock rows of the stored K x R matrix.
+constexpr int kRowsPerBlock = 32;
+__global__ void exps_cols_kernel(const double *__restrict__ X, int m, int64_t R, int64_t K,
+                                 int64_t ld, int64_t ps, int *Eb, int *eminb,
+                                 unsigned int *status, const int32_t *gate) {
+  if (gate && *gate == 0) return;
+  __shared__ int smax[8][32], smin[8][32];
+  const int64_t nrb = (R + 31) / 32, nkb = (K + kRowsPerBlock - 1) / kRowsPerBlock;
+  bool bad = false;
+  for (int64_t u = blockIdx.x; u < nrb * nkb; u += gridDim.x) {
+    const int64_t kb = u / nrb, rb = u - kb * nrb;  // neighbouring blocks: neighbouring r
+    const int64_t r = rb * 32 + threadIdx.x;
+    const int64_t k0 = kb * kRowsPerBlock;
+    int emax = kExpZero, emin = -kExpZero;
+    if (r < R) {
+      for (int64_t k = k0 + threadIdx.y; k < K && k < k0 + kRowsPerBlock; k += 8) {
+        int e;
+        entry_exps(X + k * ld + r, ps, m, e, bad);
+        if (e != kExpZero) {
+          emax = max(emax, e);
+          emin = min(emin, e);
+        }
+      }
+    }
+    smax[threadIdx.y][threadIdx.x] = emax;
+    smin[threadIdx.y][threadIdx.x] = emin;
+    __syncthreads();
+    if (threadIdx.y == 0 && r < R) {
+      for (int i = 1; i < 8; ++i) {
+        emax = max(emax, smax[i][threadIdx.x]);
+        emin = min(emin, smin[i][threadIdx.x]);
+      }
+      if (emax != kExpZero) {
+        atomicMax(Eb + r, emax + kBias);
+        atomicMax(eminb + r, kBias - emin);
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) raise_status(status, MW_ENONFINITE);
+}
+
+// E_r and the spread from the biased maxima, then the largest spread and the
+// warning (MW_WRANGE).  mode 1: the conversion only (exponents from the leading
+// words, checked later); mode 2, after that check: when the operand was not
+// passed over again (*redo == 0) the largest spread and the warning from the
+// values already converted.
 __global__ void exps_finalize_kernel(int64_t R, int *E, int *spread, int *max_spread, int range,
-                                     unsigned int *status) {
+                                     unsigned int *status, const int32_t *redo, int mode) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= R) return;
-  const int eb = E[r], mb = spread[r];
-  const int Er = eb > 0 ? eb - kBias : 0;
-  const int sp = eb > 0 ? Er - (kBias - mb) : 0;
-  E[r] = Er;
-  spread[r] = sp;
+  int Er = E[r], sp = spread[r];
+  if (mode != 2 || *redo) {
+    const int eb = Er, mb = sp;
+    Er = eb > 0 ? eb - kBias : 0;
+    sp = eb > 0 ? Er - (kBias - mb) : 0;
+    E[r] = Er;
+    spread[r] = sp;
+  }
+  if (mode == 1) return;
   if (max_spread) atomicMax(max_spread, sp);
   if (range >= 0 && sp > range) raise_status(status, MW_WRANGE);
 }
@@ -241,25 +269,57 @@ int launch_pieces_m(const SplitArgs &a, cudaStream_t s) {
 
 }  // namespace
 
+// Exponents of the operand from m words per entry.  gate: the pass over every
+// word after the leading words' check (runs only if *gate != 0, on a small grid:
+// it is rarely needed); it accumulates onto the converted values of the first
+// pass, which every biased maximum exceeds.
+int launch_exps(const SplitArgs &a, int m, int mode, const int32_t *gate, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = (int64_t)(gate ? 2 : 16) * std::max(nsm, 1);
+  if (!a.trans) {
+    const int64_t units = a.R * ((a.K + kRowChunk - 1) / kRowChunk);
+    exps_rows_kernel<<<(unsigned)std::min(units, cap), 256, 0, s>>>(
+        a.X, m, a.R, a.K, a.ld, a.plane_stride, a.exps, a.spread, status_ptr(), gate);
+  } else {
+    const int64_t units = ((a.R + 31) / 32) * ((a.K + kRowsPerBlock - 1) / kRowsPerBlock);
+    exps_cols_kernel<<<(unsigned)std::min(units, cap), dim3(32, 8), 0, s>>>(
+        a.X, m, a.R, a.K, a.ld, a.plane_stride, a.exps, a.spread, status_ptr(), gate);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "split exponent launch");
+  exps_finalize_kernel<<<(unsigned)((a.R + 255) / 256), 256, 0, s>>>(
+      a.R, a.exps, a.spread, a.max_spread, a.range, status_ptr(), a.redo, mode);
+  return cuda_fail(cudaGetLastError(), "split finalize launch");
+}
+
 int launch_split(const SplitArgs &a, bool exponents_only, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.exps, 0, sizeof(int32_t) * a.R, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.spread, 0, sizeof(int32_t) * a.R, s);
   if (e != cudaSuccess) return cuda_fail(e, "split memset");
-  if (!a.trans) {
-    dim3 grid((unsigned)a.R, (unsigned)((a.K + 1023) / 1024));
-    exps_rows_kernel<<<grid, 256, 0, s>>>(a.X, a.m, a.R, a.K, a.ld, a.plane_stride, a.exps,
-                                          a.spread, status_ptr());
-  } else {
-    dim3 grid((unsigned)((a.R + 31) / 32), (unsigned)((a.K + kRowsPerBlock - 1) / kRowsPerBlock));
-    exps_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(a.X, a.m, a.R, a.K, a.ld, a.plane_stride,
-                                                  a.exps, a.spread, status_ptr());
+  if (a.nmod > 0 && a.redo && !exponents_only && a.R * a.K >= kLeadMinEntries) {
+    // residue form, large operands: exponents from the leading words (1/m of the
+    // data), checked entry by entry by the split; only if an entry failed do the
+    // exponents over every word and the split run again
+    if ((e = cudaMemsetAsync(a.redo, 0, sizeof(int32_t), s)) != cudaSuccess)
+      return cuda_fail(e, "split memset");
+    SplitArgs b = a;
+    b.gate = nullptr;
+    int rc = launch_exps(b, 1, 1, nullptr, s);
+    if (!rc) rc = launch_residues(b, s);
+    if (!rc) rc = launch_exps(b, a.m, 2, a.redo, s);
+    if (rc) return rc;
+    b.redo = nullptr;
+    b.gate = a.redo;
+    return launch_residues(b, s);
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split exponent launch");
-  exps_finalize_kernel<<<(unsigned)((a.R + 255) / 256), 256, 0, s>>>(
-      a.R, a.exps, a.spread, a.max_spread, a.range, status_ptr());
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split finalize launch");
-  if (exponents_only) return MW_OK;
-  if (a.nmod > 0) return launch_residues(a, s);
+  SplitArgs b = a;
+  b.redo = nullptr;
+  b.gate = nullptr;
+  int rc = launch_exps(b, a.m, 0, nullptr, s);
+  if (rc || exponents_only) return rc;
+  if (a.nmod > 0) return launch_residues(b, s);
   if (a.format == MW_DIGITS_BF16) return launch_pieces_m<__nv_bfloat16>(a, s);
   return launch_pieces_m<double>(a, s);
 }

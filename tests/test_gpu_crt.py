@@ -112,6 +112,38 @@ def test_crt_paper_pattern_and_zeros(mw, cuda):
     assert not C[:, 3, :].any() and not C[:, :, 5].any()
 
 
+@pytest.mark.parametrize("m,M,N,K,lead", [(4, 70, 45, 130, False), (2, 2048, 2048, 2048, True)])
+def test_crt_entries_not_normalised(mw, cuda, m, M, N, K, lead):
+    """Entries whose later word is larger than the first (a zero leading word, a
+    last word far above the first) in rows of A and a column of B.  Operands of
+    at least 2^22 entries take the exponents from the leading words and the
+    residue split checks every entry: such an operand is cut again with the
+    exponents over every word (the flags after the largest spreads say which).
+    Either way the exponents, residues and words equal the oracle's bit for bit."""
+    rng = SplitMix64(1025 + m)
+    A, B = uniform_mdouble(rng, m, M, K), uniform_mdouble(rng, m, K, N)
+
+    def flags(ws):
+        return ws[4 * (2 * M + 2 * N + 2):4 * (2 * M + 2 * N + 4)].view(torch.int32).cpu().tolist()
+
+    _, ws, _, _ = run_crt(mw, cuda, A, B, mw.plan_for(to_dev(A, cuda), to_dev(B, cuda), "crt"))
+    assert flags(ws) == [0, 0]
+    A[0, 3, 5] = 0.0
+    A[1, 3, 5] = 2.0                      # row 3: leading word zero, second word 2
+    A[0, 1, 0] = 1e-3
+    A[m - 1, 1, 0] = 4.0                  # row 1: the last word far above the first
+    B[0, 2, 4] = 0.0
+    B[m - 1, 2, 4] = -8.0                 # column 4 of B
+    tA, tB = to_dev(A, cuda), to_dev(B, cuda)
+    plan = mw.plan_for(tA, tB, "crt")
+    rows = None if not lead else [0, 1, 3, 1000, M - 1]
+    cols = None if not lead else [0, 4, 777, N - 1]
+    check_crt(mw, cuda, A, B, plan=plan, rows=rows, cols=cols)
+    _, ws, _, _ = run_crt(mw, cuda, A, B, plan)
+    assert flags(ws) == ([1, 1] if lead else [0, 0])
+    mw.check_status()
+
+
 def test_crt_long_k_reduces_mod_p(mw, cuda):
     """K = 40,000 quad doubles: the moduli above 363 drain every 64 products and
     reduce their int32 sums mod p every 511 drains; the stored residues equal
