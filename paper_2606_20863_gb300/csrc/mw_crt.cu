@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "mw_column.cuh"
@@ -139,13 +140,17 @@ __device__ __forceinline__ bool in_range_bits(const uint64_t (&T)[NL], int L) {
 // ---- residue split on the tensor cores -------------------------------------------
 // T = sum_q d_q 2^(8q) with balanced base-256 digits d_q (|d| <= 128, the digits
 // the slice form cuts with w = 8), so T mod p_t = sum_q d_q c_qt mod p_t with
-// c_qt = 2^(8q) mod p_t taken balanced (|c| <= 256).  One MMA per tile of 128
-// entries: A (128 x 64) holds the digits of the tile's entries, written by the
-// threads; B (64 x n) the constants c_qt, built once per CTA, zero for q >= S;
-// both in fp16 (exact for integers up to 2048).  The fp32 sums
-// |sum_q d_q c_qt| <= 64 2^15 = 2^21 are exact, and the epilogue reduces them
-// mod p_t (balanced_f) into a shared tile of bfloat16 residues that one TMA
-// store writes to the residue planes.
+// c_qt = 2^(8q) mod p_t taken balanced (|c| <= 256).  Two MMAs per tile of 256
+// entries (slots 0..255 of the tile's box): A_h (128 x 64) holds the digits of
+// the entries in slots 2j + h, in row rho(j) = j ^ ((j >> 4) & 7) (a permutation
+// that keeps the threads' shared-memory stores free of bank conflicts), written
+// by the threads; B (64 x n) the constants c_qt, built once per CTA, zero for
+// q >= S; both in fp16 (exact for integers up to 2048).  The fp32 sums
+// |sum_q d_q c_qt| <= 64 2^15 = 2^21 are exact; a thread of the epilogue reads
+// the sums of the entries in slots 2j and 2j + 1 (tensor-memory lane rho(j)),
+// reduces them mod p_t (balanced_f) and writes both as one pair of bfloat16
+// into row t of a shared tile of residues that one TMA store writes to the
+// residue planes.
 // Digits from bytes: with H = 128 (1 + 2^8 + ... + 2^(8(S-2))), byte q of T + H
 // is d_q + 128 for q < S-1; the fp16 number with exponent field 0x64 and that
 // byte as low mantissa bits is 1024 + byte, so one byte permute and one packed
@@ -154,16 +159,24 @@ __device__ __forceinline__ bool in_range_bits(const uint64_t (&T)[NL], int L) {
 // difference, +128 or -128, goes into column 63, whose constants are those of
 // column S-1 (S <= 48).  The other columns q >= S multiply zero constants and
 // may hold anything finite.
-// TRANS = false: a tile is 128 consecutive k of one row r; TRANS = true (the
-// operand stored K x R): 4 consecutive r x 32 consecutive k, so that the loads
-// along r fill whole sectors.
-constexpr int kResTile = 128;
-constexpr uint32_t kTileBytes = 128 * 128;        // 128 rows x 64 fp16
+// TRANS = false: a tile is 256 consecutive k of one row r (slot = k); TRANS =
+// true (the operand stored K x R): 8 consecutive r x 32 consecutive k (slot =
+// 32 r + k), thread i reading r = i mod 8, k = i / 8, so that the loads along r
+// fill whole sectors.
+constexpr int kResTile = 256;                     // entries of a tile, threads of a CTA
+constexpr uint32_t kHalfBytes = 128 * 128;        // one A: 128 rows x 64 fp16
 
 // Bytes of shared memory of the residue split for npad constants rows.
 inline size_t residue_smem(int npad) {
-  return 1024 + kTileBytes + (size_t)npad * 128 + (size_t)npad * 256 + 32;
+  return 1024 + 2 * kHalfBytes + (size_t)npad * 128 + (size_t)npad * 512 + 32;
 }
+// Tensor-memory columns: two accumulators of npad columns.
+__host__ __device__ inline uint32_t residue_tmem_cols(int npad) {
+  uint32_t c = 32;
+  while (c < 2u * (uint32_t)npad) c *= 2;
+  return c;
+}
+__host__ __device__ __forceinline__ uint32_t res_rho(uint32_t j) { return j ^ ((j >> 4) & 7u); }
 
 template <int MW>
 struct SplitEntry {      // one thread's entry of a tile: position and words
@@ -173,17 +186,17 @@ struct SplitEntry {      // one thread's entry of a tile: position and words
 };
 
 template <int MW, int NL, bool TRANS>
-__global__ void __launch_bounds__(kResTile, 4)
+__global__ void __launch_bounds__(kResTile, 2)
     residues_mma_kernel(const __grid_constant__ CUtensorMap omap, const double *__restrict__ X,
                         int64_t R, int64_t K, int64_t ld, int64_t ps, int L, int S, int nmod,
                         int npad, int64_t dld, const int *E, unsigned int *status,
                         int32_t *redo, const int32_t *gate) {
   if (gate && *gate == 0) return;                  // the pass over every word is not needed
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *sA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *sB = sA + kTileBytes;                   // npad rows x 64 constants
-  uint8_t *stage = sB + (size_t)npad * 128;        // npad rows of 128 residues (256 B)
-  uint64_t *bar = (uint64_t *)(stage + (size_t)npad * 256);
+  uint8_t *sA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);   // A_0, A_1
+  uint8_t *sB = sA + 2 * kHalfBytes;               // npad rows x 64 constants
+  uint8_t *stage = sB + (size_t)npad * 128;        // npad rows of 256 residues (512 B)
+  uint64_t *bar = (uint64_t *)(stage + (size_t)npad * 512);
   uint32_t *holder = (uint32_t *)(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int idx = tid; idx < npad * 64; idx += kResTile) {
@@ -203,24 +216,25 @@ __global__ void __launch_bounds__(kResTile, 4)
     fence_barrier_init();
     prefetch_map(&omap);
   }
-  const uint32_t ncols = npad <= 64 ? 64u : 128u;
+  const uint32_t ncols = residue_tmem_cols(npad);
   if (warp == 0) tmem_alloc(holder, ncols);
   fence_proxy_async_smem();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *holder;
   const uint32_t idesc = idesc_f16(128, npad);
-  const int64_t ktiles = TRANS ? (dld + 31) / 32 : (dld + 127) / 128;
-  const int64_t rtiles = TRANS ? (R + 3) / 4 : R;
+  const int64_t ktiles = TRANS ? (dld + 31) / 32 : (dld + 255) / 256;
+  const int64_t rtiles = TRANS ? (R + 7) / 8 : R;
   // tile u = a * inner + b: (rt, kt) = (a, b) for rows (k contiguous), (b, a) for
   // the operand stored K x R, so that the CTAs running together read neighbouring
   // r of the same k rows (whole sectors); each CTA steps u by the grid size
   const int64_t inner = TRANS ? rtiles : ktiles, outer = TRANS ? ktiles : rtiles;
   const int64_t gq = gridDim.x / inner, gr = gridDim.x - gq * inner;
-  // this thread's slot in a row of the shared residue tile: the box is 128 k of
-  // one row, or 4 rows x 32 k
-  const uint32_t slot = TRANS ? (uint32_t)((tid & 3) * 32 + (tid >> 2)) : (uint32_t)tid;
-  uint16_t *mine = reinterpret_cast<uint16_t *>(stage) + slot;
+  // this thread's slot in the tile (the box is 256 k of one row, or 8 rows x 32
+  // k), and the row of A_(slot & 1) that takes its digits
+  const uint32_t slot = TRANS ? (uint32_t)((tid & 7) * 32 + (tid >> 3)) : (uint32_t)tid;
+  uint8_t *arow = sA + (slot & 1) * kHalfBytes;
+  const uint32_t rowA = res_rho(slot >> 1);
   volatile int abort_flag = 0;
 
   auto step = [&](int64_t &a, int64_t &b) {
@@ -236,8 +250,8 @@ __global__ void __launch_bounds__(kResTile, 4)
     e.r = e.k = 0;
     if (ta < outer) {
       const int64_t rt = TRANS ? tb : ta, kt = TRANS ? ta : tb;
-      e.r = TRANS ? rt * 4 + (tid & 3) : rt;
-      e.k = TRANS ? kt * 32 + (tid >> 2) : kt * 128 + tid;
+      e.r = TRANS ? rt * 8 + (tid & 7) : rt;
+      e.k = TRANS ? kt * 32 + (tid >> 3) : kt * 256 + tid;
       e.valid = e.r < R && e.k < dld;
     }
     const bool in = e.valid && e.k < K;
@@ -293,7 +307,7 @@ __global__ void __launch_bounds__(kResTile, 4)
           }
         }
         if (c == 7) w[3] = neg ? 0xD8000000u : 0x58000000u;   // column 63: -128 / +128 in fp16
-        *reinterpret_cast<uint4 *>(sA + sw128_offset(tid, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(arow + sw128_offset(rowA, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
     fence_proxy_async_smem();
@@ -301,9 +315,13 @@ __global__ void __launch_bounds__(kResTile, 4)
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint64_t ad = sw128_desc(smem_u32(sA)), bd = sw128_desc(smem_u32(sB));
+      const uint64_t a0 = sw128_desc(smem_u32(sA)), a1 = sw128_desc(smem_u32(sA + kHalfBytes));
+      const uint64_t bd = sw128_desc(smem_u32(sB));
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) tc_mma(tmem, ad + 2 * kk, bd + 2 * kk, idesc, kk ? 1u : 0u);
+      for (int kk = 0; kk < 4; ++kk) tc_mma(tmem, a0 + 2 * kk, bd + 2 * kk, idesc, kk ? 1u : 0u);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc_mma(tmem + npad, a1 + 2 * kk, bd + 2 * kk, idesc, kk ? 1u : 0u);
       tc_commit(&bar[0]);
     }
     {
@@ -315,33 +333,43 @@ __global__ void __launch_bounds__(kResTile, 4)
     if (!ok) break;
     ph ^= 1;
     tc_fence_after();
-    // every sum reduced mod p_t into row t of the shared tile
-    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+    // every sum reduced mod p_t into row t of the shared tile: warp w reads lanes
+    // 32 (w % 4).. (slot pairs rho(lane)) and, of every 32 moduli, the 16 of half
+    // w / 4 (compile-time indices, so the constants of balanced_f stay operands)
+    {
+      const uint32_t lane32 = (uint32_t)((warp & 3) * 32 + (tid & 31));
+      const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(stage) + res_rho(lane32);
+      auto reduce = [&](auto half) {
+        constexpr int HF = decltype(half)::value;
 #pragma unroll
-    for (int h = 0; h < 3; ++h) {                 // 32 moduli at a time
-      if (32 * h >= npad) break;
-      uint32_t v[32];
-      if (32 * h + 32 <= npad) tc_ld32(ta + 32 * h, v);
-      else tc_ld16(ta + 32 * h, v);
-      tc_wait_ld();
-      if (32 * h + 32 <= nmod) {                  // a whole chunk: no bound per modulus
+        for (int h = 0; h < 3; ++h) {
+          const int t0 = 32 * h + 16 * HF;
+          if (t0 >= nmod) break;
+          uint32_t ve[16], vo[16];
+          tc_ld16(ta + t0, ve);
+          tc_ld16(ta + npad + t0, vo);
+          tc_wait_ld();
 #pragma unroll
-        for (int u = 0; u < 32; ++u)
-          mine[(32 * h + u) * 128] = bf16_bits_small(balanced_f(__uint_as_float(v[u]), 32 * h + u));
-      } else {
-#pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          if (32 * h + u >= nmod) break;
-          mine[(32 * h + u) * 128] = bf16_bits_small(balanced_f(__uint_as_float(v[u]), 32 * h + u));
+          for (int u = 0; u < 16; ++u) {
+            if (t0 + u >= nmod) break;
+            const float re = balanced_f(__uint_as_float(ve[u]), 32 * h + 16 * HF + u);
+            const float ro = balanced_f(__uint_as_float(vo[u]), 32 * h + 16 * HF + u);
+            uint32_t pr;
+            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(pr) : "f"(ro), "f"(re));
+            dst[(size_t)(t0 + u) * 128] = pr;
+          }
         }
-      }
+      };
+      if (warp < 4) reduce(std::integral_constant<int, 0>());
+      else reduce(std::integral_constant<int, 1>());
     }
     tc_fence_before();
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {                                // entries past R or dld are clipped
-      if (TRANS) tma_store_3d(&omap, (int)(ca * 32), (int)(cb * 4), 0, smem_u32(stage));
-      else tma_store_3d(&omap, (int)(cb * 128), (int)ca, 0, smem_u32(stage));
+      if (TRANS) tma_store_3d(&omap, (int)(ca * 32), (int)(cb * 8), 0, smem_u32(stage));
+      else tma_store_3d(&omap, (int)(cb * 256), (int)ca, 0, smem_u32(stage));
     }
     ec = en;
   }
@@ -366,12 +394,12 @@ int launch_residues_t(const SplitArgs &a, cudaStream_t s) {
   if (a.digit_ld % 8 || a.R > 0x7fffffffLL || a.digit_ld > 0x7fffffffLL)
     return fail(MW_EUNSUPPORTED, "residue split: planes of %lld x %lld", (long long)a.R,
                 (long long)a.digit_ld);
-  // residue planes [t][r][k] of dld columns; boxes of one row x 128 k, or 4 rows
+  // residue planes [t][r][k] of dld columns; boxes of one row x 256 k, or 8 rows
   // x 32 k, every modulus; no swizzle (the shared tile is dense)
   alignas(64) CUtensorMap map;
   const uint64_t dims[3] = {(uint64_t)a.digit_ld, (uint64_t)a.R, (uint64_t)a.nmod};
   const uint64_t strides[2] = {(uint64_t)a.digit_ld * 2, (uint64_t)a.R * a.digit_ld * 2};
-  const uint32_t box[3] = {a.trans ? 32u : 128u, a.trans ? 4u : 1u, (uint32_t)a.nmod};
+  const uint32_t box[3] = {a.trans ? 32u : 256u, a.trans ? 8u : 1u, (uint32_t)a.nmod};
   int rc = make_map_bf16(&map, a.digits, 3, dims, strides, box, false);
   if (rc) return rc;
   const size_t smem = residue_smem(npad);
@@ -396,10 +424,10 @@ int launch_residues_t(const SplitArgs &a, cudaStream_t s) {
   // resident CTAs: shared memory (1 KB reserved per CTA), registers, tensor memory
   const int by_smem = smem_sm / (int)(smem + 1024);
   const int by_regs = 65536 / (std::max(fa.numRegs, 1) * kResTile);
-  const int by_tmem = npad <= 64 ? 8 : 4;
+  const int by_tmem = (int)(512 / residue_tmem_cols(npad));
   const int per_sm = std::max(1, std::min({by_smem, by_regs, by_tmem}));
-  const int64_t ktiles = a.trans ? (a.digit_ld + 31) / 32 : (a.digit_ld + 127) / 128;
-  const int64_t ntiles = (a.trans ? (a.R + 3) / 4 : a.R) * ktiles;
+  const int64_t ktiles = a.trans ? (a.digit_ld + 31) / 32 : (a.digit_ld + 255) / 256;
+  const int64_t ntiles = (a.trans ? (a.R + 7) / 8 : a.R) * ktiles;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * nsm);
   kern<<<grid, kResTile, smem, s>>>(map, a.X, a.R, a.K, a.ld, a.plane_stride, a.S, S, a.nmod,
                                     npad, a.digit_ld, a.exps, status_ptr(), a.redo, a.gate);
