@@ -291,15 +291,13 @@ def timed(step, steps, flush, mw, dist, dev, phase=True):
 # is captured again.
 KERNEL_SOURCES = ("mw_ozaki.cu", "mw_tc.cuh", "mw_device.cuh", "mw_work.cuh")
 TRAFFIC = {
-    "qd1024": {"bytes": 397976064 + 90011136, "digest": "c2d2db0c82661e45"},
-    "dd4096": {"bytes": 70850295808 + 1618317056, "digest": "c2d2db0c82661e45"},
-    "qd4096": {"bytes": 319538991616 + 2793685760, "digest": "c2d2db0c82661e45"},
+    "qd1024": {"bytes": 394153216 + 85361664, "digest": "9ce880bc15265ecb"},
     # 2,000 of the 20,000 products captured (the whole batch holds ~100 GB), x10
-    "od_batch": {"bytes": 10 * (2873674240 + 2763377152), "digest": "c2d2db0c82661e45"},
+    "od_batch": {"bytes": 10 * (2874157056 + 2759791616), "digest": "9ce880bc15265ecb"},
     # residue form, captured at 2048^3 (quad double 64 moduli, double double 37) and
     # scaled by 4: residue planes in and residues out both grow with N^2
-    "qd4096_crt": {"bytes": 4 * (1076138496 + 508145664), "digest": "c2d2db0c82661e45"},
-    "dd4096_crt": {"bytes": 4 * (622106112 + 280369152), "digest": "c2d2db0c82661e45"},
+    "qd4096_crt": {"bytes": 4 * (1073851648 + 508689920), "digest": "9ce880bc15265ecb"},
+    "dd4096_crt": {"bytes": 4 * (620855040 + 281017600), "digest": "9ce880bc15265ecb"},
 }
 
 

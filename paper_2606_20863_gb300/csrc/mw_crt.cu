@@ -186,7 +186,7 @@ struct SplitEntry {      // one thread's entry of a tile: position and words
 };
 
 template <int MW, int NL, bool TRANS>
-__global__ void __launch_bounds__(kResTile, 2)
+__global__ void __launch_bounds__(kResTile, 3)
     residues_mma_kernel(const __grid_constant__ CUtensorMap omap, const double *__restrict__ X,
                         int64_t R, int64_t K, int64_t ld, int64_t ps, int L, int S, int nmod,
                         int npad, int64_t dld, const int *E, unsigned int *status,
@@ -423,7 +423,7 @@ int launch_residues_t(const SplitArgs &a, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "residue split attributes");
   // resident CTAs: shared memory (1 KB reserved per CTA), registers, tensor memory
   const int by_smem = smem_sm / (int)(smem + 1024);
-  const int by_regs = 65536 / (std::max(fa.numRegs, 1) * kResTile);
+  const int by_regs = ctas_by_registers(fa.numRegs, kResTile);
   const int by_tmem = (int)(512 / residue_tmem_cols(npad));
   const int per_sm = std::max(1, std::min({by_smem, by_regs, by_tmem}));
   const int64_t ktiles = a.trans ? (a.digit_ld + 31) / 32 : (a.digit_ld + 255) / 256;
@@ -712,7 +712,7 @@ int launch_crt_fuse_t(const OzakiArgs &a, const CrtFuse &F, const CUtensorMap &m
   // resident CTAs: what shared memory (1 KB reserved per CTA), registers and the
   // tensor memory (512 columns) hold; the limb columns leave shared memory only
   // when that lets more CTAs reside
-  const int by_regs = 65536 / (std::max(fa.numRegs, 1) * 128);
+  const int by_regs = ctas_by_registers(fa.numRegs, 128);
   const int by_tmem = (int)(512 / FuseShape<NL>::TCOLS);
   const int cap = std::min(by_regs, by_tmem);
   const int in_smem = smem_sm / (int)(fuse_smem(F.D, NL, false) + 1024);

@@ -96,6 +96,16 @@ size_t ozaki_partials_bytes(int64_t M, int64_t N, int D, int group, bool narrow)
 // + j, crt_ld(N) a multiple of 8 (rows start on 16-byte boundaries and
 // tensor-map strides are multiples of 16 bytes).  Then the 8-byte work counter.
 __host__ __device__ inline int64_t crt_ld(int64_t N) { return (N + 7) & ~(int64_t)7; }
+
+// CTAs of `threads` threads using `regs` registers a thread that the register
+// file of one SM holds: registers are given to warps in blocks of 256, and each
+// of the four sub-partitions (16384 registers) holds its share of a CTA's warps.
+inline int ctas_by_registers(int regs, int threads) {
+  const int per_warp = ((regs < 1 ? 1 : regs) * 32 + 255) / 256 * 256;
+  const int warps_per_part = 16384 / per_warp;
+  const int cta_warps_per_part = ((threads + 31) / 32 + 3) / 4;
+  return warps_per_part / cta_warps_per_part;
+}
 size_t crt_residue_planes_bytes(int64_t M, int64_t N, int D);
 size_t crt_partials_bytes(int64_t M, int64_t N, int D);
 // Tensor map of `rank` dimensions over a bfloat16 array (dims innermost first,
