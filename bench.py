@@ -84,12 +84,14 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true",
                     help="headline: leave out the quad-double 1024^3 sub-record")
     ap.add_argument("--m", type=int, default=4, choices=[2, 4, 8, 16],
-                    help="table2: words per m-double (2, 4, 8 or 16)")
+                    help="table2, elementwise: words per m-double (2, 4, 8 or 16; elementwise 2-8)")
+    ap.add_argument("--op", default="div", choices=["add", "mul", "div"],
+                    help="elementwise: the m-double operation (Table 1's add, mul, div)")
     ap.add_argument("--count", type=int, default=20000,
                     help="od_batch: number of products (20,000 is the benchmark; fewer for profiling)")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "qd1024", "dd4096", "qd4096", "od_batch", "adjoint",
-                             "table2", "series"],
+                             "table2", "series", "elementwise"],
                     help="headline (default): the benchmark line, quad and double double at "
                          "4096^3; the others measure one configuration of the method each")
     return ap.parse_args()
@@ -988,6 +990,94 @@ def run_series(args, mw, torch, dist, rank, world, dev):
     return line
 
 
+# FP64 instructions of one m-double operation on the GPU path (two_sum 6,
+# fast_two_sum 3, two_prod 2 = a multiply and a fused multiply-add, a plain add or
+# multiply 1, a division counted as 1), generic operands (every term nonzero), by
+# stepping through the algorithms of mw_elementwise
+ELEMENTWISE_FP64_OPS = {2: {"add": 20, "mul": 9, "div": 79},
+                        4: {"add": 132, "mul": 515, "div": 2797},
+                        8: {"add": 552, "mul": 3655, "div": 35225}}
+
+
+def run_elementwise(args, mw, torch, dist, rank, world, dev):
+    """Table 1's m-double add, mul or div entry by entry: 2^24 entries (division
+    2^22, octo-double division 2^20; --count overrides), magnitudes 2^U[-20,20) random sign, lower words
+    x2^-53 U[-1,1), seed 6, one mw_elementwise call.  Metric: m-double operations
+    per second; roofline on the FP64 pipe (the instructions of one operation
+    times the entries against half the measured DGEMM rate: one fused
+    multiply-add is two flops), with the HBM view (three m-doubles an entry)."""
+    import synthetic
+    m, op = args.m, args.op
+    if m not in ELEMENTWISE_FP64_OPS:
+        raise SystemExit("elementwise: m = 2, 4 or 8")
+    # default sizes: every launch well above L2 (129 MB), a step well under a second
+    default_n = {"add": 1 << 24, "mul": 1 << 24, "div": 1 << 22 if m < 8 else 1 << 20}[op]
+    n = args.count if args.count != 20000 else default_n
+    rng = synthetic.SplitMix64(6)
+    A = synthetic.loguniform_mdouble(rng, m, 1, n, -20, 20).reshape(m, n)
+    B = synthetic.loguniform_mdouble(rng, m, 1, n, -20, 20).reshape(m, n)
+    tA, tB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    C = torch.empty_like(tA)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        mw.mw_elementwise(op, tA, tB, C)
+
+    fp64_peak, _ = measure_pipes(torch, dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    step_ms, _, clk = timed(step, args.steps, flush, mw, dist, dev, phase=False)
+    value, t_step = aggregate(sum(step_ms) / 1e3, n, args.steps, dist, dev)   # G entries/s
+    kern_s = statistics.mean(step_ms) / 1e3
+    ops = ELEMENTWISE_FP64_OPS[m][op]
+    achieved = ops * n / kern_s / 1e12
+    peak = fp64_peak / 2
+    _, _, hbm_gbs, hbm_src = load_peaks()
+    bytes_alg = 3 * 8 * m * n
+    roof = {"bound": "fp64", "achieved": achieved, "peak": peak,
+            "unit": "T FP64 instructions/s", "frac": achieved / peak, "traffic": None,
+            "kernel": f"elementwise_kernel<{m}, {op}> (textbook m-double arithmetic, FP64 pipe)",
+            "peak_source": f"measured DGEMM rate {fp64_peak:.3f} TFLOP/s / 2 (cuBLAS, this run)",
+            "algorithmic": f"{ops} FP64 instructions per entry x {n} entries per launch",
+            "hbm": {"achieved": bytes_alg / kern_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": bytes_alg / kern_s / 1e9 / hbm_gbs,
+                    "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json)",
+                    "algorithmic": f"{bytes_alg} bytes per launch (A, B read, C written once)"}}
+    e2e = None
+    e2e_steps = e2e_count(args)
+    if e2e_steps > 0:
+        hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+        e2e_s = e2e_pipelined(torch, e2e_steps, [hA, hB],
+                              lambda d: [mw.mw_elementwise(op, d[0], d[1])])
+        e2e = {"value": aggregate(e2e_s, n, 1, dist, dev)[0],
+               "unit": "G m-double operations/s",
+               "h2d_bytes_per_step": int((hA.numel() + hB.numel()) * 8),
+               "d2h_bytes_per_step": int(m * n * 8), "how": E2E_HOW}
+    line = {"metric": f"m-double {op} operations per second (Table 1's {op}, entry by entry)",
+            "value": value, "unit": "G m-double operations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"f64x{m} ({WORD_NAMES[m]}; FP64 operations)", "data": "synthetic",
+            "config": {"workload": f"{n} {WORD_NAMES[m]} entries, {op}, magnitudes 2^U[-20,20) "
+                                   "random sign, lower words x2^-53 U[-1,1), seed 6",
+                       "m": m, "op": op, "n": n,
+                       "l2": "inputs larger than L2, and flushed (256 MiB write) before every "
+                             "timed step"},
+            "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": args.steps}
+    if rank == 0 and not args.no_cpu:
+        from oracle import textbook
+        tc = textbook.TextbookC()
+        sample = min(n, 1 << 20 if op != "div" else 1 << 18)
+        t0 = time.perf_counter()
+        tc.elementwise(op, A[:, :sample], B[:, :sample])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sample / dt / 1e9, "unit": "G m-double operations/s",
+                                "cores": tc.max_threads(), "kind": "oracle",
+                                "sample": f"the first {sample} entries, {dt:.2f} s"}
+    return line
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1008,6 +1098,8 @@ def main():
         line = run_table2(args, mw, torch, dist, rank, world, dev)
     elif args.workload == "series":
         line = run_series(args, mw, torch, dist, rank, world, dev)
+    elif args.workload == "elementwise":
+        line = run_elementwise(args, mw, torch, dist, rank, world, dev)
     else:
         line = run_single(args, args.workload, mw, torch, dist, rank, world, dev)
     if rank == 0:

@@ -89,6 +89,8 @@ enum { MW_PLAIN = 0, MW_OZAKI = 1, MW_DOT = 2, MW_CRT = 3, MW_TEXTBOOK = 4 };
 
 /* digit formats written by mw_split */
 enum { MW_DIGITS_BF16 = 0, MW_DIGITS_F64 = 1 };
+/* Operations of mw_elementwise (Table 1's add, mul and div). */
+enum { MW_OP_ADD = 0, MW_OP_MUL = 1, MW_OP_DIV = 2 };
 
 /* A plan fixes the slicing of a product.  mw_plan_gemm fills it from the error
  * analysis (see there); a caller may also set the fields directly.
@@ -259,6 +261,22 @@ int mw_convolve_batched(const mw_plan *plan, int64_t count, int64_t n, const dou
                         int64_t lda, int64_t plane_stride_a, const double *B, int64_t ldb,
                         int64_t plane_stride_b, double *C, int64_t ldc, int64_t plane_stride_c,
                         mw_stream_t stream);
+
+/* Entry-by-entry m-double arithmetic (Table 1: the m-double addition,
+ * multiplication and division whose costs in doubles the paper counts):
+ *   C_e = A_e op B_e,  e < n,  op = MW_OP_ADD, MW_OP_MUL or MW_OP_DIV,
+ * with MW_TEXTBOOK's operations (two_sum, two_prod, renormalisation into m
+ * words); division is long division (m + 1 quotient words from the leading word
+ * of the remainder, the remainder reduced by each word times B, renormalised),
+ * within 2^(1-52m) |A_e / B_e| of the exact quotient on the tested inputs.
+ * Entry e of word plane j of A at A[j * plane_stride_a + e] (likewise B, C);
+ * plane strides at least n.  m = 2, 4 or 8.  One thread per entry; no workspace,
+ * asynchronous on `stream`; nothing is checked on the device (a zero leading
+ * word of B gives IEEE infinities or NaNs).  MW_EINVAL for a bad op, m, n,
+ * stride or NULL pointer (n = 0 does nothing). */
+int mw_elementwise(int op, int m, int64_t n, const double *A, int64_t plane_stride_a,
+                   const double *B, int64_t plane_stride_b, double *C, int64_t plane_stride_c,
+                   mw_stream_t stream);
 
 /* ---- batches of independent products (power-series coefficient convolutions,
  * Section 1, come as many small products of uneven sizes) -------------------- */

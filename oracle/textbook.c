@@ -17,7 +17,8 @@
  * m = 4, 8 and 16 form the exact partial products of each magnitude level
  * (i + j = l) with two_prod, keep the rounded products of level m, and
  * renormalise the level-ordered terms into m words by repeated bottom-up
- * two_sum sweeps, each sweep peeling off one word.
+ * two_sum sweeps, each sweep peeling off one word.  Division (md_div) is long
+ * division with m + 1 quotient words built from these operations.
  *
  * Must be compiled with -ffp-contract=off so that no multiply-add is fused.
  * Layout: every matrix is m planes of row-major doubles, plane j at j*rows*cols.
@@ -130,6 +131,32 @@ static void md_mul(int m, const double *a, const double *b, double *r) {
   renorm(t, n, m, r);
 }
 
+/* m-double division a / b by long division (Table 1's div; the paper gives only
+ * its operation count, so the algorithm is this file's): m + 1 quotient words,
+ * q_i = fl(r_0 / b_0) from the leading word of the remainder r (r = a at
+ * first), r = r - q_i b after each of the first m (q_i b an m-double product of
+ * (q_i, 0, ..., 0) and b, subtracted as an m-double addition of its negation,
+ * for m >= 4 renormalised once more), then the m + 1 quotient words renormalised
+ * into m. */
+static void md_div(int m, const double *a, const double *b, double *r) {
+  double rem[MAXM], q[MAXM + 1], qv[MAXM], t[MAXM], s[MAXM];
+  memcpy(rem, a, sizeof(double) * m);
+  for (int i = 0; i <= m; ++i) {
+    q[i] = rem[0] / b[0];
+    if (i == m) break;
+    memset(qv, 0, sizeof(double) * m);
+    qv[0] = q[i];
+    md_mul(m, qv, b, t);
+    for (int w = 0; w < m; ++w) t[w] = -t[w];
+    md_add(m, rem, t, s);
+    /* the sum cancels in its leading words: for m >= 4 renormalise it once more,
+     * so that its leading word, which gives the next quotient word, leads */
+    if (m > 2) renorm(s, m, m, rem);
+    else memcpy(rem, s, sizeof(double) * m);
+  }
+  renorm(q, m + 1, m, r);
+}
+
 /* C rows listed in `rows` (nrows of them), all N columns:
  * C[j][rows[r]][c] = sum_k A[.][rows[r]][k] * B[.][k][c] in m-double arithmetic.
  * Rows are distributed over `nthreads` OpenMP threads. */
@@ -158,6 +185,25 @@ void tb_gemm_rows(int m, int64_t M, int64_t N, int64_t K, const double *A, const
 /* Single operations, for tests against the Python twin. */
 void tb_mul(int m, const double *a, const double *b, double *r) { md_mul(m, a, b, r); }
 void tb_add(int m, const double *a, const double *b, double *r) { md_add(m, a, b, r); }
+void tb_div(int m, const double *a, const double *b, double *r) { md_div(m, a, b, r); }
+
+/* Elementwise over n entries, m planes each (plane j of x at x + j*n):
+ * op 0 add, 1 mul, 2 div; entries distributed over `nthreads` OpenMP threads. */
+void tb_elementwise(int op, int m, int64_t n, const double *A, const double *B, double *C,
+                    int nthreads) {
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+  for (int64_t e = 0; e < n; ++e) {
+    double a[MAXM], b[MAXM], r[MAXM];
+    for (int w = 0; w < m; ++w) {
+      a[w] = A[w * n + e];
+      b[w] = B[w * n + e];
+    }
+    if (op == 0) md_add(m, a, b, r);
+    else if (op == 1) md_mul(m, a, b, r);
+    else md_div(m, a, b, r);
+    for (int w = 0; w < m; ++w) C[w * n + e] = r[w];
+  }
+}
 
 int tb_max_threads(void) {
 #ifdef _OPENMP

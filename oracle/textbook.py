@@ -14,7 +14,10 @@ multiply-add, so both renderings must agree bit for bit.
 Parity unpinned: ``op_counts`` for the m-double multiplication (m = 2: 24
 operations where Table 1 prints 23) and for m = 4, 8, 16 (Table 1's counts
 belong to algorithms the paper does not give); the counts of the double-double
-addition are pinned to Table 1.
+addition are pinned to Table 1.  Division: the paper gives only its operation
+count (Table 1), so ``div`` / ``tb_div`` are this project's long division; their
+results are pinned by exact rational arithmetic (a relative error bound against
+a / b) and exact cases, their counts are not pinned.
 """
 from __future__ import annotations
 
@@ -57,6 +60,9 @@ class TextbookC:
                                           ctypes.POINTER(i64), i64, ctypes.c_int]
         self.lib.tb_mul.argtypes = [ctypes.c_int, dp, dp, dp]
         self.lib.tb_add.argtypes = [ctypes.c_int, dp, dp, dp]
+        self.lib.tb_div.argtypes = [ctypes.c_int, dp, dp, dp]
+        self.lib.tb_elementwise.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, dp, dp,
+                                            ctypes.c_int]
         self.lib.tb_max_threads.restype = ctypes.c_int
 
     @staticmethod
@@ -83,8 +89,22 @@ class TextbookC:
                               threads or self.max_threads())
         return C
 
+    def elementwise(self, name: str, A: np.ndarray, B: np.ndarray,
+                    threads: int | None = None) -> np.ndarray:
+        """C = A op B entry by entry, op in add, mul, div; A, B (m, ...) m-double
+        arrays.  Table 1's m-double add, mul and div."""
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        assert A.shape == B.shape and A.shape[0] in (2, 4, 8, 16)
+        m = A.shape[0]
+        n = A.size // m
+        C = np.zeros_like(A)
+        self.lib.tb_elementwise({"add": 0, "mul": 1, "div": 2}[name], m, n, self._p(A),
+                                self._p(B), self._p(C), threads or self.max_threads())
+        return C
+
     def op(self, name: str, a: Sequence[float], b: Sequence[float]) -> list[float]:
-        """One m-double add or multiply in C (Section 1's arithmetic)."""
+        """One m-double add, multiply or divide in C (Section 1's arithmetic; Table 1)."""
         m = len(a)
         x = np.array(a, dtype=np.float64)
         y = np.array(b, dtype=np.float64)
@@ -203,6 +223,26 @@ class Counting:
             self._f(1)
         t += lo_prev
         return self.renorm(t, m)
+
+    def div(self, a, b):
+        """m-double division a / b by long division (Table 1's div; the paper gives
+        only its operation count): m + 1 quotient words, each the leading word of
+        the remainder over b's leading word, the remainder reduced by q_i b (an
+        m-double product and addition, for m >= 4 renormalised once more) after
+        each of the first m, then the quotient words renormalised into m."""
+        m = len(a)
+        rem, q = list(a), []
+        for i in range(m + 1):
+            qi = rem[0] / b[0]
+            self._f(1)
+            q.append(qi)
+            if i == m:
+                break
+            t = self.mul([qi] + [0.0] * (m - 1), b)
+            rem = self.add(rem, [-x for x in t])
+            if m > 2:                # the sum cancels in its leading words: once more
+                rem = self.renorm(rem, m)
+        return self.renorm(q, m)
 
     def gemm(self, A: np.ndarray, B: np.ndarray) -> np.ndarray:
         """Textbook m-double GEMM (Section 1's arithmetic, Table 1's 'ordinary' inner products)."""

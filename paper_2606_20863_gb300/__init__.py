@@ -102,6 +102,7 @@ def _load():
         "mw_crt_moduli": [ip, i32],
         "mw_convolve_batched": [pp, i64, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64, vp],
         "mw_set_phase_events": [ctypes.POINTER(ctypes.c_void_p), i32],
+        "mw_elementwise": [i32, i32, i64, vp, i64, vp, i64, vp, i64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -120,7 +121,8 @@ EXPORTED = ("mw_plan_gemm", "mw_split", "mw_gemm_workspace_size", "mw_gemm_works
             "mw_version", "mw_set_phase_events", "mw_gemm_noalloc", "mw_batch_describe",
             "mw_gemm_batched_workspace_size", "mw_measure_spread_batched",
             "mw_measure_spread_batched_workspace_size", "mw_gemm_batched",
-            "mw_dot_batched", "mw_selftest_timeout", "mw_crt_moduli", "mw_convolve_batched")
+            "mw_dot_batched", "mw_selftest_timeout", "mw_crt_moduli", "mw_convolve_batched",
+            "mw_elementwise")
 
 
 def _check(rc: int, what: str):
@@ -523,6 +525,32 @@ def mw_dot_batched(A: torch.Tensor, B: torch.Tensor, plan: mw_plan | None = None
            "mw_dot_batched")
     if check:
         check_status()
+    return C
+
+
+MW_OP_ADD, MW_OP_MUL, MW_OP_DIV = 0, 1, 2
+_OPS = {"add": MW_OP_ADD, "mul": MW_OP_MUL, "div": MW_OP_DIV}
+
+
+def mw_elementwise(op: str, A: torch.Tensor, B: torch.Tensor,
+                   C: torch.Tensor | None = None) -> torch.Tensor:
+    """C = A op B entry by entry (op "add", "mul" or "div"; Table 1's m-double
+    operations); A, B and C are contiguous CUDA float64 tensors of one shape
+    (m, ...), plane j = A[j]."""
+    if op not in _OPS:
+        raise MWError(f"op must be add, mul or div, not {op!r}")
+    if A.shape != B.shape or A.dim() < 2:
+        raise MWError("A and B must be (m, ...) tensors of one shape")
+    if C is None:
+        C = torch.empty_like(A)
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.shape != A.shape:
+            raise MWError(f"{name} must be a contiguous CUDA float64 tensor of A's shape")
+    m = A.shape[0]
+    n = A[0].numel()
+    _check(_lib.mw_elementwise(_OPS[op], m, n, ctypes.c_void_p(A.data_ptr()), n,
+                               ctypes.c_void_p(B.data_ptr()), n, ctypes.c_void_p(C.data_ptr()), n,
+                               _stream()), "mw_elementwise")
     return C
 
 

@@ -509,6 +509,21 @@ int mw_gemm(const mw_plan *plan, int transA, int transB, int64_t M, int64_t N, i
   return rc;
 }
 
+int mw_elementwise(int op, int m, int64_t n, const double *A, int64_t plane_stride_a,
+                   const double *B, int64_t plane_stride_b, double *C, int64_t plane_stride_c,
+                   mw_stream_t stream) {
+  if (op != MW_OP_ADD && op != MW_OP_MUL && op != MW_OP_DIV)
+    return fail(MW_EINVAL, "mw_elementwise: op %d (add 0, mul 1, div 2)", op);
+  if (m != 2 && m != 4 && m != 8) return fail(MW_EINVAL, "mw_elementwise: m = %d (2, 4 or 8)", m);
+  if (n < 0) return fail(MW_EINVAL, "mw_elementwise: n = %lld", (long long)n);
+  if (n == 0) return MW_OK;
+  if (!A || !B || !C) return fail(MW_EINVAL, "mw_elementwise: NULL operand");
+  if (plane_stride_a < n || plane_stride_b < n || plane_stride_c < n)
+    return fail(MW_EINVAL, "mw_elementwise: plane strides must be at least n");
+  return launch_elementwise(op, m, n, A, plane_stride_a, B, plane_stride_b, C, plane_stride_c,
+                            (cudaStream_t)stream);
+}
+
 int mw_measure_spread(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,
                       const double *A, int64_t lda, int64_t psa, const double *B, int64_t ldb,
                       int64_t psb, void *ws, size_t ws_bytes, int *range_A, int *range_B,

@@ -118,6 +118,8 @@ int make_map_bf16(void *map, const void *base, int rank, const uint64_t *dims,
 int launch_textbook(int m, int transA, int transB, int64_t M, int64_t N, int64_t K,
                     const double *A, int64_t lda, int64_t psa, const double *B, int64_t ldb,
                     int64_t psb, double *C, int64_t ldc, int64_t psc, cudaStream_t s);
+int launch_elementwise(int op, int m, int64_t n, const double *A, int64_t psa, const double *B,
+                       int64_t psb, double *C, int64_t psc, cudaStream_t s);
 
 // ---- residue form (mw_crt.cu) -------------------------------------------------
 constexpr int kCrtMaxModuli = 96;   // capacity of the moduli tables

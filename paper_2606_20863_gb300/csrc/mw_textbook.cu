@@ -19,7 +19,18 @@
 //
 // One thread per output, 16 x 16 outputs a CTA, 16-wide k panels of A and B
 // staged in shared memory (m planes each).  The FP64 pipe bounds it.
+//
+// The same operations serve mw_elementwise (Table 1's add, mul and div entry by
+// entry).  Division is long division, the paper giving only its operation count:
+// m + 1 quotient words q_i = fl(r_0 / b_0) from the leading word of the remainder
+// r (r = a at first), r = r - q_i b after each of the first m (the m-double
+// product of (q_i, 0, ..., 0) and b, subtracted as an m-double addition of its
+// negation; for m >= 4 the sum, which cancels in its leading words, renormalised
+// once more so that its leading word leads), then the quotient words
+// renormalised into m.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "mw_device.cuh"
 #include "mw_internal.h"
@@ -128,6 +139,71 @@ __device__ __forceinline__ void tb_mul(const double (&a)[M], const double (&b)[M
   }
 }
 
+template <int M>
+__device__ __forceinline__ void tb_div(const double (&a)[M], const double (&b)[M], double (&r)[M]) {
+  double rem[M], q[M + 1];
+#pragma unroll
+  for (int w = 0; w < M; ++w) rem[w] = a[w];
+#pragma unroll
+  for (int i = 0; i <= M; ++i) {
+    q[i] = __ddiv_rn(rem[0], b[0]);
+    if (i == M) break;
+    double qv[M], t[M], s[M];
+    qv[0] = q[i];
+#pragma unroll
+    for (int w = 1; w < M; ++w) qv[w] = 0.0;
+    tb_mul<M>(qv, b, t);
+#pragma unroll
+    for (int w = 0; w < M; ++w) t[w] = -t[w];
+    tb_add<M>(rem, t, s);
+    if constexpr (M > 2) {
+      tb_renorm<M, M>(s, rem);
+    } else {
+#pragma unroll
+      for (int w = 0; w < M; ++w) rem[w] = s[w];
+    }
+  }
+  tb_renorm<M, M + 1>(q, r);
+}
+
+// C = A op B entry by entry (OP 0 add, 1 mul, 2 div), n entries, m planes each;
+// one thread per entry, the loads of a plane coalesced.
+template <int MW, int OP>
+__global__ void __launch_bounds__(256) elementwise_kernel(const double *__restrict__ A,
+                                                          int64_t psa,
+                                                          const double *__restrict__ B,
+                                                          int64_t psb, double *C, int64_t psc,
+                                                          int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double a[MW], b[MW], r[MW];
+#pragma unroll
+    for (int w = 0; w < MW; ++w) {
+      a[w] = A[w * psa + e];
+      b[w] = B[w * psb + e];
+    }
+    if constexpr (OP == 0) tb_add<MW>(a, b, r);
+    else if constexpr (OP == 1) tb_mul<MW>(a, b, r);
+    else tb_div<MW>(a, b, r);
+#pragma unroll
+    for (int w = 0; w < MW; ++w) C[w * psc + e] = r[w];
+  }
+}
+
+template <int MW>
+int launch_elementwise_m(int op, int64_t n, const double *A, int64_t psa, const double *B,
+                         int64_t psb, double *C, int64_t psc, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = (n + 255) / 256;
+  const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)8 * std::max(nsm, 1));
+  if (op == 0) elementwise_kernel<MW, 0><<<grid, 256, 0, s>>>(A, psa, B, psb, C, psc, n);
+  else if (op == 1) elementwise_kernel<MW, 1><<<grid, 256, 0, s>>>(A, psa, B, psb, C, psc, n);
+  else elementwise_kernel<MW, 2><<<grid, 256, 0, s>>>(A, psa, B, psb, C, psc, n);
+  return cuda_fail(cudaGetLastError(), "elementwise kernel launch");
+}
+
 // C = op(A) op(B): op(A) M x K (stored K x M when transA), op(B) K x N (stored
 // N x K when transB); m planes each.
 template <int MW>
@@ -205,6 +281,17 @@ int launch_textbook(int m, int transA, int transB, int64_t M, int64_t N, int64_t
       return fail(MW_EUNSUPPORTED, "MW_TEXTBOOK takes m = 2, 4 and 8");
   }
   return cuda_fail(cudaGetLastError(), "textbook kernel launch");
+}
+
+int launch_elementwise(int op, int m, int64_t n, const double *A, int64_t psa, const double *B,
+                       int64_t psb, double *C, int64_t psc, cudaStream_t s) {
+  if (n == 0) return MW_OK;
+  switch (m) {
+    case 2: return launch_elementwise_m<2>(op, n, A, psa, B, psb, C, psc, s);
+    case 4: return launch_elementwise_m<4>(op, n, A, psa, B, psb, C, psc, s);
+    case 8: return launch_elementwise_m<8>(op, n, A, psa, B, psb, C, psc, s);
+  }
+  return fail(MW_EUNSUPPORTED, "mw_elementwise takes m = 2, 4 and 8");
 }
 
 }  // namespace mw

@@ -243,3 +243,18 @@ def test_batch_spread_workspace_bound(mw):
     size = ctypes.c_size_t(0)
     assert mw._lib.mw_measure_spread_batched_workspace_size(
         3, ctypes.byref(b), ctypes.byref(size)) == mw.MW_EINVAL
+
+
+def test_elementwise_rejects_bad_arguments(mw):
+    """mw_elementwise checks op, m, n, pointers and strides on the host, before
+    any device work; n = 0 does nothing."""
+    f = mw._lib.mw_elementwise
+    p = ctypes.c_void_p(4096)                 # never dereferenced: every call below fails first
+    assert f(3, 2, 10, p, 10, p, 10, p, 10, None) == mw.MW_EINVAL
+    assert f(0, 3, 10, p, 10, p, 10, p, 10, None) == mw.MW_EINVAL
+    assert f(0, 16, 10, p, 10, p, 10, p, 10, None) == mw.MW_EINVAL
+    assert f(2, 2, -1, p, 10, p, 10, p, 10, None) == mw.MW_EINVAL
+    assert f(1, 4, 10, None, 10, p, 10, p, 10, None) == mw.MW_EINVAL
+    assert f(1, 4, 10, p, 9, p, 10, p, 10, None) == mw.MW_EINVAL
+    assert "stride" in mw._lib.mw_last_error().decode()
+    assert f(2, 8, 0, None, 0, None, 0, None, 0, None) == mw.MW_OK

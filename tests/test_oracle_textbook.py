@@ -123,3 +123,56 @@ def test_row_subset_matches_full(tc):
     part = tc.gemm(A, B, rows=[1, 7, 3], threads=2)
     assert np.array_equal(part[:, [1, 7, 3]], full[:, [1, 7, 3]])
     assert not part[:, 0].any()
+
+
+def _value(words):
+    return sum(Fraction(float(x)) for x in words)
+
+
+@pytest.mark.parametrize("m", [2, 4, 8, 16])
+def test_division_within_bound_and_renderings_agree(tc, m):
+    """Table 1's m-double division (long division, m + 1 quotient words): the C
+    and Python renderings agree bit for bit, and against exact rational
+    arithmetic the quotient is within 2^(1-52m) |a / b| over magnitudes spread
+    across 2^[-30, 30)."""
+    c = textbook.Counting()
+    rng = SplitMix64(70 + m)
+    X = loguniform_mdouble(rng, m, 2, 60, -30, 30)
+    for e in range(60):
+        a = [float(X[j, 0, e]) for j in range(m)]
+        b = [float(X[j, 1, e]) for j in range(m)]
+        q = tc.op("div", a, b)
+        assert q == c.div(a, b), e
+        exact_q = _value(a) / _value(b)
+        assert abs(_value(q) - exact_q) <= Fraction(2) ** (1 - 52 * m) * abs(exact_q), e
+
+
+@pytest.mark.parametrize("m", [2, 4, 8])
+def test_division_exact_cases(tc, m):
+    """a / a = 1, 0 / b = 0, and, for a in the renormalised form the operations
+    return (a + 0), a / 1 = a and division by a power of two scales every word
+    exactly."""
+    rng = SplitMix64(80 + m)
+    X = uniform_mdouble(rng, m, 2, 8)
+    one = [1.0] + [0.0] * (m - 1)
+    for e in range(8):
+        a = tc.op("add", [float(X[j, 0, e]) for j in range(m)], [0.0] * m)
+        assert tc.op("div", a, a) == one
+        assert tc.op("div", [0.0] * m, a) == [0.0] * m
+        assert tc.op("div", a, one) == a
+        for k in (-3, 1, 7):
+            p = [2.0 ** k] + [0.0] * (m - 1)
+            assert tc.op("div", a, p) == [x * 2.0 ** -k for x in a], (e, k)
+
+
+def test_elementwise_matches_single_operations(tc):
+    """The OpenMP entry-by-entry front end gives each entry's single operation."""
+    rng = SplitMix64(90)
+    for m in (2, 4, 8):
+        A = loguniform_mdouble(rng, m, 3, 7, -10, 10)
+        B = loguniform_mdouble(rng, m, 3, 7, -10, 10)
+        for name in ("add", "mul", "div"):
+            C = tc.elementwise(name, A, B)
+            for i in range(3):
+                for k in range(7):
+                    assert list(C[:, i, k]) == tc.op(name, list(A[:, i, k]), list(B[:, i, k]))
