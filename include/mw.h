@@ -270,7 +270,8 @@ int mw_convolve_batched(const mw_plan *plan, int64_t count, int64_t n, const dou
  * of the remainder, the remainder reduced by each word times B, renormalised),
  * within 2^(1-52m) |A_e / B_e| of the exact quotient on the tested inputs.
  * Entry e of word plane j of A at A[j * plane_stride_a + e] (likewise B, C);
- * plane strides at least n.  m = 2, 4 or 8.  One thread per entry; no workspace,
+ * plane strides at least n; C may be A or B (each entry is read before it is
+ * written).  m = 2, 4 or 8.  One thread per entry; no workspace,
  * asynchronous on `stream`; nothing is checked on the device (a zero leading
  * word of B gives IEEE infinities or NaNs).  MW_EINVAL for a bad op, m, n,
  * stride or NULL pointer (n = 0 does nothing). */
