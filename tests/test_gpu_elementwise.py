@@ -38,7 +38,7 @@ def test_elementwise_bit_exact(mw, cuda, tc, m, op):
 
 def test_elementwise_shapes_and_errors(mw, cuda, tc):
     """Any (m, ...) shape is one run of entries; one entry; a preallocated C; a
-    non-contiguous operand is refused."""
+    non-contiguous operand or an unknown operation is refused; C may be A."""
     rng = SplitMix64(1150)
     A = loguniform_mdouble(rng, 4, 3, 5, -4, 4)
     B = loguniform_mdouble(rng, 4, 3, 5, -4, 4)
@@ -52,3 +52,6 @@ def test_elementwise_shapes_and_errors(mw, cuda, tc):
         mw.mw_elementwise("add", to_dev(A, cuda).transpose(1, 2), to_dev(B, cuda).transpose(1, 2))
     with pytest.raises(mw.MWError):
         mw.mw_elementwise("pow", to_dev(A, cuda), to_dev(B, cuda))
+    tA = to_dev(A, cuda)                        # in place: C is A
+    mw.mw_elementwise("add", tA, to_dev(B, cuda), tA)
+    assert np.array_equal(tA.cpu().numpy(), tc.elementwise("add", A, B))
